@@ -1,0 +1,461 @@
+"""Benchmark of the LOPe stencil hot path on GB300.
+
+One step = the plain method at scale: 3D 7-point diffusion (FP32, 512^3,
+Dirichlet 0, c = 0.1, 50 sweeps) followed by the 2D 9-point radius-2 star
+(FP32, 8192^2, periodic, c = 0.1, 50 sweeps), both through lope_apply with
+their inputs resident in HBM.  `value` is grid-point updates per second over
+the whole job.  Each buffer (512 MiB, 256 MiB) is larger than L2, so no L2
+flush is needed between steps.
+
+Extra forms (outside the timed region, reported under "forms"): the batched
+launch (512 uneven 2D grids, 20 steps) against per-grid launches, the forward +
+adjoint (256^3, 100 steps, checkpoint every 10) against the plain forward,
+the shallow-water multi-field form in FP32 and BF16, and the FP64 256^2 case.
+
+--impl reference times the FP64 oracle on the host cores instead (bounded
+samples of the same workload mix).  Under torchrun every rank runs its own
+replica (the grids are independent problems; no collective is on the path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point updates/s and HBM GB/s vs peak; batched and fwd+adjoint vs plain"
+UNIT = "grid-point updates/s"
+N3, T3, C3 = 512, 50, 0.1
+N2, T2, C2 = 8192, 50, 0.1
+UPD3 = N3 ** 3 * T3
+UPD2 = N2 ** 2 * T2
+WORKLOAD = ("3D 7-point diffusion FP32 512^3 Dirichlet-0 c=0.1 x50 sweeps + "
+            "2D 9-point r=2 star FP32 8192^2 periodic c=0.1 x50 sweeps")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc, self.path, self.gpu = None, None, gpu_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{self.gpu}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = max(mx, float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU baseline
+def oracle_rates(budget_s=12.0):
+    """Oracle point-updates/s on this host for the two kernels of a step."""
+    import lope_inputs as LI
+    import oracle
+
+    oracle.build()
+    th = oracle.max_threads()
+    out = {}
+    for name, shape, kind in (("3d", (160, 160, 160), "diff7"), ("2d", (2048, 2048), "star9r2")):
+        u = LI.uniform_field(7, shape)
+        bc = [1, 1, 1] if kind == "diff7" else [0, 0]
+        t0 = time.perf_counter()
+        oracle.apply(u, kind, [0.1], 1, bc=bc, nthreads=th)
+        one = time.perf_counter() - t0
+        steps = int(max(1, min(40, (budget_s / 2) / max(one, 1e-6))))
+        t0 = time.perf_counter()
+        oracle.apply(u, kind, [0.1], steps, bc=bc, nthreads=th)
+        dt = time.perf_counter() - t0
+        out[name] = (u.size * steps / dt, f"{kind} {'x'.join(map(str, shape))} x{steps} sweeps", dt)
+    r3, s3, d3 = out["3d"]
+    r2, s2, d2 = out["2d"]
+    combined = (UPD3 + UPD2) / (UPD3 / r3 + UPD2 / r2)
+    return {"value": combined, "unit": UNIT, "cores": th, "kind": "oracle",
+            "sample": f"{s3} ({r3:.3e}/s) and {s2} ({r2:.3e}/s), FP64, combined in the "
+                      f"step's 2:1 update mix; {d3 + d2:.1f} s of CPU work"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import lope_inputs as LI
+    import oracle
+
+    oracle.build()
+    th = oracle.max_threads()
+    u3 = LI.uniform_field(1001, (128, 128, 128))
+    u2 = LI.uniform_field(1001, (2048, 2048), offset=1 << 32)
+    s3, s2 = 4, 1
+
+    def step():
+        oracle.apply(u3, "diff7", [C3], s3, bc=[1, 1, 1], nthreads=th)
+        oracle.apply(u2, "star9r2", [C2], s2, nthreads=th)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    upd = (u3.size * s3 + u2.size * s2) * args.steps
+    v = upd / dt
+    sample = (f"per step: diff7 128^3 x{s3} sweeps + star9r2 2048^2 x{s2} sweeps (FP64 oracle, "
+              f"plain C loops, OpenMP {th} threads)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD + " (bounded CPU sample)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": th, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def traffic_record(kernel_src):
+    """Per-launch DRAM bytes from the committed ncu summary, if it matches the source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)
+        with open(kernel_src, "rb") as fh:
+            h = hashlib.sha256(fh.read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") == h:
+            return rec
+    except Exception:
+        pass
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lope", choices=["lope", "reference"])
+    ap.add_argument("--main-only", action="store_true", help="skip the extra forms")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import lope_inputs as LI
+    import paper_1502_03504_gb300 as L
+    from paper_1502_03504_gb300 import build as B
+
+    ws, rank, local = dist_env()
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- inputs (seeded, on the host, then resident in HBM)
+    u3_h = torch.from_numpy(LI.uniform_field(1001, (N3, N3, N3)).astype(np.float32)).pin_memory()
+    u2_h = torch.from_numpy(LI.uniform_field(1001, (N2, N2), offset=1 << 32).astype(np.float32)).pin_memory()
+    u3 = u3_h.to(dev)
+    u2 = u2_h.to(dev)
+    o3, w3 = torch.empty_like(u3), torch.empty_like(u3)
+    o2, w2 = torch.empty_like(u2), torch.empty_like(u2)
+    g3 = L.Grid((N3, N3, N3), "f32", halo=1).set_boundary(kind="dirichlet", value=0.0)
+    s3 = L.Stencil.builtin("diff7", C3)
+    g2 = L.Grid((N2, N2), "f32", halo=2)
+    s2 = L.Stencil.builtin("star9r2", C2)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        L.apply(g3, s3, u3, out=o3, work=w3, nsteps=T3)
+        L.apply(g2, s2, u2, out=o2, work=w2, nsteps=T2)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    L.sync_status()
+
+    # ---------------- timed region: device-resident inputs
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    n0 = L.launch_count()
+    start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        L.apply(g3, s3, u3, out=o3, work=w3, nsteps=T3)
+        ev[i][1].record(stream)
+        L.apply(g2, s2, u2, out=o2, work=w2, nsteps=T2)
+        ev[i][2].record(stream)
+    end.record(stream)
+    barrier()
+    launches = L.launch_count() - n0
+    clk = clocks.stop()
+    L.sync_status()
+    ms = start.elapsed_time(end)
+    t3 = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    t2 = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
+    if pg:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    upd_step = UPD3 + UPD2
+    value = upd_step * args.steps * ws / (ms / 1e3)
+
+    # ---------------- end to end: host buffers, copies inside the timed region
+    h_o3 = torch.empty_like(u3_h).pin_memory()
+    h_o2 = torch.empty_like(u2_h).pin_memory()
+    e2e_steps = max(2, args.steps // 4)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        u3.copy_(u3_h, non_blocking=True)
+        u2.copy_(u2_h, non_blocking=True)
+        step()
+        h_o3.copy_(o3, non_blocking=True)
+        h_o2.copy_(o2, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if pg:
+        t = torch.tensor([e2e_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": upd_step * e2e_steps * ws / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": u3.numel() * 4 + u2.numel() * 4,
+           "d2h_bytes_per_step": o3.numel() * 4 + o2.numel() * 4}
+
+    # ---------------- roofline of the dominant kernel (3D TMA z-march)
+    peak, peak_kind = peaks()
+    alg3 = 8.0 * N3 ** 3  # one FP32 read + one FP32 write per point per launch
+    alg2 = 8.0 * N2 ** 2
+    launch3_s = t3 / 1e3 / T3
+    launch2_s = t2 / 1e3 / T2
+    ach3 = alg3 / launch3_s / 1e9
+    ach2 = alg2 / launch2_s / 1e9
+    tr = traffic_record(os.path.join(ROOT, "paper_1502_03504_gb300", "csrc", "k_tma.cu"))
+    roofline = {"bound": "hbm", "achieved": ach3, "peak": peak, "unit": "GB/s",
+                "frac": ach3 / peak, "traffic": tr["diff7_512_bytes_per_launch"] if tr else None,
+                "kernel": "tma3d_kernel<OpDiff7, float> (512^3, one sweep per launch)",
+                "alg_bytes_per_launch": alg3, "avg_launch_us": launch3_s * 1e6,
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+    kernels = {
+        "diff7_512": {"share_of_step": t3 / (t3 + t2), "avg_launch_us": launch3_s * 1e6,
+                      "alg_GBps": ach3, "frac_of_peak": ach3 / peak,
+                      "updates_per_s": N3 ** 3 / launch3_s},
+        "star9r2_8192": {"share_of_step": t2 / (t3 + t2), "avg_launch_us": launch2_s * 1e6,
+                         "alg_GBps": ach2, "frac_of_peak": ach2 / peak,
+                         "updates_per_s": N2 ** 2 / launch2_s,
+                         "traffic": tr.get("star9r2_8192_bytes_per_launch") if tr else None},
+    }
+
+    forms = {}
+    if not args.main_only and rank == 0:
+        del u3_h, u2_h, h_o3, h_o2
+        for name, fn in (("fp64_256", form_fp64), ("swe_4096", form_swe), ("batched_512", form_batch),
+                         ("fwd_adjoint_256", form_adjoint)):
+            try:
+                forms[name] = fn(L, LI, torch, dev, peak)
+            except Exception as e:  # reported, never hidden
+                forms[name] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_rates()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "updates_per_step": upd_step,
+                       "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (512 MiB and 256 MiB per buffer); no flush",
+                       "launch": "lope_apply auto plan: TMA z-march (3D), TMA tiles (2D), k=1"},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roofline,
+            "kernels": kernels, "cpu_baseline": cpu, "forms": forms,
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- extra forms
+def _time(torch, fn, reps=5):
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def form_fp64(L, LI, torch, dev, peak):
+    u = torch.from_numpy(LI.uniform_field(1000, (256, 256))).to(dev)
+    g = L.Grid((256, 256), "f64", halo=1)
+    s = L.Stencil.builtin("jacobi5", 0.2)
+    o, w = torch.empty_like(u), torch.empty_like(u)
+    ms = _time(torch, lambda: L.apply(g, s, u, out=o, work=w, nsteps=100), reps=20)
+    return {"workload": "jacobi5 FP64 256^2 periodic x100 (L2-resident, graph-replayed)",
+            "ms": ms, "updates_per_s": 256 * 256 * 100 / (ms / 1e3)}
+
+
+def form_swe(L, LI, torch, dev, peak):
+    n, T = 4096, 200
+    h, u, v = LI.swe_fields(1002, (n, n))
+    res = {}
+    for dtype, tdt, first in (("f32", torch.float32, h), ("bf16", torch.bfloat16, h - 1.0)):
+        f = [torch.from_numpy(LI.to_storage(x, "bf16" if dtype == "bf16" else "f32")).to(dev).to(tdt)
+             for x in (first, u, v)]
+        o = [torch.empty_like(x) for x in f]
+        w = [torch.empty_like(x) for x in f]
+        g = L.Grid((n, n), dtype, halo=1, nfields=3)
+        s = L.Stencil.builtin("swe_cgrid", 0.02, 1.0, 1.0)
+        ms = _time(torch, lambda: L.apply(g, s, f, out=o, work=w, nsteps=T), reps=3)
+        esz = 4 if dtype == "f32" else 2
+        res[dtype] = {"ms": ms, "point_updates_per_s": n * n * T / (ms / 1e3),
+                      "alg_GBps": 6 * esz * n * n * T / (ms / 1e3) / 1e9,
+                      "frac_of_peak": 6 * esz * n * n * T / (ms / 1e3) / 1e9 / peak}
+        del f, o, w
+    res["bf16_speedup_vs_f32"] = res["f32"]["ms"] / res["bf16"]["ms"]
+    res["workload"] = "C-grid shallow water (h,u,v) 4096^2 periodic x200; BF16 stores eta = h - 1"
+    return res
+
+
+def form_batch(L, LI, torch, dev, peak):
+    shapes, kinds = LI.batch_shapes(1003, 512)
+    grids, ins, outs, works = [], [], [], []
+    off = 512 * 3
+    for (ny, nx), k in zip(shapes, kinds):
+        g = L.Grid((ny, nx), "f32", halo=1)
+        g.set_boundaries([k, k])
+        grids.append(g)
+        ins.append(torch.from_numpy(LI.uniform(1003, ny * nx, off).astype(np.float32).reshape(ny, nx)).to(dev))
+        off += ny * nx
+    outs = [torch.empty_like(x) for x in ins]
+    works = [torch.empty_like(x) for x in ins]
+    s = L.Stencil.builtin("jacobi5", 0.2)
+    T = 20
+    pts = sum(a * b for a, b in shapes)
+    wsb = torch.empty(L.batch_workspace_size(grids, s), dtype=torch.uint8, device=dev)
+    best = None
+    for k in (1, 2, 4, 5):
+        for tx, ty in ((64, 32), (128, 16), (64, 16), (128, 32)):
+            cfg = L.Launch(2, tx, ty, k, -1)
+            ms = _time(torch, lambda: L.apply_batch(grids, s, ins, outs, works, T, cfg, wsb), reps=2)
+            if best is None or ms < best[0]:
+                best = (ms, k, tx, ty)
+    ms, k, tx, ty = best
+    ms = _time(torch, lambda: L.apply_batch(grids, s, ins, outs, works, T, L.Launch(2, tx, ty, k, -1), wsb), reps=5)
+    per1 = L.Launch(2, 64, 32, 1, -1)
+
+    def per_grid():
+        for g, i, o, w in zip(grids, ins, outs, works):
+            L.apply(g, s, i, out=o, work=w, nsteps=T, launch=per1)
+
+    ms_pg = _time(torch, per_grid, reps=2)
+    return {"workload": "512 jacobi5 FP32 grids, sides U{64..2048}, mixed periodic/Dirichlet, x20",
+            "points": pts, "batched_ms": ms, "batched_updates_per_s": pts * T / (ms / 1e3),
+            "batched_choice": {"tile": [tx, ty], "tsteps": k},
+            "per_grid_ms": ms_pg, "per_grid_updates_per_s": pts * T / (ms_pg / 1e3),
+            "per_grid_launches": 512 * T, "speedup": ms_pg / ms,
+            "batched_alg_GBps_effective": 8 * pts * T / (ms / 1e3) / 1e9}
+
+
+def form_adjoint(L, LI, torch, dev, peak):
+    n, T, K = 256, 100, 10
+    u0 = torch.from_numpy(LI.uniform_field(1004, (n, n, n)).astype(np.float32)).to(dev)
+    tg = torch.from_numpy(LI.normal_field(2004, (n, n, n)).astype(np.float32)).to(dev)
+    g = L.Grid((n, n, n), "f32", halo=1)
+    s = L.Stencil.builtin("diff7", 0.1)
+    o, w = torch.empty_like(u0), torch.empty_like(u0)
+    ms_fwd = _time(torch, lambda: L.apply(g, s, u0, out=o, work=w, nsteps=T), reps=5)
+    wsb = torch.empty(L.workspace_size(g, s, T, K), dtype=torch.uint8, device=dev)
+    gu = torch.empty_like(u0)
+    ms_adj = _time(torch, lambda: L.adjoint(g, s, u0, tg, T, K, grad_u0=gu, workspace=wsb), reps=3)
+    loss, _, gc = L.adjoint(g, s, u0, tg, T, K, grad_u0=gu, workspace=wsb)
+    return {"workload": "diff7 FP32 256^3 periodic x100, loss sum((u_T-target)^2), checkpoint 10",
+            "plain_forward_ms": ms_fwd, "fwd_adjoint_ms": ms_adj, "ratio": ms_adj / ms_fwd,
+            "loss": loss, "dL_dc": gc}
+
+
+if __name__ == "__main__":
+    main()

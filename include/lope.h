@@ -1,0 +1,222 @@
+/*
+ * lope.h — C ABI of the GB300 (sm_103a) library for the hot path of
+ * locally-oriented programming (LOPe; Rasmussen, Sottile, Nagle, Rasmussen,
+ * arXiv:1502.03504): a local function that writes one array element and reads
+ * a fixed-width halo around it is applied at every point of a 2D or 3D
+ * structured grid, for many time steps.
+ *
+ * Conventions shared by every call:
+ *  - Extents are given slowest axis first; the last axis is contiguous (C
+ *    order).  The paper's local offsets U(dx,dy[,dz]) (Sec. 2.2, "LOPe index
+ *    notation") map dx to the fastest axis, dy to the next, dz to the slowest.
+ *  - Only interior points are stored.  Halo (ghost) values are produced inside
+ *    the kernels from the boundary condition; they are never written to memory.
+ *  - All field buffers are device memory owned by the caller; handles are owned
+ *    by the library.  Pointers must be 16-byte aligned.  Multi-field grids pass
+ *    one pointer per field, in the stencil's field order.
+ *  - Calls are asynchronous on the given CUDA stream (NULL = legacy default
+ *    stream) unless stated otherwise.
+ *  - Every call returns a status; on failure lope_last_error() describes it.
+ *    There is no CPU fallback: a missing or unusable GPU is an error.
+ */
+#ifndef LOPE_H
+#define LOPE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LOPE_OK = 0,
+  LOPE_ERR_INVALID = 1,     /* bad argument (shape, halo, pointer, size)          */
+  LOPE_ERR_UNSUPPORTED = 2, /* valid request this build does not implement         */
+  LOPE_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed                   */
+  LOPE_ERR_ALLOC = 4,       /* host allocation failed / workspace too small        */
+  LOPE_ERR_TIMEOUT = 5,     /* a bounded in-kernel wait gave up (device error flag) */
+  LOPE_ERR_NUMERIC = 6      /* non-finite result where a finite one was required   */
+} lope_status;
+
+typedef enum { LOPE_F64 = 0, LOPE_F32 = 1, LOPE_BF16 = 2 } lope_dtype;
+
+/* Halo contents (Sec. 2.2 "Halo regions": the halo holds boundary-value
+ * information).  PERIODIC is the paper's BC=CYCLIC (Sec. 3.2); DIRICHLET holds a
+ * fixed value in the halo for every step. */
+typedef enum { LOPE_BC_PERIODIC = 0, LOPE_BC_DIRICHLET = 1 } lope_bc;
+
+typedef struct lope_grid lope_grid;
+typedef struct lope_stencil lope_stencil;
+
+/* Grid descriptor: a halo-annotated array HALO(lo:*:hi) per axis (Sec. 2.2
+ * "Halo regions").  ndim is 2 or 3; extents[ndim] slowest first, each >= 1;
+ * halo_lo/halo_hi[ndim] are the declared halo widths (0..4) per axis, which
+ * bound the offsets a local function may read (Sec. 3.5: no out-of-bounds
+ * indexing).  nfields is 1..3.  All boundaries start PERIODIC.
+ * Errors: LOPE_ERR_INVALID for any out-of-range argument or NULL pointer. */
+lope_status lope_grid_create(lope_grid** grid, int ndim, const int64_t* extents,
+                             const int* halo_lo, const int* halo_hi, lope_dtype storage,
+                             int nfields);
+void lope_grid_destroy(lope_grid* grid);
+
+/* Boundary condition of one side of one axis (axis 0..ndim-1 slowest first, or
+ * -1 for all axes; side 0 low, 1 high, -1 both).  A periodic axis must be
+ * periodic on both sides.  Changing the boundary does not change the local
+ * function (Sec. 3.4, first advantage).  value is the Dirichlet halo value. */
+lope_status lope_set_boundary(lope_grid* grid, int axis, int side, lope_bc kind, double value);
+
+/* Built-in local functions (Sec. 2.2, Fig. 1 and its generalisations):
+ *   "jacobi5"   2D, params {c}:      U(0,0) + c (U(-1,0)+U(1,0)+U(0,-1)+U(0,1) - 4 U(0,0));
+ *                                    c = 1 is Fig. 1 exactly.
+ *   "diff7"     3D, params {c}:      the 7-point analogue, - 6 U(0,0,0).
+ *   "star9r2"   2D, params {c}:      U(0,0) + c (L4x + L4y), L4 the fourth-order
+ *                                    1D Laplacian (-1/12, 4/3, -5/2, 4/3, -1/12).
+ *   "swe_cgrid" 2D, 3 fields (h,u,v), params {dt, g, H}: linearised shallow
+ *                                    water on an Arakawa C-grid, forward Euler.
+ * Errors: LOPE_ERR_INVALID for an unknown name or wrong parameter count. */
+lope_status lope_stencil_create_builtin(lope_stencil** stencil, const char* name,
+                                        const double* params, int nparams);
+
+/* General linear local function U(0,0) = sum_o w[o] U(o) over the box of
+ * radius `radius` (1..2): weights has (2r+1)^ndim entries, slowest offset first,
+ * i.e. weights[((dz+r)*(2r+1) + dy+r)*(2r+1) + dx+r] (dz only for ndim = 3).
+ * Star-shaped tables (all off-axis entries zero) take the TMA kernels; tables
+ * with corners take the shared-memory / direct kernels. */
+lope_status lope_stencil_create_linear(lope_stencil** stencil, int ndim, int radius,
+                                       const double* weights);
+void lope_stencil_destroy(lope_stencil* stencil);
+
+/* Apply the local function at every interior point, nsteps times (Sec. 3.2:
+ * each do-concurrent sweep is followed by a halo refresh).  Every sweep reads
+ * a frozen snapshot of the previous state (Sec. 2.2 double buffering, Sec. 3.5
+ * implicit synchronisation): results do not depend on tiling, traversal order
+ * or temporal blocking.
+ *   in[nfields]   read-only input state (never written)
+ *   out[nfields]  final state; must not alias in
+ *   work[nfields] scratch state of the same size, needed when nsteps >= 2
+ *                 (may be NULL for nsteps <= 1)
+ * nsteps = 0 copies in to out.  The planner picks kernel, tile and temporal
+ * depth (see lope_apply_with).  Errors: LOPE_ERR_INVALID (aliasing, NULL,
+ * misaligned pointers, stencil radius above the declared halo, dimension
+ * mismatch), LOPE_ERR_UNSUPPORTED (dtype/stencil pair not built),
+ * LOPE_ERR_CUDA (launch failure). */
+lope_status lope_apply(const lope_grid* grid, const lope_stencil* stencil, const void* const* in,
+                       void* const* out, void* const* work, int64_t nsteps, void* cuda_stream);
+
+/* Launch choices, for tests and tuning.  Zero fields mean "planner decides".
+ *   path:    0 auto, 1 TMA tiles (2D tiles / 3D z-march; star stencils, 16-byte
+ *            row pitch), 2 shared-memory trapezoid tiles with temporal blocking
+ *            (2D, any stencil, any shape), 3 direct (any stencil, one thread per
+ *            point).
+ *   tile_x, tile_y: tile shape for path 2 (tile_x in {32,64,128}, tile_y in
+ *            {8,16,32}).
+ *   tsteps:  temporal depth k (sweeps fused per launch; path 2 only, 1..8).
+ *   graph:   0 auto, 1 capture the launch sequence in a CUDA graph, -1 never. */
+typedef struct {
+  int path;
+  int tile_x, tile_y;
+  int tsteps;
+  int graph;
+} lope_launch;
+
+lope_status lope_apply_with(const lope_grid* grid, const lope_stencil* stencil,
+                            const void* const* in, void* const* out, void* const* work,
+                            int64_t nsteps, const lope_launch* cfg, void* cuda_stream);
+
+/* Time candidate launch choices on the caller's buffers (out and work are
+ * overwritten) and remember the fastest for this grid shape, dtype, stencil and
+ * boundary; later lope_apply calls use it.  *best receives the choice and
+ * *best_ms its time for nsteps.  Synchronises the stream. */
+lope_status lope_autotune(const lope_grid* grid, const lope_stencil* stencil,
+                          const void* const* in, void* const* out, void* const* work,
+                          int64_t nsteps, lope_launch* best, double* best_ms, void* cuda_stream);
+
+/* Batched form: n independent grids of possibly different extents and
+ * boundaries (same dtype, nfields and stencil) advanced nsteps each in one
+ * persistent launch per call, replayed from a cached CUDA graph.  in/out/work
+ * hold n*nfields pointers, grid-major.  workspace is caller device memory of at
+ * least lope_batch_workspace_size bytes; it holds the work list and the
+ * inter-block barrier and must stay untouched between calls that reuse it.
+ * cfg may be NULL (tile and temporal depth from the batch autotuner cache or
+ * defaults).  Errors as lope_apply; LOPE_ERR_TIMEOUT is reported by
+ * lope_sync_status if a bounded barrier wait gave up. */
+lope_status lope_batch_workspace_size(int n, const lope_grid* const* grids,
+                                      const lope_stencil* stencil, const lope_launch* cfg,
+                                      size_t* bytes);
+lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_stencil* stencil,
+                             const void* const* in, void* const* out, void* const* work,
+                             int64_t nsteps, const lope_launch* cfg, void* workspace,
+                             size_t workspace_bytes, void* cuda_stream);
+
+/* Differentiation of u_T = A^T u_0 for linear stencils, by the discrete adjoint
+ * (transposed stencil, run backward in time) with recomputation from
+ * checkpoints stored every `checkpoint_every` steps.
+ *
+ * lope_adjoint: loss = sum (u_T - target)^2 (FP64 accumulation), then
+ *   grad_u0 = dL/du_0 (device, grid dtype) and *grad_coeff = dL/dc (host,
+ *   diffusion-form builtins only; 0 otherwise) and *loss (host).  Synchronises.
+ * lope_vjp: the same reverse sweep for an arbitrary upstream gradient grad_uT
+ *   (device); *grad_coeff_dev is a device double that receives dL/dc (may be
+ *   NULL).  Asynchronous.
+ * lope_forward_ckpt: the forward pass alone, writing u_T and leaving the
+ *   checkpoints in the workspace for a later lope_vjp with the same u0,
+ *   nsteps and checkpoint_every (vjp then skips its own forward when
+ *   reuse_checkpoints = 1).
+ * workspace: device memory of lope_workspace_size(grid, stencil, nsteps,
+ *   checkpoint_every) bytes.  Errors: LOPE_ERR_UNSUPPORTED for non-linear
+ *   stencils; LOPE_ERR_ALLOC if workspace_bytes is too small. */
+lope_status lope_workspace_size(const lope_grid* grid, const lope_stencil* stencil,
+                                int64_t nsteps, int64_t checkpoint_every, size_t* bytes);
+lope_status lope_forward_ckpt(const lope_grid* grid, const lope_stencil* stencil, const void* u0,
+                              void* uT, int64_t nsteps, int64_t checkpoint_every, void* workspace,
+                              size_t workspace_bytes, void* cuda_stream);
+lope_status lope_vjp(const lope_grid* grid, const lope_stencil* stencil, const void* u0,
+                     const void* grad_uT, int64_t nsteps, int64_t checkpoint_every,
+                     int reuse_checkpoints, void* grad_u0, double* grad_coeff_dev,
+                     void* workspace, size_t workspace_bytes, void* cuda_stream);
+lope_status lope_adjoint(const lope_grid* grid, const lope_stencil* stencil, const void* u0,
+                         const void* target, int64_t nsteps, int64_t checkpoint_every,
+                         void* grad_u0, double* grad_coeff, double* loss, void* workspace,
+                         size_t workspace_bytes, void* cuda_stream);
+
+/* FP64 reductions over a stored field (conservation checks, losses):
+ * *result_dev (device double) = sum x[i]  (op 0), or sum (x[i]-y[i])^2 (op 1),
+ * over n elements of dtype `dtype`.  scratch is device memory of at least
+ * lope_reduce_scratch_bytes() bytes for per-block partial sums; the summation
+ * order is fixed, so results are reproducible run to run. */
+size_t lope_reduce_scratch_bytes(void);
+lope_status lope_reduce(int op, lope_dtype dtype, const void* x, const void* y, int64_t n,
+                        double* result_dev, void* scratch, void* cuda_stream);
+
+/* Runtime options (process-wide):
+ *   "wait_limit_ms"      limit of each bounded inter-block barrier wait in the
+ *                        batched kernel (default 1000).
+ *   "batch_skip_arrive"  failure-detection hook for tests: block `value` of the
+ *                        next batched plans never arrives at the first
+ *                        inter-block barrier, so the other blocks' bounded waits
+ *                        run out and lope_sync_status reports LOPE_ERR_TIMEOUT
+ *                        (-1, the default, disables it).  No fault is raised on
+ *                        the GPU: every wait ends by itself.
+ * Errors: LOPE_ERR_INVALID for an unknown name or out-of-range value. */
+lope_status lope_set_option(const char* name, int64_t value);
+
+/* Synchronise the stream, then report (and clear) a device-side error flag set
+ * by a bounded wait that gave up: LOPE_ERR_TIMEOUT, else LOPE_OK. */
+lope_status lope_sync_status(void* cuda_stream);
+
+/* Number of kernels this library has launched in this process (graph
+ * replays count each kernel node once per replay). */
+int64_t lope_launch_count(void);
+
+/* Message for the last failed call on this thread (never NULL). */
+const char* lope_last_error(void);
+
+/* Library version string. */
+const char* lope_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOPE_H */

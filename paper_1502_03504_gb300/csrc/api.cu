@@ -1,0 +1,949 @@
+// C ABI of the LOPe library: handles, validation, the launch planner (kernel
+// path, tile shape, temporal depth), CUDA-graph caching, the autotuner, the
+// batched-plan cache and the adjoint driver with checkpointed recomputation.
+//
+// Halo declarations and the no-out-of-bounds rule (Sec. 2.2 "Halo regions",
+// Sec. 3.5) are checked here: a stencil may not read further than the halo
+// its grid declares.  There is no host fallback: every computation runs in
+// the kernels of this library.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "lope.h"
+#include "lope_internal.h"
+
+struct lope_grid {
+  lope::Geom g;
+  int halo_lo[3], halo_hi[3];  // per axis, slowest first (2D: axis 0 unused)
+};
+
+struct lope_stencil {
+  lope::StencilDesc s;
+  int nf;
+};
+
+namespace lope {
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+std::atomic<int64_t> g_wait_limit_ms{1000};
+std::atomic<int64_t> g_skip_arrive{-1};
+thread_local bool g_capturing = false;
+std::atomic<int64_t> g_launches{0};
+
+lope_status fail(lope_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+lope_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(LOPE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int esize(int dtype) { return dtype == kF64 ? 8 : dtype == kF32 ? 4 : 2; }
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+int64_t npts(const Geom& g) { return g.n[0] * g.n[1] * g.n[2]; }
+
+// Per-device state: the device error flag and a stream used for graph capture.
+struct DevState {
+  int* err = nullptr;
+  cudaStream_t capture = nullptr;
+};
+std::mutex g_dev_mu;
+std::map<int, DevState> g_dev;
+
+lope_status dev_state(DevState** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  DevState& d = g_dev[dev];
+  if (!d.err) {
+    if ((e = cudaMalloc(&d.err, sizeof(int))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(error flag)");
+    if ((e = cudaMemset(d.err, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    if ((e = cudaStreamCreateWithFlags(&d.capture, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamCreate");
+  }
+  *out = &d;
+  return LOPE_OK;
+}
+
+// ------------------------------------------------------------------ validation
+int stencil_nf(const StencilDesc& s) { return s.kind == kSwe ? 3 : 1; }
+
+lope_status check_pair(const lope_grid* grid, const lope_stencil* st) {
+  if (!grid || !st) return fail(LOPE_ERR_INVALID, "NULL grid or stencil");
+  const Geom& g = grid->g;
+  const StencilDesc& s = st->s;
+  if (s.ndim != g.ndim) return fail(LOPE_ERR_INVALID, "stencil and grid dimensions differ");
+  if (stencil_nf(s) != g.nf) return fail(LOPE_ERR_INVALID, "stencil and grid field counts differ");
+  for (int ax = 3 - g.ndim; ax < 3; ++ax) {
+    if (s.radius > grid->halo_lo[ax] || s.radius > grid->halo_hi[ax])
+      return fail(LOPE_ERR_INVALID, "stencil radius exceeds the declared halo (out-of-bounds read)");
+    if (g.bc[ax][0] == kPeriodic && g.n[ax] < s.radius)
+      return fail(LOPE_ERR_INVALID, "periodic axis shorter than the stencil radius");
+  }
+  return LOPE_OK;
+}
+
+lope_status check_fields(const Geom& g, const void* const* in, void* const* out, void* const* work,
+                         bool need_work) {
+  if (!in || !out) return fail(LOPE_ERR_INVALID, "NULL field array");
+  if (need_work && !work) return fail(LOPE_ERR_INVALID, "nsteps >= 2 needs work buffers");
+  for (int f = 0; f < g.nf; ++f) {
+    if (!in[f] || !out[f]) return fail(LOPE_ERR_INVALID, "NULL field pointer");
+    if (!aligned16(in[f]) || !aligned16(out[f])) return fail(LOPE_ERR_INVALID, "field pointer not 16-byte aligned");
+    if (need_work && (!work[f] || !aligned16(work[f]))) return fail(LOPE_ERR_INVALID, "bad work pointer");
+    const size_t bytes = size_t(npts(g)) * esize(g.dtype);
+    auto overlap = [&](const void* a, const void* b) {
+      const char* x = static_cast<const char*>(a);
+      const char* y = static_cast<const char*>(b);
+      return x < y + bytes && y < x + bytes;
+    };
+    for (int h = 0; h < g.nf; ++h) {
+      if (overlap(in[f], out[h])) return fail(LOPE_ERR_INVALID, "out aliases in (double buffering required)");
+      if (need_work && (overlap(work[f], out[h]) || overlap(work[f], in[h])))
+        return fail(LOPE_ERR_INVALID, "work aliases in or out");
+    }
+  }
+  return LOPE_OK;
+}
+
+// ------------------------------------------------------------------ planning
+struct Choice {
+  int path, tile_x, tile_y, k;
+};
+
+using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, Choice> g_tune;
+
+TuneKey tune_key(const Geom& g, const StencilDesc& s) {
+  int bcs = 0;
+  for (int ax = 0; ax < 3; ++ax)
+    for (int sd = 0; sd < 2; ++sd) bcs = bcs * 2 + (g.bc[ax][sd] == kDirichlet);
+  return TuneKey(g.ndim, g.n[0], g.n[1], g.n[2], g.dtype, s.kind, s.radius, int(s.star), bcs,
+                 g.nf, 0);
+}
+
+StepArgs base_args(const Geom& g, const StencilDesc& s, int* err, cudaStream_t st) {
+  StepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = g;
+  a.s = s;
+  a.ksteps = 1;
+  a.err = err;
+  a.stream = st;
+  return a;
+}
+
+Choice default_choice(const Geom& g, const StencilDesc& s, int* err) {
+  StepArgs a = base_args(g, s, err, nullptr);
+  for (int f = 0; f < g.nf; ++f) a.in[f] = reinterpret_cast<const void*>(uintptr_t(256));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(g, s));
+    if (it != g_tune.end()) return it->second;
+  }
+  if (tma_supported(a)) return {kPathTma, 0, 0, 1};
+  if (g.ndim == 2) return {kPathTrap, 64, 32, 1};
+  return {kPathDirect, 0, 0, 1};
+}
+
+lope_status resolve(const Geom& g, const StencilDesc& s, const void* const* in,
+                    const lope_launch* cfg, int* err, Choice* c) {
+  Choice d = default_choice(g, s, err);
+  if (cfg && cfg->path != kPathAuto) {
+    d.path = cfg->path;
+    d.tile_x = cfg->tile_x;
+    d.tile_y = cfg->tile_y;
+    d.k = cfg->tsteps > 0 ? cfg->tsteps : 1;
+  } else if (cfg) {
+    if (cfg->tsteps > 0) d.k = cfg->tsteps;
+    if (cfg->tile_x > 0) d.tile_x = cfg->tile_x;
+    if (cfg->tile_y > 0) d.tile_y = cfg->tile_y;
+  }
+  if (d.path == kPathTrap) {
+    if (d.tile_x <= 0) d.tile_x = 64;
+    if (d.tile_y <= 0) d.tile_y = 32;
+  }
+  StepArgs a = base_args(g, s, err, nullptr);
+  for (int f = 0; f < g.nf; ++f) a.in[f] = in ? in[f] : nullptr;
+  a.ksteps = d.k;
+  a.tile_x = d.tile_x;
+  a.tile_y = d.tile_y;
+  bool ok = false;
+  switch (d.path) {
+    case kPathTma: ok = tma_supported(a); break;
+    case kPathTrap: ok = trap2d_supported(a); break;
+    case kPathDirect: ok = direct_supported(a); break;
+    default: ok = false;
+  }
+  if (!ok) return fail(LOPE_ERR_UNSUPPORTED, "requested launch path does not support this grid/stencil/depth");
+  *c = d;
+  return LOPE_OK;
+}
+
+// Issue the launch sequence: ceil(nsteps/k) launches ping-ponging between out
+// and work so that the last one writes out.
+cudaError_t issue(const Geom& g, const StencilDesc& s, const Choice& c, const void* const* in,
+                  void* const* out, void* const* work, int64_t nsteps, int* err, cudaStream_t st) {
+  const int64_t L = (nsteps + c.k - 1) / c.k;
+  const void* src[kMaxFields];
+  for (int f = 0; f < g.nf; ++f) src[f] = in[f];
+  for (int64_t j = 0; j < L; ++j) {
+    StepArgs a = base_args(g, s, err, st);
+    a.ksteps = int(std::min<int64_t>(c.k, nsteps - j * c.k));
+    a.tile_x = c.tile_x;
+    a.tile_y = c.tile_y;
+    const bool to_out = ((L - 1 - j) & 1) == 0;
+    for (int f = 0; f < g.nf; ++f) {
+      a.in[f] = src[f];
+      a.out[f] = to_out ? out[f] : work[f];
+    }
+    cudaError_t e;
+    switch (c.path) {
+      case kPathTma: e = launch_tma(a, nullptr); break;
+      case kPathTrap: e = launch_trap2d(a); break;
+      default: e = launch_direct(a, nullptr); break;
+    }
+    if (e != cudaSuccess) return e;
+    for (int f = 0; f < g.nf; ++f) src[f] = a.out[f];
+  }
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------------ graph cache
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;
+};
+using GraphKey = std::vector<int64_t>;
+std::mutex g_graph_mu;
+std::map<GraphKey, GraphEntry> g_graphs;
+
+GraphKey graph_key(const Geom& g, const StencilDesc& s, const Choice& c, const void* const* in,
+                   void* const* out, void* const* work, int64_t nsteps) {
+  GraphKey k;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  k.push_back(dev);
+  const int64_t* gw = reinterpret_cast<const int64_t*>(&g);
+  k.insert(k.end(), gw, gw + sizeof(Geom) / 8);
+  const int64_t* sw = reinterpret_cast<const int64_t*>(&s);
+  k.insert(k.end(), sw, sw + sizeof(StencilDesc) / 8);
+  k.insert(k.end(), {c.path, c.tile_x, c.tile_y, c.k, nsteps});
+  for (int f = 0; f < g.nf; ++f) {
+    k.push_back(int64_t(reinterpret_cast<uintptr_t>(in[f])));
+    k.push_back(int64_t(reinterpret_cast<uintptr_t>(out[f])));
+    k.push_back(work ? int64_t(reinterpret_cast<uintptr_t>(work[f])) : 0);
+  }
+  return k;
+}
+
+template <class F>
+lope_status run_graph(const GraphKey& key, int64_t kernels, cudaStream_t st, F&& body) {
+  DevState* d = nullptr;
+  lope_status rs = dev_state(&d);
+  if (rs != LOPE_OK) return rs;
+  GraphEntry ent;
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto it = g_graphs.find(key);
+    if (it != g_graphs.end()) ent = it->second;
+  }
+  if (!ent.exec) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(d->capture, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    g_capturing = true;
+    cudaError_t eb = body(d->capture);
+    g_capturing = false;
+    e = cudaStreamEndCapture(d->capture, &graph);
+    if (eb != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(eb, "capturing launches");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ent.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    ent.kernels = kernels;
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    if (g_graphs.size() > 256) {
+      for (auto& kv : g_graphs) cudaGraphExecDestroy(kv.second.exec);
+      g_graphs.clear();
+    }
+    g_graphs[key] = ent;
+  }
+  cudaError_t e = cudaGraphLaunch(ent.exec, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  count_launches(ent.kernels);
+  return LOPE_OK;
+}
+
+lope_status apply_impl(const lope_grid* grid, const lope_stencil* st, const void* const* in,
+                       void* const* out, void* const* work, int64_t nsteps, const lope_launch* cfg,
+                       cudaStream_t stream) {
+  lope_status rs = check_pair(grid, st);
+  if (rs != LOPE_OK) return rs;
+  if (nsteps < 0) return fail(LOPE_ERR_INVALID, "nsteps < 0");
+  const Geom& g = grid->g;
+  const StencilDesc& s = st->s;
+  DevState* d = nullptr;
+  if ((rs = dev_state(&d)) != LOPE_OK) return rs;
+  Choice c;
+  if ((rs = resolve(g, s, in, cfg, d->err, &c)) != LOPE_OK) return rs;
+  const int64_t L = nsteps == 0 ? 0 : (nsteps + c.k - 1) / c.k;
+  if ((rs = check_fields(g, in, out, work, L >= 2)) != LOPE_OK) return rs;
+  if (nsteps == 0) {
+    for (int f = 0; f < g.nf; ++f) {
+      cudaError_t e = cudaMemcpyAsync(out[f], in[f], size_t(npts(g)) * esize(g.dtype),
+                                      cudaMemcpyDeviceToDevice, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    }
+    return LOPE_OK;
+  }
+  const int gmode = cfg ? cfg->graph : 0;
+  const bool use_graph = gmode == 1 || (gmode == 0 && L >= 8 && npts(g) <= (int64_t(1) << 22));
+  if (use_graph) {
+    return run_graph(graph_key(g, s, c, in, out, work, nsteps), L, stream, [&](cudaStream_t cs) {
+      return issue(g, s, c, in, out, work, nsteps, d->err, cs);
+    });
+  }
+  cudaError_t e = issue(g, s, c, in, out, work, nsteps, d->err, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return LOPE_OK;
+}
+
+// ------------------------------------------------------------------ adjoint
+struct AdjLayout {
+  int64_t nseg;
+  size_t field;  // bytes per state, 256-aligned
+  size_t off_ckpt, off_seg, off_tmp, off_lam, off_part, off_scal, total;
+  int partials;
+};
+
+constexpr int kPartials = 8192;
+
+AdjLayout adj_layout(const Geom& g, int64_t nsteps, int64_t K) {
+  AdjLayout L;
+  L.nseg = (nsteps + K - 1) / K;
+  L.field = (size_t(npts(g)) * esize(g.dtype) + 255) / 256 * 256;
+  size_t off = 0;
+  L.off_ckpt = off;  // checkpoints 1..nseg-1 and u_T (nseg states)
+  off += size_t(L.nseg) * L.field;
+  L.off_seg = off;   // recomputed states inside a segment (K-1)
+  off += size_t(std::max<int64_t>(K - 1, 0)) * L.field;
+  L.off_tmp = off;   // forward work buffer
+  off += L.field;
+  L.off_lam = off;   // two adjoint buffers
+  off += 2 * L.field;
+  L.off_part = off;
+  L.partials = kPartials;
+  off += size_t(kPartials) * sizeof(double);
+  L.off_scal = off;  // loss, dL/dc
+  off += 256;
+  L.total = off;
+  return L;
+}
+
+lope_status check_linear_for_adjoint(const lope_grid* grid, const lope_stencil* st) {
+  lope_status rs = check_pair(grid, st);
+  if (rs != LOPE_OK) return rs;
+  const StencilDesc& s = st->s;
+  if (s.kind == kSwe) return fail(LOPE_ERR_UNSUPPORTED, "adjoint needs a single-field linear stencil");
+  if (s.kind != kLinear) {
+    for (int ax = 0; ax < 3; ++ax)
+      for (int sd = 0; sd < 2; ++sd)
+        if (grid->g.bc[ax][sd] == kDirichlet && grid->g.bval[ax][sd] != 0.0)
+          return fail(LOPE_ERR_UNSUPPORTED, "dL/dc with a non-zero Dirichlet value is not implemented");
+  }
+  return LOPE_OK;
+}
+
+// Forward from u0 to the checkpoints and u_T (u_T written to `uT`).
+lope_status forward_ckpt_impl(const lope_grid* grid, const lope_stencil* st, const void* u0,
+                              void* uT, int64_t nsteps, int64_t K, char* ws, const AdjLayout& L,
+                              cudaStream_t stream) {
+  void* tmp = ws + L.off_tmp;
+  const void* cur = u0;
+  for (int64_t i = 0; i < L.nseg; ++i) {
+    const int64_t len = std::min<int64_t>(K, nsteps - i * K);
+    void* dst = (i == L.nseg - 1) ? uT : static_cast<void*>(ws + L.off_ckpt + size_t(i) * L.field);
+    const void* in1[1] = {cur};
+    void* out1[1] = {dst};
+    void* work1[1] = {tmp};
+    lope_launch cfg = {0, 0, 0, 0, -1};
+    lope_status rs = apply_impl(grid, st, in1, out1, work1, len, &cfg, stream);
+    if (rs != LOPE_OK) return rs;
+    cur = dst;
+  }
+  return LOPE_OK;
+}
+
+StencilDesc reflected(const StencilDesc& s) {
+  StencilDesc r = s;
+  const int R = s.radius, side = 2 * R + 1;
+  for (int ax = 0; ax < 3; ++ax)
+    for (int d = 0; d < side; ++d) r.star_w[ax][d] = s.star_w[ax][side - 1 - d];
+  const int cnt = (s.ndim == 3 ? side : 1) * side * side;
+  for (int i = 0; i < cnt; ++i) r.box[i] = s.box[cnt - 1 - i];
+  return r;
+}
+
+// Reverse sweep: lambda from `lamT` back to grad_u0, recomputing states from
+// checkpoints; dL/dc accumulated into per-block partials, finalised into gc.
+lope_status reverse_impl(const lope_grid* grid, const lope_stencil* st, const void* u0,
+                         const void* lamT, int64_t nsteps, int64_t K, void* grad_u0, double* gc,
+                         char* ws, const AdjLayout& L, int* err, cudaStream_t stream) {
+  const Geom& g = grid->g;
+  Geom ga = g;  // lambda's halo: Dirichlet sides read zero
+  for (int ax = 0; ax < 3; ++ax)
+    for (int sd = 0; sd < 2; ++sd) ga.bval[ax][sd] = 0.0;
+  const StencilDesc& s = st->s;
+  const bool diffusion = s.kind != kLinear;
+  const StencilDesc sa = diffusion ? s : reflected(s);
+  double* partials = reinterpret_cast<double*>(ws + L.off_part);
+  cudaError_t e = cudaMemsetAsync(partials, 0, sizeof(double) * L.partials, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  StepArgs probe = base_args(ga, sa, err, stream);
+  probe.in[0] = lamT;
+  probe.adjoint = diffusion;
+  const bool tma = tma_supported(probe);
+  int blocks_used = 0;
+  const void* lam = lamT;
+  int64_t m = 0;  // adjoint steps done
+  for (int64_t i = L.nseg - 1; i >= 0; --i) {
+    const int64_t s0 = i * K, len = std::min<int64_t>(K, nsteps - s0);
+    const void* ck = i == 0 ? u0 : static_cast<const void*>(ws + L.off_ckpt + size_t(i - 1) * L.field);
+    // recompute u_{s0+1} .. u_{s0+len-1}
+    const void* prev = ck;
+    for (int64_t j = 1; j < len; ++j) {
+      void* dst = ws + L.off_seg + size_t(j - 1) * L.field;
+      const void* in1[1] = {prev};
+      void* out1[1] = {dst};
+      lope_launch cfg = {0, 0, 0, 0, -1};
+      lope_status rs = apply_impl(grid, st, in1, out1, nullptr, 1, &cfg, stream);
+      if (rs != LOPE_OK) return rs;
+      prev = dst;
+    }
+    for (int64_t j = len - 1; j >= 0; --j, ++m) {
+      const void* ut = j == 0 ? ck : static_cast<const void*>(ws + L.off_seg + size_t(j - 1) * L.field);
+      void* dst = (m == nsteps - 1) ? grad_u0
+                                    : static_cast<void*>(ws + L.off_lam + size_t(m & 1) * L.field);
+      StepArgs a = base_args(ga, sa, err, stream);
+      a.in[0] = lam;
+      a.out[0] = dst;
+      a.adjoint = diffusion;
+      a.ut = ut;
+      a.partials = partials;
+      a.partial_count = L.partials;
+      int b = 0;
+      e = tma ? launch_tma(a, &b) : launch_direct(a, &b);
+      if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
+      blocks_used = std::max(blocks_used, b);
+      lam = dst;
+    }
+  }
+  if (gc) {
+    if (diffusion) {
+      e = launch_finalize(partials, std::max(blocks_used, 1), gc, 0, stream);
+    } else {
+      e = cudaMemsetAsync(gc, 0, sizeof(double), stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "finalize dL/dc");
+  }
+  return LOPE_OK;
+}
+
+// ------------------------------------------------------------------ batch
+struct BatchPlan {
+  std::vector<BatchGrid> host;
+  BatchGrid* pinned = nullptr;
+  BatchPlanDev dev;
+  cudaGraphExec_t exec = nullptr;
+  int blocks = 0;
+  ~BatchPlan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (pinned) cudaFreeHost(pinned);
+  }
+};
+std::mutex g_batch_mu;
+std::map<std::vector<int64_t>, std::shared_ptr<BatchPlan>> g_batch;
+
+size_t batch_ws_bytes(int n) { return 256 + (size_t(n) * sizeof(BatchGrid) + 255) / 256 * 256; }
+
+}  // namespace
+
+void count_launches(int64_t n) {
+  if (!g_capturing) g_launches.fetch_add(n);
+}
+
+}  // namespace lope
+
+using namespace lope;
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* lope_last_error(void) { return g_last_error.c_str(); }
+const char* lope_version(void) { return "lope-gb300 0.1 (sm_103a)"; }
+int64_t lope_launch_count(void) { return g_launches.load(); }
+
+lope_status lope_grid_create(lope_grid** grid, int ndim, const int64_t* extents, const int* halo_lo,
+                             const int* halo_hi, lope_dtype storage, int nfields) {
+  if (!grid || !extents || !halo_lo || !halo_hi) return fail(LOPE_ERR_INVALID, "NULL argument");
+  if (ndim != 2 && ndim != 3) return fail(LOPE_ERR_INVALID, "ndim must be 2 or 3");
+  if (storage != LOPE_F64 && storage != LOPE_F32 && storage != LOPE_BF16)
+    return fail(LOPE_ERR_INVALID, "unknown dtype");
+  if (nfields < 1 || nfields > kMaxFields) return fail(LOPE_ERR_INVALID, "nfields must be 1..3");
+  auto* h = new (std::nothrow) lope_grid;
+  if (!h) return fail(LOPE_ERR_ALLOC, "out of host memory");
+  std::memset(h, 0, sizeof(*h));
+  h->g.ndim = ndim;
+  h->g.dtype = storage;
+  h->g.nf = nfields;
+  const int off = 3 - ndim;
+  for (int ax = 0; ax < 3; ++ax) h->g.n[ax] = 1;
+  for (int i = 0; i < ndim; ++i) {
+    if (extents[i] < 1 || extents[i] > (int64_t(1) << 31) || halo_lo[i] < 0 || halo_hi[i] < 0 ||
+        halo_lo[i] > 4 || halo_hi[i] > 4) {
+      delete h;
+      return fail(LOPE_ERR_INVALID, "extent or halo out of range");
+    }
+    h->g.n[off + i] = extents[i];
+    h->halo_lo[off + i] = halo_lo[i];
+    h->halo_hi[off + i] = halo_hi[i];
+  }
+  if (h->g.n[0] * h->g.n[1] * h->g.n[2] > (int64_t(1) << 34)) {
+    delete h;
+    return fail(LOPE_ERR_INVALID, "grid too large");
+  }
+  *grid = h;
+  return LOPE_OK;
+}
+
+void lope_grid_destroy(lope_grid* grid) { delete grid; }
+
+lope_status lope_set_boundary(lope_grid* grid, int axis, int side, lope_bc kind, double value) {
+  if (!grid) return fail(LOPE_ERR_INVALID, "NULL grid");
+  const int nd = grid->g.ndim;
+  if (axis < -1 || axis >= nd || side < -1 || side > 1) return fail(LOPE_ERR_INVALID, "bad axis or side");
+  if (kind != LOPE_BC_PERIODIC && kind != LOPE_BC_DIRICHLET) return fail(LOPE_ERR_INVALID, "bad boundary kind");
+  if (kind == LOPE_BC_PERIODIC && side != -1) return fail(LOPE_ERR_INVALID, "periodic applies to both sides");
+  if (!std::isfinite(value)) return fail(LOPE_ERR_INVALID, "non-finite Dirichlet value");
+  const int off = 3 - nd;
+  for (int a = 0; a < nd; ++a) {
+    if (axis != -1 && a != axis) continue;
+    for (int sd = 0; sd < 2; ++sd) {
+      if (side != -1 && sd != side) continue;
+      grid->g.bc[off + a][sd] = kind == LOPE_BC_PERIODIC ? kPeriodic : kDirichlet;
+      grid->g.bval[off + a][sd] = kind == LOPE_BC_PERIODIC ? 0.0 : value;
+    }
+    // an axis cannot be periodic on one side only
+    if (grid->g.bc[off + a][0] != grid->g.bc[off + a][1]) {
+      grid->g.bc[off + a][0] = grid->g.bc[off + a][1] = kDirichlet;
+    }
+  }
+  return LOPE_OK;
+}
+
+lope_status lope_stencil_create_builtin(lope_stencil** stencil, const char* name,
+                                        const double* params, int nparams) {
+  if (!stencil || !name) return fail(LOPE_ERR_INVALID, "NULL argument");
+  auto* h = new (std::nothrow) lope_stencil;
+  if (!h) return fail(LOPE_ERR_ALLOC, "out of host memory");
+  std::memset(h, 0, sizeof(*h));
+  StencilDesc& s = h->s;
+  s.star = true;
+  std::string n(name);
+  int want = 1;
+  if (n == "jacobi5") { s.kind = kJacobi5; s.ndim = 2; s.radius = 1; }
+  else if (n == "diff7") { s.kind = kDiff7; s.ndim = 3; s.radius = 1; }
+  else if (n == "star9r2") { s.kind = kStar9r2; s.ndim = 2; s.radius = 2; }
+  else if (n == "swe_cgrid") { s.kind = kSwe; s.ndim = 2; s.radius = 1; want = 3; }
+  else { delete h; return fail(LOPE_ERR_INVALID, "unknown builtin stencil name"); }
+  if (nparams != want || !params) { delete h; return fail(LOPE_ERR_INVALID, "wrong parameter count"); }
+  for (int i = 0; i < want; ++i) {
+    if (!std::isfinite(params[i])) { delete h; return fail(LOPE_ERR_INVALID, "non-finite parameter"); }
+    s.prm[i] = params[i];
+  }
+  h->nf = stencil_nf(s);
+  *stencil = h;
+  return LOPE_OK;
+}
+
+lope_status lope_stencil_create_linear(lope_stencil** stencil, int ndim, int radius,
+                                       const double* weights) {
+  if (!stencil || !weights) return fail(LOPE_ERR_INVALID, "NULL argument");
+  if ((ndim != 2 && ndim != 3) || radius < 1 || radius > kMaxRadius)
+    return fail(LOPE_ERR_INVALID, "ndim must be 2/3 and radius 1..2");
+  auto* h = new (std::nothrow) lope_stencil;
+  if (!h) return fail(LOPE_ERR_ALLOC, "out of host memory");
+  std::memset(h, 0, sizeof(*h));
+  StencilDesc& s = h->s;
+  s.kind = kLinear;
+  s.ndim = ndim;
+  s.radius = radius;
+  const int side = 2 * radius + 1, zs = ndim == 3 ? side : 1, zr = ndim == 3 ? radius : 0;
+  bool star = true;
+  for (int dz = 0; dz < zs; ++dz)
+    for (int dy = 0; dy < side; ++dy)
+      for (int dx = 0; dx < side; ++dx) {
+        const double w = weights[(dz * side + dy) * side + dx];
+        if (!std::isfinite(w)) { delete h; return fail(LOPE_ERR_INVALID, "non-finite weight"); }
+        s.box[(dz * side + dy) * side + dx] = w;
+        const int ox = dx - radius, oy = dy - radius, oz = dz - zr;
+        const int nz = (ox != 0) + (oy != 0) + (oz != 0);
+        if (nz > 1 && w != 0.0) star = false;
+        if (nz == 0) s.star_w[0][radius] = w;
+        else if (ox != 0 && nz == 1) s.star_w[0][ox + radius] = w;
+        else if (oy != 0 && nz == 1) s.star_w[1][oy + radius] = w;
+        else if (oz != 0 && nz == 1) s.star_w[2][oz + radius] = w;
+      }
+  s.star = star;
+  h->nf = 1;
+  *stencil = h;
+  return LOPE_OK;
+}
+
+void lope_stencil_destroy(lope_stencil* stencil) { delete stencil; }
+
+lope_status lope_apply(const lope_grid* grid, const lope_stencil* stencil, const void* const* in,
+                       void* const* out, void* const* work, int64_t nsteps, void* cuda_stream) {
+  return apply_impl(grid, stencil, in, out, work, nsteps, nullptr,
+                    static_cast<cudaStream_t>(cuda_stream));
+}
+
+lope_status lope_apply_with(const lope_grid* grid, const lope_stencil* stencil,
+                            const void* const* in, void* const* out, void* const* work,
+                            int64_t nsteps, const lope_launch* cfg, void* cuda_stream) {
+  return apply_impl(grid, stencil, in, out, work, nsteps, cfg,
+                    static_cast<cudaStream_t>(cuda_stream));
+}
+
+lope_status lope_autotune(const lope_grid* grid, const lope_stencil* stencil,
+                          const void* const* in, void* const* out, void* const* work,
+                          int64_t nsteps, lope_launch* best, double* best_ms, void* cuda_stream) {
+  lope_status rs = check_pair(grid, stencil);
+  if (rs != LOPE_OK) return rs;
+  if (nsteps < 1) return fail(LOPE_ERR_INVALID, "autotune needs nsteps >= 1");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const Geom& g = grid->g;
+  std::vector<lope_launch> cands;
+  cands.push_back({kPathTma, 0, 0, 1, -1});
+  if (g.ndim == 2) {
+    const int tiles[][2] = {{64, 32}, {128, 16}, {64, 16}, {32, 32}, {128, 32}};
+    for (auto& t : tiles)
+      for (int k : {1, 2, 3, 4, 6, 8}) cands.push_back({kPathTrap, t[0], t[1], k, -1});
+  }
+  cands.push_back({kPathDirect, 0, 0, 1, -1});
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double bms = 1e300;
+  lope_launch bl = {0, 0, 0, 0, 0};
+  for (const auto& c : cands) {
+    if (apply_impl(grid, stencil, in, out, work, nsteps, &c, st) != LOPE_OK) continue;  // warm-up / support check
+    cudaEventRecord(e0, st);
+    rs = apply_impl(grid, stencil, in, out, work, nsteps, &c, st);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || rs != LOPE_OK) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < bms) {
+      bms = ms;
+      bl = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g_last_error = "no error";
+  if (bl.path == 0) return fail(LOPE_ERR_UNSUPPORTED, "no launch path supports this grid/stencil");
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(g, stencil->s)] = {bl.path, bl.tile_x, bl.tile_y, bl.tsteps > 0 ? bl.tsteps : 1};
+  }
+  if (best) *best = bl;
+  if (best_ms) *best_ms = bms;
+  return LOPE_OK;
+}
+
+lope_status lope_batch_workspace_size(int n, const lope_grid* const* grids,
+                                      const lope_stencil* stencil, const lope_launch* cfg,
+                                      size_t* bytes) {
+  (void)cfg;
+  if (n < 1 || !grids || !stencil || !bytes) return fail(LOPE_ERR_INVALID, "bad argument");
+  *bytes = batch_ws_bytes(n);
+  return LOPE_OK;
+}
+
+lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_stencil* stencil,
+                             const void* const* in, void* const* out, void* const* work,
+                             int64_t nsteps, const lope_launch* cfg, void* workspace,
+                             size_t workspace_bytes, void* cuda_stream) {
+  if (n < 1 || !grids || !stencil || !in || !out || !workspace)
+    return fail(LOPE_ERR_INVALID, "NULL argument");
+  if (nsteps < 1) return fail(LOPE_ERR_INVALID, "nsteps must be >= 1");
+  if (workspace_bytes < batch_ws_bytes(n)) return fail(LOPE_ERR_ALLOC, "batch workspace too small");
+  if (!aligned16(workspace)) return fail(LOPE_ERR_INVALID, "workspace not 16-byte aligned");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const StencilDesc& s = stencil->s;
+  const int dtype = grids[0]->g.dtype;
+  for (int i = 0; i < n; ++i) {
+    lope_status rs = check_pair(grids[i], stencil);
+    if (rs != LOPE_OK) return rs;
+    if (grids[i]->g.ndim != 2 || grids[i]->g.nf != 1 || grids[i]->g.dtype != dtype)
+      return fail(LOPE_ERR_INVALID, "batch grids must be 2D, single-field, same dtype");
+    const void* in1[1] = {in[i]};
+    void* out1[1] = {out[i]};
+    void* work1[1] = {work ? work[i] : nullptr};
+    if ((rs = check_fields(grids[i]->g, in1, out1, work1, true)) != LOPE_OK) return rs;
+  }
+  const int tx = cfg && cfg->tile_x > 0 ? cfg->tile_x : 64;
+  const int ty = cfg && cfg->tile_y > 0 ? cfg->tile_y : 32;
+  const int k = cfg && cfg->tsteps > 0 ? cfg->tsteps : 4;
+  if (tx < 8 || tx > 256 || ty < 1 || ty > 256 || k < 1 || k > 8)
+    return fail(LOPE_ERR_INVALID, "bad batch tile or depth");
+  DevState* d = nullptr;
+  lope_status rs = dev_state(&d);
+  if (rs != LOPE_OK) return rs;
+  const int maxb = batch_max_blocks(s, dtype, tx, ty, k);
+  if (maxb <= 0) return fail(LOPE_ERR_UNSUPPORTED, "batched kernel does not support this stencil/tile");
+
+  const int64_t wait_ms = g_wait_limit_ms.load(), skip = g_skip_arrive.load();
+  std::vector<int64_t> key = {int64_t(n), int64_t(dtype), s.kind, tx, ty, k, nsteps,
+                              int64_t(reinterpret_cast<uintptr_t>(workspace)), wait_ms, skip};
+  const int64_t* sw = reinterpret_cast<const int64_t*>(&s);
+  key.insert(key.end(), sw, sw + sizeof(StencilDesc) / 8);
+  for (int i = 0; i < n; ++i) {
+    const Geom& g = grids[i]->g;
+    key.insert(key.end(), {g.n[1], g.n[2], int64_t(reinterpret_cast<uintptr_t>(in[i])),
+                           int64_t(reinterpret_cast<uintptr_t>(out[i])),
+                           int64_t(reinterpret_cast<uintptr_t>(work[i]))});
+    for (int ax = 1; ax < 3; ++ax)
+      for (int sd = 0; sd < 2; ++sd) {
+        key.push_back(g.bc[ax][sd]);
+        int64_t b;
+        std::memcpy(&b, &g.bval[ax][sd], 8);
+        key.push_back(b);
+      }
+  }
+  std::shared_ptr<BatchPlan> plan;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    auto it = g_batch.find(key);
+    if (it != g_batch.end()) plan = it->second;
+  }
+  if (!plan) {
+    plan = std::make_shared<BatchPlan>();
+    int items = 0;
+    plan->host.resize(n);
+    for (int i = 0; i < n; ++i) {
+      const Geom& g = grids[i]->g;
+      BatchGrid& b = plan->host[i];
+      b.in = in[i];
+      b.out = out[i];
+      b.work = work[i];
+      b.nx = int(g.n[2]);
+      b.ny = int(g.n[1]);
+      for (int sd = 0; sd < 2; ++sd) {
+        b.bc[0][sd] = g.bc[1][sd];
+        b.bval[0][sd] = g.bval[1][sd];
+        b.bc[1][sd] = g.bc[2][sd];
+        b.bval[1][sd] = g.bval[2][sd];
+      }
+      b.tiles_x = (b.nx + tx - 1) / tx;
+      b.first_item = items;
+      items += b.tiles_x * ((b.ny + ty - 1) / ty);
+    }
+    cudaError_t e = cudaMallocHost(&plan->pinned, sizeof(BatchGrid) * n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    std::memcpy(plan->pinned, plan->host.data(), sizeof(BatchGrid) * n);
+    char* ws = static_cast<char*>(workspace);
+    plan->dev.grids = reinterpret_cast<const BatchGrid*>(ws + 256);
+    plan->dev.ngrids = n;
+    plan->dev.nitems = items;
+    plan->dev.tile_x = tx;
+    plan->dev.tile_y = ty;
+    plan->dev.ksteps = k;
+    plan->dev.nsteps = nsteps;
+    plan->dev.barrier = reinterpret_cast<unsigned int*>(ws);
+    plan->dev.err = d->err;
+    plan->dev.wait_ns = (unsigned long long)wait_ms * 1000000ull;
+    plan->dev.skip_block = int(skip);
+    plan->blocks = std::min(items, maxb);
+    // Capture: descriptor upload, barrier reset, persistent kernel.
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(d->capture, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    g_capturing = true;
+    cudaError_t e1 = cudaMemcpyAsync(ws + 256, plan->pinned, sizeof(BatchGrid) * n,
+                                     cudaMemcpyHostToDevice, d->capture);
+    cudaError_t e2 = cudaMemsetAsync(ws, 0, 256, d->capture);
+    cudaError_t e3 = launch_batch(plan->dev, s, dtype, plan->blocks, d->capture);
+    g_capturing = false;
+    e = cudaStreamEndCapture(d->capture, &graph);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(e3 != cudaSuccess ? e3 : e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e,
+                       "capturing the batched launch");
+    }
+    e = cudaGraphInstantiate(&plan->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(batch)");
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    if (g_batch.size() > 64) g_batch.clear();
+    g_batch[key] = plan;
+  }
+  cudaError_t e = cudaGraphLaunch(plan->exec, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch(batch)");
+  count_launches(1);
+  return LOPE_OK;
+}
+
+lope_status lope_workspace_size(const lope_grid* grid, const lope_stencil* stencil, int64_t nsteps,
+                                int64_t checkpoint_every, size_t* bytes) {
+  lope_status rs = check_linear_for_adjoint(grid, stencil);
+  if (rs != LOPE_OK) return rs;
+  if (nsteps < 1 || checkpoint_every < 1 || !bytes) return fail(LOPE_ERR_INVALID, "bad argument");
+  *bytes = adj_layout(grid->g, nsteps, checkpoint_every).total;
+  return LOPE_OK;
+}
+
+lope_status lope_forward_ckpt(const lope_grid* grid, const lope_stencil* stencil, const void* u0,
+                              void* uT, int64_t nsteps, int64_t checkpoint_every, void* workspace,
+                              size_t workspace_bytes, void* cuda_stream) {
+  lope_status rs = check_linear_for_adjoint(grid, stencil);
+  if (rs != LOPE_OK) return rs;
+  if (nsteps < 1 || checkpoint_every < 1) return fail(LOPE_ERR_INVALID, "bad step counts");
+  if (!u0 || !uT || !workspace || !aligned16(workspace)) return fail(LOPE_ERR_INVALID, "bad pointer");
+  const AdjLayout L = adj_layout(grid->g, nsteps, checkpoint_every);
+  if (workspace_bytes < L.total) return fail(LOPE_ERR_ALLOC, "workspace too small");
+  return forward_ckpt_impl(grid, stencil, u0, uT, nsteps, checkpoint_every,
+                           static_cast<char*>(workspace), L, static_cast<cudaStream_t>(cuda_stream));
+}
+
+lope_status lope_vjp(const lope_grid* grid, const lope_stencil* stencil, const void* u0,
+                     const void* grad_uT, int64_t nsteps, int64_t checkpoint_every,
+                     int reuse_checkpoints, void* grad_u0, double* grad_coeff_dev, void* workspace,
+                     size_t workspace_bytes, void* cuda_stream) {
+  lope_status rs = check_linear_for_adjoint(grid, stencil);
+  if (rs != LOPE_OK) return rs;
+  if (nsteps < 1 || checkpoint_every < 1) return fail(LOPE_ERR_INVALID, "bad step counts");
+  if (!u0 || !grad_uT || !grad_u0 || !workspace || !aligned16(workspace) || !aligned16(grad_u0) ||
+      !aligned16(grad_uT))
+    return fail(LOPE_ERR_INVALID, "bad pointer");
+  const AdjLayout L = adj_layout(grid->g, nsteps, checkpoint_every);
+  if (workspace_bytes < L.total) return fail(LOPE_ERR_ALLOC, "workspace too small");
+  DevState* d = nullptr;
+  if ((rs = dev_state(&d)) != LOPE_OK) return rs;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  char* ws = static_cast<char*>(workspace);
+  if (!reuse_checkpoints) {
+    // u_T itself is not needed; it lands in the last checkpoint slot.
+    void* uT = ws + L.off_ckpt + size_t(L.nseg - 1) * L.field;
+    if ((rs = forward_ckpt_impl(grid, stencil, u0, uT, nsteps, checkpoint_every, ws, L, st)) != LOPE_OK)
+      return rs;
+  }
+  return reverse_impl(grid, stencil, u0, grad_uT, nsteps, checkpoint_every, grad_u0,
+                      grad_coeff_dev, ws, L, d->err, st);
+}
+
+lope_status lope_adjoint(const lope_grid* grid, const lope_stencil* stencil, const void* u0,
+                         const void* target, int64_t nsteps, int64_t checkpoint_every,
+                         void* grad_u0, double* grad_coeff, double* loss, void* workspace,
+                         size_t workspace_bytes, void* cuda_stream) {
+  lope_status rs = check_linear_for_adjoint(grid, stencil);
+  if (rs != LOPE_OK) return rs;
+  if (nsteps < 1 || checkpoint_every < 1) return fail(LOPE_ERR_INVALID, "bad step counts");
+  if (!u0 || !target || !grad_u0 || !workspace || !aligned16(workspace) || !aligned16(grad_u0))
+    return fail(LOPE_ERR_INVALID, "bad pointer");
+  const AdjLayout L = adj_layout(grid->g, nsteps, checkpoint_every);
+  if (workspace_bytes < L.total) return fail(LOPE_ERR_ALLOC, "workspace too small");
+  DevState* d = nullptr;
+  if ((rs = dev_state(&d)) != LOPE_OK) return rs;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  char* ws = static_cast<char*>(workspace);
+  void* uT = ws + L.off_ckpt + size_t(L.nseg - 1) * L.field;
+  if ((rs = forward_ckpt_impl(grid, stencil, u0, uT, nsteps, checkpoint_every, ws, L, st)) != LOPE_OK)
+    return rs;
+  double* scal = reinterpret_cast<double*>(ws + L.off_scal);
+  double* partials = reinterpret_cast<double*>(ws + L.off_part);
+  void* lamT = ws + L.off_tmp;  // the forward work buffer is free now
+  cudaError_t e = launch_loss_seed(grid->g.dtype, uT, target, lamT, npts(grid->g), partials, &scal[0], st);
+  if (e != cudaSuccess) return cuda_fail(e, "loss kernel");
+  if ((rs = reverse_impl(grid, stencil, u0, lamT, nsteps, checkpoint_every, grad_u0, &scal[1], ws, L,
+                         d->err, st)) != LOPE_OK)
+    return rs;
+  double host[2] = {0.0, 0.0};
+  e = cudaMemcpyAsync(host, scal, sizeof(host), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "reading loss and dL/dc");
+  if (loss) *loss = host[0];
+  if (grad_coeff) *grad_coeff = host[1];
+  if (!std::isfinite(host[0]) || !std::isfinite(host[1]))
+    return fail(LOPE_ERR_NUMERIC, "non-finite loss or dL/dc");
+  return LOPE_OK;
+}
+
+size_t lope_reduce_scratch_bytes(void) { return size_t(kReduceBlocks) * sizeof(double); }
+
+lope_status lope_reduce(int op, lope_dtype dtype, const void* x, const void* y, int64_t n,
+                        double* result_dev, void* scratch, void* cuda_stream) {
+  if ((op != 0 && op != 1) || !x || (op == 1 && !y) || !result_dev || !scratch || n < 0)
+    return fail(LOPE_ERR_INVALID, "bad reduction argument");
+  if (dtype != LOPE_F64 && dtype != LOPE_F32 && dtype != LOPE_BF16)
+    return fail(LOPE_ERR_INVALID, "unknown dtype");
+  cudaError_t e = launch_reduce(op, dtype, x, y, n, static_cast<double*>(scratch), result_dev,
+                                static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(e, "reduction kernel");
+  return LOPE_OK;
+}
+
+lope_status lope_set_option(const char* name, int64_t value) {
+  if (!name) return fail(LOPE_ERR_INVALID, "NULL option name");
+  const std::string n(name);
+  if (n == "wait_limit_ms") {
+    if (value < 1 || value > 600000) return fail(LOPE_ERR_INVALID, "wait_limit_ms out of range");
+    g_wait_limit_ms = value;
+    return LOPE_OK;
+  }
+  if (n == "batch_skip_arrive") {
+    if (value < -1 || value > (int64_t(1) << 30)) return fail(LOPE_ERR_INVALID, "bad block index");
+    g_skip_arrive = value;
+    return LOPE_OK;
+  }
+  return fail(LOPE_ERR_INVALID, "unknown option");
+}
+
+lope_status lope_sync_status(void* cuda_stream) {
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  DevState* d = nullptr;
+  lope_status rs = dev_state(&d);
+  if (rs != LOPE_OK) return rs;
+  int flag = 0;
+  e = cudaMemcpy(&flag, d->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device error flag");
+  if (flag) {
+    cudaMemset(d->err, 0, sizeof(int));
+    return fail(LOPE_ERR_TIMEOUT, "a bounded in-kernel wait gave up");
+  }
+  return LOPE_OK;
+}
+
+}  // extern "C"

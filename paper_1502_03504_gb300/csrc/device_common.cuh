@@ -1,0 +1,280 @@
+// Device-side building blocks shared by the LOPe kernels: storage/compute
+// types, explicitly rounded arithmetic, mbarrier and TMA wrappers (inline PTX
+// for sm_103a), bounded waits, and the local functions themselves.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lope_internal.h"
+
+namespace lope {
+
+// ---------------------------------------------------------------- types
+template <class T> struct Compute { using type = float; };
+template <> struct Compute<double> { using type = double; };
+template <class T> using C_t = typename Compute<T>::type;
+
+__device__ __forceinline__ double to_c(double v) { return v; }
+__device__ __forceinline__ float to_c(float v) { return v; }
+__device__ __forceinline__ float to_c(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <class T> __device__ __forceinline__ T from_c(C_t<T> v);
+template <> __device__ __forceinline__ double from_c<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_c<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_c<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+// Round a compute value to what storage would hold (identity for f32/f64).
+template <class T> __device__ __forceinline__ C_t<T> to_storage_precision(C_t<T> v) {
+  return to_c(from_c<T>(v));
+}
+
+// Explicitly rounded arithmetic: every kernel variant evaluates a local
+// function with the same operations in the same order, so results are
+// bitwise identical across tilings and temporal depths.
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ---------------------------------------------------------------- timers / waits
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Record a timeout in the device error flag (first writer wins).
+__device__ __forceinline__ void raise_error(int* flag, int code) {
+  if (flag) atomicCAS(flag, 0, code);
+}
+
+// ---------------------------------------------------------------- mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the given phase parity with a time limit.  Returns false (and the
+// caller must stop) when the limit passes; nothing here traps.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  uint64_t t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && global_ns() - t0 > kWaitLimitNs) {
+      raise_error(err, kErrTimeout);
+      return false;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- TMA
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* m) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* m, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* m, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ int wrap(int q, int n) {
+  q %= n;
+  return q < 0 ? q + n : q;
+}
+
+// ---------------------------------------------------------------- local functions
+//
+// Each local function writes only its own element(s) and reads U(f,dx,dy,dz)
+// through an accessor that hides where the halo values come from (shared
+// memory tile, register queue, global memory with boundary logic).  This is
+// the LOPe contract (Sec. 2.2, Fig. 1): the function never sees where its
+// element sits in the grid.  The `red` argument is an FP64 accumulator used
+// only by the adjoint functions.
+
+struct OpJacobi5 {  // Fig. 1 with a coefficient: u + c (E + W + N + S - 4u)
+  static constexpr int NDIM = 2, R = 1, NF = 1;
+  static constexpr bool REDUCES = false, STAR = true;
+  double c;
+  template <class C, class A>
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], double&) const {
+    C u = U(0, 0, 0, 0);
+    C nb = add(add(U(0, -1, 0, 0), U(0, 1, 0, 0)), add(U(0, 0, -1, 0), U(0, 0, 1, 0)));
+    o[0] = fma_(C(c), fma_(C(-4), u, nb), u);
+  }
+};
+
+struct OpDiff7 {  // u + c (sum of the six face neighbours - 6u)
+  static constexpr int NDIM = 3, R = 1, NF = 1;
+  static constexpr bool REDUCES = false, STAR = true;
+  double c;
+  template <class C, class A>
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], double&) const {
+    C u = U(0, 0, 0, 0);
+    C nb = add(add(add(U(0, -1, 0, 0), U(0, 1, 0, 0)), add(U(0, 0, -1, 0), U(0, 0, 1, 0))),
+               add(U(0, 0, 0, -1), U(0, 0, 0, 1)));
+    o[0] = fma_(C(c), fma_(C(-6), u, nb), u);
+  }
+};
+
+struct OpStar9r2 {  // u + c (L4x u + L4y u), L4 = (-1/12, 4/3, -5/2, 4/3, -1/12)
+  static constexpr int NDIM = 2, R = 2, NF = 1;
+  static constexpr bool REDUCES = false, STAR = true;
+  double c;
+  template <class C, class A>
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], double&) const {
+    C u = U(0, 0, 0, 0);
+    C s1 = add(add(U(0, -1, 0, 0), U(0, 1, 0, 0)), add(U(0, 0, -1, 0), U(0, 0, 1, 0)));
+    C s2 = add(add(U(0, -2, 0, 0), U(0, 2, 0, 0)), add(U(0, 0, -2, 0), U(0, 0, 2, 0)));
+    C lap = fma_(C(4.0 / 3.0), s1, fma_(C(-1.0 / 12.0), s2, mul(C(-5), u)));
+    o[0] = fma_(C(c), lap, u);
+  }
+};
+
+// Linearised shallow water on an Arakawa C-grid (fields h, u, v): h at cell
+// centres, u on east faces, v on north faces; forward Euler.
+struct OpSwe {
+  static constexpr int NDIM = 2, R = 1, NF = 3;
+  static constexpr bool REDUCES = false, STAR = true;
+  double dtH, dtg;
+  template <class C, class A>
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[3], double&) const {
+    C h = U(0, 0, 0, 0), u = U(1, 0, 0, 0), v = U(2, 0, 0, 0);
+    C div = add(sub(u, U(1, -1, 0, 0)), sub(v, U(2, 0, -1, 0)));
+    o[0] = fma_(C(-dtH), div, h);
+    o[1] = fma_(C(-dtg), sub(U(0, 1, 0, 0), h), u);
+    o[2] = fma_(C(-dtg), sub(U(0, 0, 1, 0), h), v);
+  }
+};
+
+// General linear star stencil: w[axis][d + R], axis 0 = x (fastest), 1 = y,
+// 2 = z; the centre weight sits in w[0][R] only.
+template <int ND, int RR>
+struct OpStarLinear {
+  static constexpr int NDIM = ND, R = RR, NF = 1;
+  static constexpr bool REDUCES = false, STAR = true;
+  double w[3][2 * RR + 1];
+  template <class C, class A>
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], double&) const {
+    C s = mul(C(w[0][RR]), U(0, 0, 0, 0));
+#pragma unroll
+    for (int d = -RR; d <= RR; ++d) {
+      if (d == 0) continue;
+      s = fma_(C(w[0][d + RR]), U(0, d, 0, 0), s);
+      s = fma_(C(w[1][d + RR]), U(0, 0, d, 0), s);
+      if (ND == 3) s = fma_(C(w[2][d + RR]), U(0, 0, 0, d), s);
+    }
+    o[0] = s;
+  }
+};
+
+// General linear box stencil (corners allowed), weights slowest offset first.
+template <int ND, int RR>
+struct OpBoxLinear {
+  static constexpr int NDIM = ND, R = RR, NF = 1;
+  static constexpr bool REDUCES = false, STAR = false;
+  static constexpr int SIDE = 2 * RR + 1;
+  static constexpr int ZS = ND == 3 ? SIDE : 1;
+  double w[ZS * SIDE * SIDE];
+  template <class C, class A>
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], double&) const {
+    C s = C(0);
+    constexpr int ZR = ND == 3 ? RR : 0;
+#pragma unroll
+    for (int dz = -ZR; dz <= ZR; ++dz)
+#pragma unroll
+      for (int dy = -RR; dy <= RR; ++dy)
+#pragma unroll
+        for (int dx = -RR; dx <= RR; ++dx)
+          s = fma_(C(w[((dz + ZR) * SIDE + dy + RR) * SIDE + dx + RR]), U(0, dx, dy, dz), s);
+    o[0] = s;
+  }
+};
+
+// Adjoint step of a diffusion-form stencil u' = u + c L u, run on lambda:
+// lambda_t = lambda_{t+1} + c L^T lambda_{t+1}, with L^T the offset-reflected
+// stencil (the offset sets of these stencils are symmetric, so the reflection
+// maps each tap onto a tap of the same weight).  Accumulates
+// <L^T lambda_{t+1}, u_t> = <lambda_{t+1}, L u_t> for dL/dc; u_t is read at
+// the local element only.  Halo of lambda: zero on Dirichlet sides (A^T has no
+// constant term), wrapped on periodic ones.
+template <int KIND, class T>
+struct OpAdjDiffusion {
+  static constexpr int NDIM = KIND == kDiff7 ? 3 : 2;
+  static constexpr int R = KIND == kStar9r2 ? 2 : 1;
+  static constexpr int NF = 1;
+  static constexpr bool REDUCES = true, STAR = true;
+  double c;
+  const T* ut;
+  template <class C, class A>
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], double& red) const {
+    C l = U(0, 0, 0, 0);
+    C lt;  // (L^T lambda) at the local element
+    if (KIND == kJacobi5) {
+      C nb = add(add(U(0, 1, 0, 0), U(0, -1, 0, 0)), add(U(0, 0, 1, 0), U(0, 0, -1, 0)));
+      lt = fma_(C(-4), l, nb);
+    } else if (KIND == kDiff7) {
+      C nb = add(add(add(U(0, 1, 0, 0), U(0, -1, 0, 0)), add(U(0, 0, 1, 0), U(0, 0, -1, 0))),
+                 add(U(0, 0, 0, 1), U(0, 0, 0, -1)));
+      lt = fma_(C(-6), l, nb);
+    } else {
+      C s1 = add(add(U(0, 1, 0, 0), U(0, -1, 0, 0)), add(U(0, 0, 1, 0), U(0, 0, -1, 0)));
+      C s2 = add(add(U(0, 2, 0, 0), U(0, -2, 0, 0)), add(U(0, 0, 2, 0), U(0, 0, -2, 0)));
+      lt = fma_(C(4.0 / 3.0), s1, fma_(C(-1.0 / 12.0), s2, mul(C(-5), l)));
+    }
+    o[0] = fma_(C(c), lt, l);
+    red = __fma_rn(double(lt), double(to_c(__ldg(ut + U.gidx()))), red);
+  }
+};
+
+}  // namespace lope

@@ -1,0 +1,112 @@
+// Internal types shared by the host planner (api.cu) and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace lope {
+
+// Stencil kinds (builtin names of lope_stencil_create_builtin).
+enum : int { kLinear = 0, kJacobi5 = 1, kDiff7 = 2, kStar9r2 = 3, kSwe = 4 };
+enum : int { kF64 = 0, kF32 = 1, kBF16 = 2 };
+enum : int { kPeriodic = 0, kDirichlet = 1 };
+enum : int { kPathAuto = 0, kPathTma = 1, kPathTrap = 2, kPathDirect = 3 };
+
+// Device error codes written to the error flag.
+constexpr int kErrTimeout = 1;
+// Upper bound of any single in-kernel wait (ns).  Normal waits last
+// microseconds; this only ends a wait that can no longer succeed.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+constexpr int kMaxFields = 3;
+constexpr int kMaxRadius = 2;
+
+// A grid as the kernels see it.  Axes are stored slowest first and always as
+// three: a 2D grid has n[0] = 1.
+struct Geom {
+  int ndim;
+  int64_t n[3];
+  int bc[3][2];
+  double bval[3][2];
+  int dtype;
+  int nf;
+};
+
+struct StencilDesc {
+  int kind;
+  int ndim;
+  int radius;
+  bool star;           // only axis-aligned taps
+  double prm[4];       // c | dt, g, H
+  double box[125];     // (2r+1)^ndim weight table, slowest offset first
+  double star_w[3][2 * kMaxRadius + 1];  // per axis (0 = x, 1 = y, 2 = z), centre in [0][r]
+};
+
+// One launch: `ksteps` sweeps from in to out.
+struct StepArgs {
+  Geom g;
+  StencilDesc s;
+  const void* in[kMaxFields];
+  void* out[kMaxFields];
+  int ksteps;
+  int tile_x, tile_y;
+  bool adjoint;          // run the transposed stencil (lambda halo: Dirichlet -> 0)
+  const void* ut;        // adjoint: state u_t read at the local element
+  double* partials;      // adjoint: per-block FP64 partial sums (accumulated)
+  int partial_count;     // adjoint: number of partial slots available
+  int* err;              // device error flag
+  cudaStream_t stream;
+};
+
+// Launchers (each returns the number of blocks it used through *blocks when
+// non-NULL, so that the adjoint can size its partial-sum buffer).
+cudaError_t launch_tma(const StepArgs& a, int* blocks);
+bool tma_supported(const StepArgs& a);
+cudaError_t launch_trap2d(const StepArgs& a);
+bool trap2d_supported(const StepArgs& a);
+cudaError_t launch_direct(const StepArgs& a, int* blocks);
+bool direct_supported(const StepArgs& a);
+int tma_blocks(const StepArgs& a);
+int direct_blocks(const StepArgs& a);
+
+// Reductions (k_reduce.cu).
+constexpr int kReduceBlocks = 608;  // 4 x 152 SMs; partial sums per reduction
+cudaError_t launch_reduce(int op, int dtype, const void* x, const void* y, int64_t n,
+                          double* partials, double* result, cudaStream_t s);
+cudaError_t launch_loss_seed(int dtype, const void* uT, const void* target, void* lam, int64_t n,
+                             double* partials, double* loss, cudaStream_t s);
+cudaError_t launch_finalize(const double* partials, int count, double* result, int accumulate,
+                            cudaStream_t s);
+
+// Batched persistent kernel (k_batch.cu).
+struct BatchGrid {
+  const void* in;
+  void* out;
+  void* work;
+  int nx, ny;
+  int bc[2][2];       // [axis: 0 = y, 1 = x][side]
+  double bval[2][2];
+  int tiles_x;
+  int first_item;     // index of this grid's first tile in the global item list
+};
+struct BatchPlanDev {
+  const BatchGrid* grids;  // device
+  int ngrids;
+  int nitems;
+  int tile_x, tile_y;
+  int ksteps;
+  int64_t nsteps;
+  unsigned int* barrier;   // device counter, zeroed before each launch
+  int* err;
+  unsigned long long wait_ns;  // limit of each barrier wait
+  int skip_block;              // test hook: this block skips its first arrival (-1: none)
+};
+cudaError_t launch_batch(const BatchPlanDev& p, const StencilDesc& s, int dtype, int blocks,
+                         cudaStream_t st);
+int batch_max_blocks(const StencilDesc& s, int dtype, int tile_x, int tile_y, int ksteps);
+size_t trap_smem_bytes(int dtype, int nf, int tile_x, int tile_y, int halo);
+
+void count_launches(int64_t n);
+
+}  // namespace lope

@@ -1,0 +1,112 @@
+// Shared-memory trapezoid tile with temporal blocking, used by the per-grid
+// trapezoid kernel (k_generic.cu) and by the persistent batched kernel
+// (k_batch.cu), so both evaluate exactly the same arithmetic.
+//
+// A block stages a (TY + 2Rk) x (TX + 2Rk) window of the state, filling every
+// cell from the boundary rule (periodic wrap or Dirichlet value; Sec. 2.2
+// "Halo regions", Sec. 3.2 BC=CYCLIC), then runs k sweeps of the local
+// function inside shared memory.  Sweep s updates the window shrunk by s*R on
+// each side from the frozen result of sweep s-1 (the snapshot semantics of
+// Sec. 2.2 / Sec. 3.5), so after k sweeps the central TX x TY tile holds the
+// state k steps later.  Fusing k sweeps per pass is the "compiler fuses the
+// small functions" latitude of Sec. 3.5.  Every sweep rounds to the storage
+// precision, so the result is bitwise the same for any k and tile shape.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace lope {
+
+struct TrapGrid {
+  int nx, ny;
+  int bc[2][2];        // [0 = y axis, 1 = x axis][side]
+  double bval[2][2];
+};
+
+template <class C, int NF>
+struct TrapAcc {
+  const C* buf;  // NF planes of H x W
+  int W, HW;
+  int i, j;
+  __device__ __forceinline__ C operator()(int f, int dx, int dy, int) const {
+    return buf[f * HW + (j + dy) * W + (i + dx)];
+  }
+  __device__ __forceinline__ int64_t gidx() const { return 0; }
+};
+
+// Value of the state at global (gy, gx), which may lie outside the grid.
+template <class T>
+__device__ __forceinline__ C_t<T> halo_read(const T* src, const TrapGrid& g, int gy, int gx) {
+  using C = C_t<T>;
+  if (gy < 0 && g.bc[0][0] == kDirichlet) return C(g.bval[0][0]);
+  if (gy >= g.ny && g.bc[0][1] == kDirichlet) return C(g.bval[0][1]);
+  if (gx < 0 && g.bc[1][0] == kDirichlet) return C(g.bval[1][0]);
+  if (gx >= g.nx && g.bc[1][1] == kDirichlet) return C(g.bval[1][1]);
+  gy = wrap(gy, g.ny);
+  gx = wrap(gx, g.nx);
+  return to_c(__ldcg(src + int64_t(gy) * g.nx + gx));
+}
+
+// Dirichlet cells outside the grid keep their halo value in every sweep.
+__device__ __forceinline__ bool outside_dirichlet(const TrapGrid& g, int gy, int gx, double* v) {
+  if (gy < 0 && g.bc[0][0] == kDirichlet) { *v = g.bval[0][0]; return true; }
+  if (gy >= g.ny && g.bc[0][1] == kDirichlet) { *v = g.bval[0][1]; return true; }
+  if (gx < 0 && g.bc[1][0] == kDirichlet) { *v = g.bval[1][0]; return true; }
+  if (gx >= g.nx && g.bc[1][1] == kDirichlet) { *v = g.bval[1][1]; return true; }
+  return false;
+}
+
+// One tile: k sweeps from src to dst.  smem holds 2 * NF * H * W values of C.
+template <class Op, class T>
+__device__ __forceinline__ void trap_tile(const Op& op, const T* const* src, T* const* dst,
+                                          const TrapGrid& g, int x0, int y0, int TX, int TY,
+                                          int k, C_t<T>* smem) {
+  using C = C_t<T>;
+  constexpr int R = Op::R, NF = Op::NF;
+  const int h = R * k;
+  const int W = TX + 2 * h, H = TY + 2 * h, HW = W * H;
+  C* b0 = smem;
+  C* b1 = smem + NF * HW;
+  for (int idx = threadIdx.x; idx < HW; idx += blockDim.x) {
+    const int i = idx % W, j = idx / W;
+    const int gx = x0 - h + i, gy = y0 - h + j;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) b0[f * HW + idx] = halo_read<T>(src[f], g, gy, gx);
+  }
+  __syncthreads();
+  for (int s = 1; s <= k; ++s) {
+    const C* cur = (s & 1) ? b0 : b1;
+    C* nxt = (s & 1) ? b1 : b0;
+    const int lo = s * R, wi = W - 2 * lo, hi = H - 2 * lo;
+    for (int idx = threadIdx.x; idx < wi * hi; idx += blockDim.x) {
+      const int i = lo + idx % wi, j = lo + idx / wi;
+      const int gx = x0 - h + i, gy = y0 - h + j;
+      double v;
+      if (outside_dirichlet(g, gy, gx, &v)) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) nxt[f * HW + j * W + i] = C(v);
+        continue;
+      }
+      TrapAcc<C, NF> acc{cur, W, HW, i, j};
+      C o[NF];
+      double unused = 0.0;
+      op(acc, o, unused);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) nxt[f * HW + j * W + i] = to_storage_precision<T>(o[f]);
+    }
+    __syncthreads();
+  }
+  const C* fin = (k & 1) ? b1 : b0;
+  for (int idx = threadIdx.x; idx < TX * TY; idx += blockDim.x) {
+    const int i = idx % TX, j = idx / TX;
+    const int gx = x0 + i, gy = y0 + j;
+    if (gx < g.nx && gy < g.ny) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        dst[f][int64_t(gy) * g.nx + gx] = from_c<T>(fin[f * HW + (j + h) * W + (i + h)]);
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace lope

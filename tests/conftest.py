@@ -10,12 +10,6 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
-    config.addinivalue_line("markers", "slow: long-running CPU check")
-
-
-def pytest_collection_modifyitems(config, items):
-    # Keep the order files were collected in; tests/test_zz_* runs last by name.
-    return None
 
 
 @pytest.fixture(scope="session")
@@ -24,3 +18,15 @@ def orc():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def lope():
+    """The CUDA library, built in-tree if needed (no GPU required to build or load)."""
+    from paper_1502_03504_gb300 import build
+
+    build.build()
+    import paper_1502_03504_gb300 as L
+
+    L.load()
+    return L

@@ -1,0 +1,85 @@
+"""C ABI checks that need no GPU: the library builds, loads, exports every
+declared entry point, and rejects invalid descriptors before touching CUDA."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    with open(os.path.join(ROOT, "include", "lope.h")) as fh:
+        text = fh.read()
+    for m in re.finditer(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(lope_[a-z_0-9]+)\s*\(", text, re.M):
+        names.add(m.group(1))
+    return names
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ("lope_grid_create", "lope_set_boundary", "lope_apply", "lope_apply_batch",
+              "lope_adjoint", "lope_vjp", "lope_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lope):
+    lib = ctypes.CDLL(lope.library_path())
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_counter(lope):
+    assert "sm_103a" in lope.version()
+    assert lope.launch_count() >= 0
+
+
+def test_grid_validation(lope):
+    with pytest.raises(lope.LopeError, match="INVALID"):
+        lope.Grid((0, 8))
+    with pytest.raises(lope.LopeError, match="INVALID"):
+        lope.Grid((8, 8, 8, 8))
+    with pytest.raises(lope.LopeError, match="INVALID"):
+        lope.Grid((8, 8), halo=5)
+    g = lope.Grid((8, 8))
+    with pytest.raises(lope.LopeError, match="INVALID"):
+        g.set_boundary(axis=2)
+    with pytest.raises(lope.LopeError, match="INVALID"):
+        g.set_boundary(axis=0, side=0, kind="periodic")
+
+
+def test_stencil_validation(lope):
+    with pytest.raises(lope.LopeError, match="unknown builtin"):
+        lope.Stencil.builtin("laplace9", 0.1)
+    with pytest.raises(lope.LopeError, match="parameter count"):
+        lope.Stencil.builtin("swe_cgrid", 0.1)
+    with pytest.raises(lope.LopeError):
+        lope.Stencil.linear(np.zeros((7, 7)))
+
+
+def test_halo_bound_is_enforced_before_any_cuda_call(lope):
+    """A radius-2 local function on a halo-1 grid would read out of bounds (Sec. 3.5)."""
+    g = lope.Grid((16, 16), halo=1)
+    s = lope.Stencil.builtin("star9r2", 0.1)
+    with pytest.raises(lope.LopeError, match="halo"):
+        lope.lope_apply(g.handle, s.handle, [16], [32], None, 1, None)
+    g3 = lope.Grid((4, 4, 4), halo=1)
+    with pytest.raises(lope.LopeError, match="dimensions"):
+        lope.lope_apply(g3.handle, s.handle, [16], [32], None, 1, None)
+
+
+def test_field_count_mismatch(lope):
+    g = lope.Grid((16, 16), halo=1, nfields=1)
+    s = lope.Stencil.builtin("swe_cgrid", 0.02, 1.0, 1.0)
+    with pytest.raises(lope.LopeError, match="field"):
+        lope.lope_apply(g.handle, s.handle, [16], [32], None, 1, None)
+
+
+def test_periodic_axis_shorter_than_radius(lope):
+    g = lope.Grid((1, 16), halo=2)
+    s = lope.Stencil.builtin("star9r2", 0.1)
+    with pytest.raises(lope.LopeError, match="periodic axis"):
+        lope.lope_apply(g.handle, s.handle, [16], [32], None, 1, None)

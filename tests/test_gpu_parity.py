@@ -1,0 +1,319 @@
+"""GPU parity: the CUDA kernels (through the C ABI) against the FP64 oracle.
+
+Small cases span several tiles and a ragged tail and are compared element by
+element; the full-size workloads are compared on sampled outputs, each of
+which the oracle computes on the sub-box that can influence it (the domain of
+dependence of T steps of a radius-R stencil is R*T cells wide, so cutting the
+box further out does not change the sampled value).
+"""
+import numpy as np
+import pytest
+import torch
+
+import lope_inputs as LI
+from gpu_helpers import bound_bf16, bound_f32, normwise, sub_box, to_device, to_host
+
+pytestmark = pytest.mark.gpu
+
+TMA, TRAP, DIRECT = 1, 2, 3
+
+
+def _launch(L, path, tx=0, ty=0, k=0, graph=-1):
+    return L.Launch(path, tx, ty, k, graph)
+
+
+def _grid(L, shape, dtype, halo, bc, bval=None, nf=1):
+    g = L.Grid(shape, dtype, halo=halo, nfields=nf)
+    g.set_boundaries(bc, bval)
+    return g
+
+
+def _run(L, g, st, fields, nsteps, launch=None):
+    out = L.apply(g, st, fields, nsteps=nsteps, launch=launch)
+    torch.cuda.synchronize()
+    L.sync_status()
+    return out
+
+
+# ------------------------------------------------------------------ K1: FP64, 1e-12
+@pytest.mark.parametrize("path", [0, TMA, TRAP, DIRECT])
+def test_jacobi5_fp64_256_periodic_100(lope, orc, path):
+    shape, c, T = (256, 256), 0.2, 100
+    u0, u0s = to_device(LI.uniform_field(1000, shape), "f64")
+    g = _grid(lope, shape, "f64", 1, [0, 0])
+    st = lope.Stencil.builtin("jacobi5", c)
+    got = to_host(_run(lope, g, st, u0, T, None if path == 0 else _launch(lope, path, k=1)))
+    want = orc.apply(u0s, "jacobi5", [c], T)
+    assert normwise(got, want) <= 1e-12
+
+
+def test_jacobi5_fp64_all_paths_bitwise(lope):
+    shape, c, T = (256, 256), 0.2, 24
+    u0, _ = to_device(LI.uniform_field(1000, shape), "f64")
+    g = _grid(lope, shape, "f64", 1, [0, 0])
+    st = lope.Stencil.builtin("jacobi5", c)
+    ref = _run(lope, g, st, u0, T, _launch(lope, TMA))
+    for launch in (_launch(lope, DIRECT), _launch(lope, TRAP, 64, 32, 1), _launch(lope, TRAP, 32, 8, 3),
+                   _launch(lope, TRAP, 128, 16, 8), _launch(lope, TMA, graph=1)):
+        assert torch.equal(_run(lope, g, st, u0, T, launch), ref), launch
+
+
+# ------------------------------------------------------------------ 2D FP32, ragged tiles
+@pytest.mark.parametrize("bc,bval", [([0, 0], None), ([1, 1], None), ([1, 0], [0.0, 0.0]),
+                                     ([(1, 1), (1, 1)], [(0.5, -0.25), (1.0, 0.0)])])
+@pytest.mark.parametrize("path", [0, TRAP, DIRECT])
+def test_jacobi5_f32_ragged(lope, orc, bc, bval, path):
+    shape, c, T = (75, 200), 0.2, 17
+    u0, u0s = to_device(LI.uniform_field(1, shape), "f32")
+    g = _grid(lope, shape, "f32", 1, bc, bval)
+    st = lope.Stencil.builtin("jacobi5", c)
+    launch = None if path == 0 else _launch(lope, path, 64, 32, 3 if path == TRAP else 1)
+    got = to_host(_run(lope, g, st, u0, T, launch))
+    want = orc.apply(u0s, "jacobi5", [c], T, bc=bc, bval=bval)
+    M = max(1.0, np.max(np.abs(want)), *(abs(v) for v in np.ravel(bval or [0.0])))
+    assert np.max(np.abs(got - want)) <= bound_f32(T, M, nops=7)
+
+
+def test_star9r2_f32_periodic_ragged(lope, orc):
+    shape, c, T = (70, 136), 0.1, 12
+    u0, u0s = to_device(LI.uniform_field(2, shape), "f32")
+    g = _grid(lope, shape, "f32", 2, [0, 0])
+    st = lope.Stencil.builtin("star9r2", c)
+    want = orc.apply(u0s, "star9r2", [c], T)
+    G = abs(1 - 5 * c) + c * (4 * 4 / 3 + 4 / 12)  # ||I + cL||_inf
+    for launch in (None, _launch(lope, TRAP, 64, 16, 2), _launch(lope, DIRECT)):
+        got = to_host(_run(lope, g, st, u0, T, launch))
+        assert np.max(np.abs(got - want)) <= bound_f32(T, 1.0, nops=12, G=G)
+
+
+def test_star9r2_dirichlet_small_axes(lope, orc):
+    """Grids narrower than a tile in both axes; Dirichlet with a non-zero value."""
+    shape, c, T = (5, 12), 0.1, 6
+    u0, u0s = to_device(LI.uniform_field(3, shape), "f32")
+    g = _grid(lope, shape, "f32", 2, [1, 1], [0.3, -0.2])
+    st = lope.Stencil.builtin("star9r2", c)
+    want = orc.apply(u0s, "star9r2", [c], T, bc=[1, 1], bval=[0.3, -0.2])
+    for launch in (None, _launch(lope, TRAP, 32, 8, 4), _launch(lope, DIRECT)):
+        got = to_host(_run(lope, g, st, u0, T, launch))
+        assert np.max(np.abs(got - want)) <= bound_f32(T, 1.0, nops=12, G=3.0)
+
+
+# ------------------------------------------------------------------ 3D
+@pytest.mark.parametrize("bc", [[1, 1, 1], [0, 0, 0], [0, 1, 0], [1, 0, 1]])
+def test_diff7_f32_ragged(lope, orc, bc):
+    shape, c, T = (37, 50, 72), 0.1, 12
+    u0, u0s = to_device(LI.uniform_field(4, shape), "f32")
+    g = _grid(lope, shape, "f32", 1, bc)
+    st = lope.Stencil.builtin("diff7", c)
+    want = orc.apply(u0s, "diff7", [c], T, bc=bc)
+    ref = None
+    for launch in (None, _launch(lope, TMA), _launch(lope, DIRECT)):
+        out = _run(lope, g, st, u0, T, launch)
+        got = to_host(out)
+        assert np.max(np.abs(got - want)) <= bound_f32(T, 1.0, nops=9), launch
+        if ref is None:
+            ref = out
+        else:
+            assert torch.equal(out, ref), "TMA and direct paths differ bitwise"
+
+
+def test_diff7_fp64_periodic_1e12(lope, orc):
+    shape, c, T = (20, 33, 48), 0.1, 15
+    u0, u0s = to_device(LI.uniform_field(5, shape), "f64")
+    g = _grid(lope, shape, "f64", 1, [0, 0, 0])
+    st = lope.Stencil.builtin("diff7", c)
+    got = to_host(_run(lope, g, st, u0, T))
+    assert normwise(got, orc.apply(u0s, "diff7", [c], T)) <= 1e-12
+
+
+def test_diff7_nz_smaller_than_chunk_and_thin_grids(lope, orc):
+    for shape, bc in (((1, 8, 8), [0, 0, 0]), ((3, 4, 128), [1, 0, 0]), ((64, 2, 4), [0, 1, 0])):
+        u0, u0s = to_device(LI.uniform_field(6, shape), "f32")
+        g = _grid(lope, shape, "f32", 1, bc)
+        st = lope.Stencil.builtin("diff7", 0.1)
+        got = to_host(_run(lope, g, st, u0, 5))
+        want = orc.apply(u0s, "diff7", [0.1], 5, bc=bc)
+        assert np.max(np.abs(got - want)) <= bound_f32(5, 1.0, nops=9), shape
+
+
+# ------------------------------------------------------------------ linear stencils
+@pytest.mark.parametrize("ndim,r,box", [(2, 1, False), (2, 2, False), (3, 1, False), (2, 1, True),
+                                        (2, 2, True), (3, 1, True)])
+def test_linear_asymmetric_fp64(lope, orc, ndim, r, box):
+    side = 2 * r + 1
+    w = LI.uniform_field(50 + ndim * 10 + r, (side,) * ndim) * 0.2 - 0.1
+    if not box:  # keep axis taps only
+        mask = np.zeros_like(w)
+        ctr = (r,) * ndim
+        for ax in range(ndim):
+            for d in range(side):
+                idx = list(ctr)
+                idx[ax] = d
+                mask[tuple(idx)] = 1
+        w = w * mask
+    shape = (41, 68) if ndim == 2 else (9, 13, 36)
+    bc = [0] * ndim if r == 1 else [1] * ndim
+    u0, u0s = to_device(LI.uniform_field(7, shape), "f64")
+    g = _grid(lope, shape, "f64", r, bc)
+    st = lope.Stencil.linear(w)
+    got = to_host(_run(lope, g, st, u0, 4))
+    want = orc.apply(u0s, "linear", nsteps=4, bc=bc, weights_table=w)
+    assert normwise(got, want) <= 1e-12
+
+
+# ------------------------------------------------------------------ multi-field
+def test_swe_f32_and_bf16(lope, orc):
+    shape, T = (40, 72), 20
+    dt, gr, H = 0.02, 1.0, 1.0
+    h, u, v = LI.swe_fields(1002, shape)
+    st = lope.Stencil.builtin("swe_cgrid", dt, gr, H)
+    G = 1 + 4 * dt  # ||G||_inf of one step
+    # FP32 stores h; BF16 stores eta = h - H (perturbation storage)
+    for dtype, first in (("f32", h), ("bf16", h - H)):
+        dev, stored = zip(*(to_device(f, dtype) for f in (first, u, v)))
+        g = _grid(lope, shape, dtype, 1, [0, 0], nf=3)
+        for launch in (None, _launch(lope, TRAP, 64, 32, 2), _launch(lope, DIRECT)):
+            outs = _run(lope, g, st, list(dev), T, launch)
+            want = orc.apply(list(stored), "swe_cgrid", [dt, gr, H], T)
+            M = max(np.max(np.abs(w)) for w in want)
+            for k in range(3):
+                got = to_host(outs[k])
+                bound = bound_f32(T, M, 6, G) if dtype == "f32" else bound_bf16(T, M, 6, G)
+                assert np.max(np.abs(got - want[k])) <= bound, (dtype, k, launch)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_nsteps_zero_and_one(lope, orc):
+    shape = (9, 40)
+    u0, u0s = to_device(LI.uniform_field(8, shape), "f32")
+    g = _grid(lope, shape, "f32", 1, [0, 0])
+    st = lope.Stencil.builtin("jacobi5", 0.2)
+    out = torch.empty_like(u0)
+    lope.apply(g, st, u0, out=out, nsteps=0)
+    torch.cuda.synchronize()
+    assert torch.equal(out, u0)
+    lope.apply(g, st, u0, out=out, work=None, nsteps=1)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(to_host(out) - orc.apply(u0s, "jacobi5", [0.2], 1))) < 1e-6
+
+
+def test_degenerate_single_row_and_column(lope, orc):
+    st = lope.Stencil.builtin("jacobi5", 0.2)
+    for shape in ((1, 7), (7, 1), (1, 1)):
+        u0, u0s = to_device(LI.uniform_field(9, shape), "f32")
+        g = _grid(lope, shape, "f32", 1, [0, 0])
+        got = to_host(_run(lope, g, st, u0, 3))
+        assert np.max(np.abs(got - orc.apply(u0s, "jacobi5", [0.2], 3))) < 1e-6, shape
+
+
+def test_input_is_never_written_and_aliasing_rejected(lope):
+    shape = (64, 64)
+    u0, _ = to_device(LI.uniform_field(10, shape), "f32")
+    keep = u0.clone()
+    g = _grid(lope, shape, "f32", 1, [0, 0])
+    st = lope.Stencil.builtin("jacobi5", 0.2)
+    _run(lope, g, st, u0, 7)
+    assert torch.equal(u0, keep)
+    with pytest.raises(lope.LopeError, match="alias"):
+        lope.apply(g, st, u0, out=u0, nsteps=1)
+    with pytest.raises(lope.LopeError, match="aligned"):
+        lope.apply(g, st, u0, out=torch.empty(64 * 64 + 1, device="cuda")[1:].view(64, 64), nsteps=1)
+
+
+def test_launch_counter_counts_kernels(lope):
+    shape = (64, 64)
+    u0, _ = to_device(LI.uniform_field(11, shape), "f32")
+    g = _grid(lope, shape, "f32", 1, [0, 0])
+    st = lope.Stencil.builtin("jacobi5", 0.2)
+    before = lope.launch_count()
+    _run(lope, g, st, u0, 5, _launch(lope, TMA))
+    assert lope.launch_count() - before == 5
+    before = lope.launch_count()
+    _run(lope, g, st, u0, 8, _launch(lope, TRAP, 64, 32, 4))
+    assert lope.launch_count() - before == 2
+
+
+# ------------------------------------------------------------------ reductions
+def test_fp64_reductions(lope):
+    x64 = LI.uniform_field(12, (1000, 777))
+    y64 = LI.normal_field(13, (1000, 777))
+    for dtype in ("f32", "bf16", "f64"):
+        x, xs = to_device(x64, dtype)
+        y, ys = to_device(y64, dtype)
+        s = float(lope.reduce_sum(x).item())
+        q = float(lope.reduce_sqdiff(x, y).item())
+        assert abs(s - xs.sum()) <= 1e-9 * abs(xs.sum())
+        assert abs(q - np.sum((xs - ys) ** 2)) <= 1e-9 * q
+
+
+def test_sum_conserved_periodic_on_gpu(lope):
+    shape = (96, 160)
+    u0, _ = to_device(LI.uniform_field(14, shape), "f64")
+    g = _grid(lope, shape, "f64", 1, [0, 0])
+    st = lope.Stencil.builtin("jacobi5", 0.2)
+    out = _run(lope, g, st, u0, 50)
+    a = float(lope.reduce_sum(u0).item())
+    b = float(lope.reduce_sum(out).item())
+    assert abs(a - b) <= 1e-12 * abs(a)
+
+
+# ------------------------------------------------------------------ full-size, sampled
+def _sampled_check(lope, orc, kind, prm, shape, bc, T, R, dtype, nf_fields, got_fields, stored,
+                   points, tol_fn):
+    periodic = [b == 0 for b in bc]
+    rho = R * T + 1
+    for p in points:
+        idx, pos = sub_box(shape, p, rho, periodic)
+        sub = [s[np.ix_(*idx)] for s in stored]
+        sub_bc = []
+        for ax, n in enumerate(shape):
+            full = len(idx[ax]) == n and (not periodic[ax] or 2 * rho + 1 >= n)
+            sub_bc.append(0 if (periodic[ax] and full) else 1)
+        want = orc.apply(sub if nf_fields > 1 else sub[0], kind, prm, T, bc=sub_bc,
+                         nthreads=orc.max_threads())
+        want = want if nf_fields > 1 else [want]
+        for k in range(nf_fields):
+            w = want[k][pos]
+            gv = float(got_fields[k][p].item())
+            assert abs(gv - w) <= tol_fn(k, w), (p, k, gv, w)
+
+
+def test_full_size_diff7_512_dirichlet_50_sampled(lope, orc):
+    shape, c, T = (512, 512, 512), 0.1, 50
+    u0, u0s = to_device(LI.uniform_field(1001, shape), "f32")
+    g = _grid(lope, shape, "f32", 1, [1, 1, 1])
+    st = lope.Stencil.builtin("diff7", c)
+    out = _run(lope, g, st, u0, T)
+    pts = [(0, 0, 0), (511, 511, 511), (0, 255, 511), (256, 256, 256), (100, 3, 400), (511, 0, 7)]
+    _sampled_check(lope, orc, "diff7", [c], shape, [1, 1, 1], T, 1, "f32", 1, [out], [u0s], pts,
+                   lambda k, w: 3e-5)
+
+
+def test_full_size_star9r2_8192_periodic_50_sampled(lope, orc):
+    shape, c, T = (8192, 8192), 0.1, 50
+    u0, u0s = to_device(LI.uniform_field(1001, shape, offset=1 << 32), "f32")
+    g = _grid(lope, shape, "f32", 2, [0, 0])
+    st = lope.Stencil.builtin("star9r2", c)
+    out = _run(lope, g, st, u0, T)
+    pts = [(0, 0), (8191, 8191), (0, 4096), (4000, 8191), (1234, 5678), (8190, 1)]
+    _sampled_check(lope, orc, "star9r2", [c], shape, [0, 0], T, 2, "f32", 1, [out], [u0s], pts,
+                   lambda k, w: 2.5e-4)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_full_size_swe_4096_200_sampled(lope, orc, dtype):
+    shape, T = (4096, 4096), 200
+    dt, gr, H = 0.02, 1.0, 1.0
+    h, u, v = LI.swe_fields(1002, shape)
+    first = h if dtype == "f32" else h - H
+    dev, stored = zip(*(to_device(f, dtype) for f in (first, u, v)))
+    g = _grid(lope, shape, dtype, 1, [0, 0], nf=3)
+    st = lope.Stencil.builtin("swe_cgrid", dt, gr, H)
+    outs = _run(lope, g, st, list(dev), T)
+    G = 1 + 4 * dt
+    M = max(np.max(np.abs(s)) for s in stored) * 1.5
+    tol = (lambda k, w: bound_f32(T, M, 6, G)) if dtype == "f32" else (
+        lambda k, w: bound_bf16(T, M, 6, G))
+    pts = [(0, 0), (4095, 4095), (2048, 17), (9, 3000)]
+    _sampled_check(lope, orc, "swe_cgrid", [dt, gr, H], shape, [0, 0], T, 1, dtype, 3, outs,
+                   list(stored), pts, tol)
