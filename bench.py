@@ -199,9 +199,14 @@ def main():
     ap.add_argument("--impl", default="lope", choices=["lope", "reference"])
     ap.add_argument("--main-only", action="store_true", help="skip the extra forms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--profile", default=None,
+                    help="run one kernel workload for --steps launches and exit (for ncu): "
+                         "diff7:N, diff7p:N, star9r2:N, jacobi5:N, swe:N, swebf16:N")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
 
     import torch
 
@@ -353,6 +358,55 @@ def main():
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- profiling cases
+def run_profile(args):
+    """One workload, --warmup + --steps single-sweep launches; prints per-launch time."""
+    import torch
+
+    import lope_inputs as LI
+    import paper_1502_03504_gb300 as L
+    from paper_1502_03504_gb300 import build as B
+
+    B.build()
+    name, n = args.profile.split(":")
+    n = int(n)
+    dev = torch.device("cuda", 0)
+    if name in ("diff7", "diff7p"):
+        shape, st, halo, pts = (n, n, n), L.Stencil.builtin("diff7", C3), 1, n ** 3
+        kind, nf, dtype, bpp = ("dirichlet" if name == "diff7" else "periodic"), 1, "f32", 8
+    elif name in ("star9r2", "jacobi5"):
+        shape, halo, pts = (n, n), 2 if name == "star9r2" else 1, n * n
+        st = L.Stencil.builtin(name, 0.1 if name == "star9r2" else 0.2)
+        kind, nf, dtype, bpp = "periodic", 1, "f32", 8
+    elif name in ("swe", "swebf16"):
+        shape, halo, pts = (n, n), 1, n * n
+        st = L.Stencil.builtin("swe_cgrid", 0.02, 1.0, 1.0)
+        kind, nf = "periodic", 3
+        dtype, bpp = ("f32", 24) if name == "swe" else ("bf16", 12)
+    else:
+        raise SystemExit(f"unknown profile case {name}")
+    g = L.Grid(shape, dtype, halo=halo, nfields=nf)
+    if kind == "dirichlet":
+        g.set_boundary(kind="dirichlet", value=0.0)
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+    fields = [torch.from_numpy(LI.uniform(1001, pts, k * pts).astype(np.float32).reshape(shape))
+              .to(dev).to(tdt) for k in range(nf)]
+    outs = [torch.empty_like(f) for f in fields]
+    for _ in range(args.warmup):
+        L.apply(g, st, fields, out=outs, nsteps=1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        L.apply(g, st, fields, out=outs, nsteps=1)
+    b.record()
+    torch.cuda.synchronize()
+    L.sync_status()
+    us = a.elapsed_time(b) / args.steps * 1e3
+    print(json.dumps({"profile": args.profile, "us_per_launch": us,
+                      "alg_GBps": bpp * pts / (us * 1e-6) / 1e9}), flush=True)
 
 
 # ---------------------------------------------------------------- extra forms

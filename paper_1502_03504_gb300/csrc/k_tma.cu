@@ -40,10 +40,9 @@ template <> struct TmaCfg<double> { static constexpr int TX = 32, S2 = 4, S3 = 6
 template <> struct TmaCfg<__nv_bfloat16> { static constexpr int TX = 64, S2 = 4, S3 = 6; };
 
 template <int NF> struct TmaMaps {
-  CUtensorMap main[NF];  // box {TX, TY+2R[, 1]}
-  CUtensorMap body[NF];  // box {TX, TY[, 1]}
-  CUtensorMap row[NF];   // box {TX, 1[, 1]}
-  CUtensorMap cols[NF];  // box {CW, TY[, 1]}
+  CUtensorMap wide[NF];  // box {W, TY+2R}: tile, CW halo columns each side, R halo rows each side
+  CUtensorMap rows[NF];  // box {W, R}: R consecutive halo rows
+  CUtensorMap cols[NF];  // box {CW, TY}: one 16-byte column block of the body rows
 };
 
 template <class Op, class T> struct TmaParams {
@@ -58,104 +57,143 @@ template <class Op, class T> struct TmaParams {
   int* err;
 };
 
+// Stage layout (per field, every region 128-byte aligned, as TMA requires):
+//   wide   (TY+2R) x W box, W = TX + 2 CW, loaded at (x0-CW, y0-R): the tile,
+//          CW halo columns on each side and R halo rows above and below.
+//          Out-of-range cells arrive as zeros (the Dirichlet-0 halo).
+//   colL, colR   TY x CW slots: wrapped halo columns (periodic x edge tiles)
+//   rowLo, rowHi R x W slots: wrapped halo rows (periodic y edge tiles)
+// After a stage arrives, consumers copy the wrapped slots over the zeros they
+// replace (the periodic halo, BC=CYCLIC of Sec. 3.2); every tap is then a
+// shared load at a compile-time offset from the local element.  Star stencils
+// never read the corner cells, which stay as loaded.
 template <class T, int TX, int R, int NF> struct Layout {
   static constexpr int CW = 16 / int(sizeof(T));
-  static constexpr uint32_t MAIN_B = (kTy + 2 * R) * TX * sizeof(T);
-  static constexpr uint32_t MAIN_BA = (MAIN_B + 127) / 128 * 128;
-  static constexpr uint32_t SLOT_B = kTy * CW * sizeof(T);
-  static constexpr uint32_t SLOT_BA = (SLOT_B + 127) / 128 * 128;
-  static constexpr uint32_t FIELD_B = MAIN_BA + 2 * SLOT_BA;
+  static constexpr int W = TX + 2 * CW;
+  static constexpr uint32_t WIDE_B = (kTy + 2 * R) * W * sizeof(T);
+  static constexpr uint32_t COL_B = kTy * CW * sizeof(T);
+  static constexpr uint32_t ROW_B = R * W * sizeof(T);
+  static constexpr uint32_t A(uint32_t b) { return (b + 127) / 128 * 128; }
+  static constexpr uint32_t OFF_COLL = A(WIDE_B);
+  static constexpr uint32_t OFF_COLR = OFF_COLL + A(COL_B);
+  static constexpr uint32_t OFF_ROWLO = OFF_COLR + A(COL_B);
+  static constexpr uint32_t OFF_ROWHI = OFF_ROWLO + A(ROW_B);
+  static constexpr uint32_t FIELD_B = OFF_ROWHI + A(ROW_B);
   static constexpr uint32_t STAGE_B = NF * FIELD_B;
-  static constexpr uint32_t TX_BYTES = NF * (MAIN_B + 2 * SLOT_B);
 };
 
-// Accessor over one staged plane/tile.  (cx, cy) is the local element inside
-// the tile, already clamped into the valid region; nvx/nvy are the valid
-// extents of this (possibly ragged) tile.  In 3D, z offsets come from the
-// caller's register queue q[field][R + dz].
-template <class T, int TX, int R, int NF, int NQ>
-struct PlaneAcc {
+// Which halos of a tile wrap (periodic axes only).
+struct TileInfo {
+  int x0, y0, nvx, nvy;
+  bool xl, xr;  // left / right halo columns wrap
+  bool yl, yh;  // low / high halo rows wrap
+};
+
+template <class T, int TX, int R>
+__device__ __forceinline__ TileInfo classify(int x0, int y0, int nx, int ny, int per_x, int per_y) {
+  TileInfo t;
+  t.x0 = x0;
+  t.y0 = y0;
+  t.nvx = min(TX, nx - x0);
+  t.nvy = min(kTy, ny - y0);
+  t.xl = per_x && x0 == 0;
+  t.xr = per_x && x0 + t.nvx == nx;
+  t.yl = per_y && y0 < R;
+  t.yh = per_y && y0 + t.nvy + R > ny;
+  return t;
+}
+
+// Local-function accessor: x taps are shared loads at compile-time offsets
+// from b[f] (the local element in the wide box); y taps and the centre come
+// from the thread's column registers col[f][R + dy]; z taps (3D) from the
+// register queue q[f][R + dz].
+template <class T, int TX, int R, int NF, int NQ, int NC>
+struct StageAcc {
   using L = Layout<T, TX, R, NF>;
   using C = C_t<T>;
-  const unsigned char* stage;
-  int cx, cy, nvx, nvy;
+  const T* b[NF];
+  const C (*col)[NC];  // col[f] + r, so col[f][R + dy] is row r + dy
+  int r;
   int64_t g;
-  const C (*q)[NQ];  // NQ = 2R+1 in 3D, 1 in 2D (unused)
-
-  __device__ __forceinline__ const T* mainp(int f) const {
-    return reinterpret_cast<const T*>(stage + f * L::FIELD_B);
-  }
+  const C (*q)[NQ];
   __device__ __forceinline__ C operator()(int f, int dx, int dy, int dz) const {
     if (dz != 0) return q[f][R + dz];
-    const T* m = mainp(f);
-    if (dx != 0) {
-      int col = cx + dx;
-      if (col < 0) {
-        const T* left = reinterpret_cast<const T*>(stage + f * L::FIELD_B + L::MAIN_BA);
-        return to_c(left[cy * L::CW + L::CW + col]);
-      }
-      if (col >= nvx) {
-        const T* right =
-            reinterpret_cast<const T*>(stage + f * L::FIELD_B + L::MAIN_BA + L::SLOT_BA);
-        return to_c(right[cy * L::CW + (col - nvx)]);
-      }
-      return to_c(m[(R + cy) * TX + col]);
-    }
-    if (dy != 0) {
-      int row = cy + dy;
-      int rr = row >= nvy ? R + kTy + (row - nvy) : R + row;
-      return to_c(m[rr * TX + cx]);
-    }
-    if (NQ > 1) return q[f][R];
-    return to_c(m[(R + cy) * TX + cx]);
+    if (dx != 0) return to_c(b[f][dx]);
+    return col[f][r + R + dy];
   }
   __device__ __forceinline__ int64_t gidx() const { return g; }
 };
 
+template <int RANK>
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* m, int x, int y, int z,
+                                         uint64_t* bar) {
+  if (RANK == 2) tma_load_2d(dst, m, x, y, bar);
+  else tma_load_3d(dst, m, x, y, z, bar);
+}
+
 // Issue the copies of one tile/plane of every field into stage `st`.
 template <class T, int TX, int R, int NF, int RANK>
 __device__ __forceinline__ void issue_plane(const TmaMaps<NF>& maps, unsigned char* st,
-                                            uint64_t* bar, int x0, int y0, int nvx, int nvy,
-                                            int z, int nx, int ny, int per_x, int per_y) {
+                                            uint64_t* bar, const TileInfo& t, int z, int nx,
+                                            int ny) {
   using L = Layout<T, TX, R, NF>;
-  mbar_arrive_expect_tx(bar, L::TX_BYTES);
-  const bool yedge = per_y && (y0 < R || y0 + kTy + R > ny);
-  const int xl = per_x ? wrap(x0 - L::CW, nx) : x0 - L::CW;
-  const int xr = per_x ? wrap(x0 + nvx, nx) : x0 + nvx;
+  const uint32_t per_field = L::WIDE_B + (uint32_t(t.xl) + uint32_t(t.xr)) * L::COL_B +
+                             (uint32_t(t.yl) + uint32_t(t.yh)) * L::ROW_B;
+  mbar_arrive_expect_tx(bar, NF * per_field);
+  const int xw = t.x0 - L::CW;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    unsigned char* m = st + f * L::FIELD_B;
-    unsigned char* left = m + L::MAIN_BA;
-    unsigned char* right = left + L::SLOT_BA;
-    if (!yedge) {
-      if (RANK == 2) tma_load_2d(m, &maps.main[f], x0, y0 - R, bar);
-      else tma_load_3d(m, &maps.main[f], x0, y0 - R, z, bar);
-    } else {
-      unsigned char* body = m + R * TX * sizeof(T);
-      if (RANK == 2) tma_load_2d(body, &maps.body[f], x0, y0, bar);
-      else tma_load_3d(body, &maps.body[f], x0, y0, z, bar);
+    unsigned char* w = st + f * L::FIELD_B;
+    tma_load<RANK>(w, &maps.wide[f], xw, t.y0 - R, z, bar);
+    if (t.xl) tma_load<RANK>(w + L::OFF_COLL, &maps.cols[f], nx - L::CW, t.y0, z, bar);
+    if (t.xr) tma_load<RANK>(w + L::OFF_COLR, &maps.cols[f], 0, t.y0, z, bar);
+    if (t.yl) tma_load<RANK>(w + L::OFF_ROWLO, &maps.rows[f], xw, ny - R, z, bar);
+    if (t.yh) tma_load<RANK>(w + L::OFF_ROWHI, &maps.rows[f], xw, 0, z, bar);
+  }
+}
+
+// Copy wrapped halo slots over the zero-filled cells of the wide box, order
+// the shared-memory writes before the stage's next TMA refill, and wait until
+// every consumer warp has written its share (mbarrier `fixb`, bounded wait).
+// Returns false if the wait gave up.
+template <class T, int TX, int R, int NF, int NCONS>
+__device__ __forceinline__ bool fix_halo(unsigned char* st, const TileInfo& t, int ny,
+                                         uint64_t* fixb, uint32_t parity, int* err) {
+  using L = Layout<T, TX, R, NF>;
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
-        unsigned char* lo = m + j * TX * sizeof(T);
-        unsigned char* hi = m + (R + kTy + j) * TX * sizeof(T);
-        int ylo = wrap(y0 - R + j, ny), yhi = wrap(y0 + nvy + j, ny);
-        if (RANK == 2) {
-          tma_load_2d(lo, &maps.row[f], x0, ylo, bar);
-          tma_load_2d(hi, &maps.row[f], x0, yhi, bar);
+  for (int f = 0; f < NF; ++f) {
+    T* w = reinterpret_cast<T*>(st + f * L::FIELD_B);
+    if (t.xl || t.xr) {
+      const T* sl = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_COLL);
+      const T* sr = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_COLR);
+      for (int idx = threadIdx.x; idx < t.nvy * L::CW; idx += NCONS) {
+        const int row = idx / L::CW, c = idx % L::CW;
+        if (t.xl) w[(R + row) * L::W + c] = sl[row * L::CW + c];
+        if (t.xr) w[(R + row) * L::W + L::CW + t.nvx + c] = sr[row * L::CW + c];
+      }
+    }
+    if (t.yl || t.yh) {
+      const T* lo = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_ROWLO);
+      const T* hi = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_ROWHI);
+      for (int idx = threadIdx.x; idx < 2 * R * L::W; idx += NCONS) {
+        const int j = idx / L::W, c = idx % L::W;
+        if (j < R) {
+          // low halo row j holds global row y0 - R + j (< 0 only when y0 = 0);
+          // the low slot holds rows ny - R .. ny - 1
+          if (t.yl && t.y0 - R + j < 0) w[j * L::W + c] = lo[(t.y0 + j) * L::W + c];
         } else {
-          tma_load_3d(lo, &maps.row[f], x0, ylo, z, bar);
-          tma_load_3d(hi, &maps.row[f], x0, yhi, z, bar);
+          const int jj = j - R;  // high halo row jj holds global row y0 + nvy + jj
+          const int gy = t.y0 + t.nvy + jj;
+          // the high slot holds rows 0 .. R - 1
+          if (t.yh && gy >= ny) w[(R + t.nvy + jj) * L::W + c] = hi[(gy - ny) * L::W + c];
         }
       }
     }
-    if (RANK == 2) {
-      tma_load_2d(left, &maps.cols[f], xl, y0, bar);
-      tma_load_2d(right, &maps.cols[f], xr, y0, bar);
-    } else {
-      tma_load_3d(left, &maps.cols[f], xl, y0, z, bar);
-      tma_load_3d(right, &maps.cols[f], xr, y0, z, bar);
-    }
   }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (threadIdx.x % 32 == 0) mbar_arrive(fixb);
+  return mbar_wait_bounded(fixb, parity, err);
 }
 
 __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
@@ -178,18 +216,54 @@ __device__ __forceinline__ void block_accumulate(double v, double* partials, dou
   }
 }
 
+// kRy outputs of one column of a staged tile/plane.  col[f][i] holds the
+// column's values for tile rows cy0 - R + i, i in [0, kRy + 2R).
+template <class Op, class T, int TX, int NQ, int NC>
+__device__ __forceinline__ void column_rows(const Op& op, const unsigned char* st, T* const* out,
+                                            int64_t zoff, int nx, const TileInfo& t, int cx,
+                                            int cy0, const C_t<T> (*col)[NC],
+                                            const C_t<T> (*q)[Op::NF][NQ], double& red) {
+  using C = C_t<T>;
+  constexpr int R = Op::R, NF = Op::NF;
+  using L = Layout<T, TX, R, NF>;
+  const bool xvalid = cx < t.nvx;
+  const int64_t base = zoff + int64_t(t.y0 + cy0) * nx + t.x0 + cx;
+  const int64_t gclamp = zoff + int64_t(t.y0) * nx + t.x0;  // a valid element for clamped reads
+#pragma unroll
+  for (int r = 0; r < kRy; ++r) {
+    const bool valid = xvalid && cy0 + r < t.nvy;
+    StageAcc<T, TX, R, NF, NQ, NC> acc;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      acc.b[f] = reinterpret_cast<const T*>(st + f * L::FIELD_B) + (R + cy0 + r) * L::W + L::CW + cx;
+    acc.col = col;
+    acc.r = r;
+    acc.g = valid ? base + int64_t(r) * nx : gclamp;
+    acc.q = q ? q[r] : nullptr;
+    C o[NF];
+    double r1 = 0.0;
+    op(acc, o, r1);
+    if (valid) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) out[f][base + int64_t(r) * nx] = from_c<T>(o[f]);
+      red += r1;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ 2D tiles
 template <class Op, class T, int TX, int S>
 __global__ void __launch_bounds__(TX * (kTy / kRy) + 32)
     tma2d_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
   using C = C_t<T>;
-  constexpr int R = Op::R, NF = Op::NF;
+  constexpr int R = Op::R, NF = Op::NF, NC = kRy + 2 * R;
   using L = Layout<T, TX, R, NF>;
   constexpr int NCONS = TX * (kTy / kRy);
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = align128(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * L::STAGE_B);
   uint64_t* empty = full + S;
+  uint64_t* fixb = empty + S;
   __shared__ volatile int abort_flag;
   __shared__ double red_scratch[NCONS / 32];
 
@@ -198,6 +272,7 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32)
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NCONS / 32);
+      mbar_init(&fixb[s], NCONS / 32);
     }
     abort_flag = 0;
     fence_mbar_init();
@@ -207,12 +282,9 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32)
   if (tid >= NCONS) {  // producer warp
     if (tid == NCONS) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        tma_prefetch_desc(&maps.main[f]);
-        tma_prefetch_desc(&maps.cols[f]);
-      }
+      for (int f = 0; f < NF; ++f) tma_prefetch_desc(&maps.wide[f]);
       int i = 0;
-      for (int t = blockIdx.x; t < p.nunits; t += gridDim.x, ++i) {
+      for (int u = blockIdx.x; u < p.nunits; u += gridDim.x, ++i) {
         const int s = i % S;
         const uint32_t ph = (i / S) & 1;
         if (i >= S && !mbar_wait_bounded(&empty[s], ph ^ 1, p.err)) {
@@ -220,10 +292,9 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32)
           break;
         }
         if (abort_flag) break;
-        const int x0 = (t % p.tiles_x) * TX, y0 = (t / p.tiles_x) * kTy;
-        const int nvx = min(TX, p.nx - x0), nvy = min(kTy, p.ny - y0);
-        issue_plane<T, TX, R, NF, 2>(maps, smem + s * L::STAGE_B, &full[s], x0, y0, nvx, nvy, 0,
-                                     p.nx, p.ny, p.per_x, p.per_y);
+        const TileInfo t = classify<T, TX, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * kTy, p.nx,
+                                              p.ny, p.per_x, p.per_y);
+        issue_plane<T, TX, R, NF, 2>(maps, smem + s * L::STAGE_B, &full[s], t, 0, p.nx, p.ny);
       }
       if (abort_flag) {  // let copies already issued land before the block exits
         for (int k = max(0, i - S); k < i; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
@@ -232,39 +303,34 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32)
     return;
   }
 
-  const int cx_t = tid % TX, cy0 = (tid / TX) * kRy, lane = tid % 32;
+  const int cx = tid % TX, cy0 = (tid / TX) * kRy, lane = tid % 32;
   double red = 0.0;
+  uint32_t fixph = 0;  // bit s: phase parity of fixb[s]
   int i = 0;
-  for (int t = blockIdx.x; t < p.nunits; t += gridDim.x, ++i) {
+  for (int u = blockIdx.x; u < p.nunits; u += gridDim.x, ++i) {
     const int s = i % S;
     if (!mbar_wait_bounded(&full[s], (i / S) & 1, p.err) || abort_flag) {
       abort_flag = 1;
       break;
     }
-    const int x0 = (t % p.tiles_x) * TX, y0 = (t / p.tiles_x) * kTy;
-    const int nvx = min(TX, p.nx - x0), nvy = min(kTy, p.ny - y0);
-    PlaneAcc<T, TX, R, NF, 1> acc;
-    acc.stage = smem + s * L::STAGE_B;
-    acc.nvx = nvx;
-    acc.nvy = nvy;
-    acc.cx = min(cx_t, nvx - 1);
-    acc.q = nullptr;
-#pragma unroll
-    for (int r = 0; r < kRy; ++r) {
-      const int cy_t = cy0 + r;
-      acc.cy = min(cy_t, nvy - 1);
-      const bool valid = cx_t < nvx && cy_t < nvy;
-      const int64_t gi = int64_t(y0 + acc.cy) * p.nx + x0 + acc.cx;
-      acc.g = gi;
-      C o[NF];
-      double r1 = 0.0;
-      p.op(acc, o, r1);
-      if (valid) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) p.out[f][gi] = from_c<T>(o[f]);
-        red += r1;
+    const TileInfo t = classify<T, TX, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * kTy, p.nx, p.ny,
+                                          p.per_x, p.per_y);
+    unsigned char* st = smem + s * L::STAGE_B;
+    if (t.xl || t.xr || t.yl || t.yh) {
+      const bool fixed = fix_halo<T, TX, R, NF, NCONS>(st, t, p.ny, &fixb[s], (fixph >> s) & 1u, p.err);
+      fixph ^= 1u << s;
+      if (!fixed) {
+        abort_flag = 1;
+        break;
       }
     }
+    C col[NF][NC];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int k = 0; k < NC; ++k)
+        col[f][k] = to_c(reinterpret_cast<const T*>(st + f * L::FIELD_B)[(cy0 + k) * L::W + L::CW + cx]);
+    column_rows<Op, T, TX, 1, NC>(p.op, st, p.out, 0, p.nx, t, cx, cy0, col, nullptr, red);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
@@ -276,7 +342,7 @@ template <class Op, class T, int TX, int S>
 __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
     tma3d_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
   using C = C_t<T>;
-  constexpr int R = Op::R, NF = Op::NF, NQ = 2 * R + 1;
+  constexpr int R = Op::R, NF = Op::NF, NQ = 2 * R + 1, NC = kRy + 2 * R;
   using L = Layout<T, TX, R, NF>;
   constexpr int NCONS = TX * (kTy / kRy);
   static_assert(S >= R + 2, "ring too short for the z window");
@@ -284,14 +350,16 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
   unsigned char* smem = align128(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * L::STAGE_B);
   uint64_t* empty = full + S;
+  uint64_t* fixb = empty + S;
   __shared__ volatile int abort_flag;
   __shared__ double red_scratch[NCONS / 32];
 
   const int tid = threadIdx.x;
   const int ntiles = p.tiles_x * p.tiles_y;
   const int tile = blockIdx.x % ntiles, zc = blockIdx.x / ntiles;
-  const int x0 = (tile % p.tiles_x) * TX, y0 = (tile / p.tiles_x) * kTy;
-  const int nvx = min(TX, p.nx - x0), nvy = min(kTy, p.ny - y0);
+  const TileInfo t = classify<T, TX, R>((tile % p.tiles_x) * TX, (tile / p.tiles_x) * kTy, p.nx,
+                                        p.ny, p.per_x, p.per_y);
+  const bool fix = t.xl || t.xr || t.yl || t.yh;
   const int z0 = zc * p.zchunk, z1 = min(p.nz, z0 + p.zchunk);
   const int np = (z1 - z0) + 2 * R;  // planes staged by this block
 
@@ -299,6 +367,7 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NCONS / 32);
+      mbar_init(&fixb[s], NCONS / 32);
     }
     abort_flag = 0;
     fence_mbar_init();
@@ -309,10 +378,7 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
   if (tid >= NCONS) {  // producer warp
     if (tid == NCONS) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        tma_prefetch_desc(&maps.main[f]);
-        tma_prefetch_desc(&maps.cols[f]);
-      }
+      for (int f = 0; f < NF; ++f) tma_prefetch_desc(&maps.wide[f]);
       int j = 0;
       for (; j < np; ++j) {
         const int s = j % S;
@@ -324,8 +390,7 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
         if (abort_flag) break;
         int z = z0 - R + j;
         if (p.per_z) z = wrap(z, p.nz);
-        issue_plane<T, TX, R, NF, 3>(maps, smem + s * L::STAGE_B, &full[s], x0, y0, nvx, nvy, z,
-                                     p.nx, p.ny, p.per_x, p.per_y);
+        issue_plane<T, TX, R, NF, 3>(maps, smem + s * L::STAGE_B, &full[s], t, z, p.nx, p.ny);
       }
       if (abort_flag) {
         for (int k = max(0, j - S); k < j; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
@@ -334,8 +399,8 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
     return;
   }
 
-  const int cx_t = tid % TX, cy0 = (tid / TX) * kRy, lane = tid % 32;
-  const int cx = min(cx_t, nvx - 1);
+  const int cx = tid % TX, cy0 = (tid / TX) * kRy, lane = tid % 32;
+  const int64_t plane = int64_t(p.nx) * p.ny;
   C q[kRy][NF][NQ];
   double red = 0.0;
   bool ok = true;
@@ -344,26 +409,28 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[j % S]);
   };
-  // Load the centre values of staged plane j into the top of each queue.
+  // Wait for staged plane j, put its wrapped halos in place, and push its
+  // centre values onto each queue.
   auto shift_in = [&](int j) -> bool {
     const int s = j % S;
     if (!mbar_wait_bounded(&full[s], (j / S) & 1, p.err) || abort_flag) {
       abort_flag = 1;
       return false;
     }
-    const T* st = reinterpret_cast<const T*>(smem + s * L::STAGE_B);
+    unsigned char* st = smem + s * L::STAGE_B;
+    if (fix && !fix_halo<T, TX, R, NF, NCONS>(st, t, p.ny, &fixb[s], (j / S) & 1, p.err)) {
+      abort_flag = 1;
+      return false;
+    }
 #pragma unroll
-    for (int r = 0; r < kRy; ++r) {
-      const int cy = min(cy0 + r, nvy - 1);
+    for (int r = 0; r < kRy; ++r)
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
 #pragma unroll
         for (int k = 0; k < NQ - 1; ++k) q[r][f][k] = q[r][f][k + 1];
         q[r][f][NQ - 1] =
-            to_c(reinterpret_cast<const T*>(reinterpret_cast<const unsigned char*>(st) +
-                                            f * L::FIELD_B)[(R + cy) * TX + cx]);
+            to_c(reinterpret_cast<const T*>(st + f * L::FIELD_B)[(R + cy0 + r) * L::W + L::CW + cx]);
       }
-    }
     return true;
   };
 
@@ -376,29 +443,23 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
     ok = shift_in(jn);
     if (!ok) break;
     const int jc = m + R;  // plane of the outputs
-    PlaneAcc<T, TX, R, NF, NQ> acc;
-    acc.stage = smem + (jc % S) * L::STAGE_B;
-    acc.nvx = nvx;
-    acc.nvy = nvy;
-    acc.cx = cx;
-    const int z = z0 + m;
+    const unsigned char* st = smem + (jc % S) * L::STAGE_B;
+    // column registers of the output plane: strip rows from the queue, the
+    // R rows on either side from shared memory
+    C col[NF][NC];
 #pragma unroll
-    for (int r = 0; r < kRy; ++r) {
-      const int cy_t = cy0 + r;
-      acc.cy = min(cy_t, nvy - 1);
-      acc.q = q[r];
-      const bool valid = cx_t < nvx && cy_t < nvy;
-      const int64_t gi = (int64_t(z) * p.ny + (y0 + acc.cy)) * p.nx + x0 + cx;
-      acc.g = gi;
-      C o[NF];
-      double r1 = 0.0;
-      p.op(acc, o, r1);
-      if (valid) {
+    for (int f = 0; f < NF; ++f) {
+      const T* w = reinterpret_cast<const T*>(st + f * L::FIELD_B);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) p.out[f][gi] = from_c<T>(o[f]);
-        red += r1;
+      for (int k = 0; k < R; ++k) {
+        col[f][k] = to_c(w[(cy0 + k) * L::W + L::CW + cx]);
+        col[f][R + kRy + k] = to_c(w[(cy0 + R + kRy + k) * L::W + L::CW + cx]);
       }
+#pragma unroll
+      for (int r = 0; r < kRy; ++r) col[f][R + r] = q[r][f][R];
     }
+    column_rows<Op, T, TX, NQ, NC>(p.op, st, p.out, int64_t(z0 + m) * plane, p.nx, t, cx, cy0, col,
+                                   q, red);
     release(jc);
     if (jn >= np - R) release(jn);  // above z1-1: centres only
   }
@@ -454,10 +515,10 @@ int sm_count() {
 template <class Op, class T, int RANK>
 struct TmaRunner {
   static constexpr int TX = TmaCfg<T>::TX;
-  static constexpr int S = RANK == 2 ? TmaCfg<T>::S2 : TmaCfg<T>::S3;
+  static constexpr int S = RANK == 2 ? (Op::NF == 1 ? TmaCfg<T>::S2 : 3) : TmaCfg<T>::S3;
   using L = Layout<T, TX, Op::R, Op::NF>;
   static constexpr int THREADS = TX * (kTy / kRy) + 32;
-  static constexpr size_t SMEM = size_t(S) * L::STAGE_B + 2 * S * sizeof(uint64_t) + 128;
+  static constexpr size_t SMEM = size_t(S) * L::STAGE_B + 3 * S * sizeof(uint64_t) + 128;
 
   static auto kernel() {
     if constexpr (RANK == 2) return &tma2d_kernel<Op, T, TX, S>;
@@ -519,9 +580,8 @@ struct TmaRunner {
     const int64_t n[3] = {a.g.n[2], a.g.n[1], a.g.n[0]};
     for (int f = 0; f < Op::NF; ++f) {
       cudaError_t e;
-      if ((e = encode<T>(&maps.main[f], a.in[f], RANK, n, TX, kTy + 2 * Op::R)) ||
-          (e = encode<T>(&maps.body[f], a.in[f], RANK, n, TX, kTy)) ||
-          (e = encode<T>(&maps.row[f], a.in[f], RANK, n, TX, 1)) ||
+      if ((e = encode<T>(&maps.wide[f], a.in[f], RANK, n, L::W, kTy + 2 * Op::R)) ||
+          (e = encode<T>(&maps.rows[f], a.in[f], RANK, n, L::W, Op::R)) ||
           (e = encode<T>(&maps.cols[f], a.in[f], RANK, n, L::CW, kTy)))
         return e;
     }
