@@ -201,6 +201,23 @@ lope_status lope_reduce(int op, lope_dtype dtype, const void* x, const void* y, 
  * Errors: LOPE_ERR_INVALID for an unknown name or out-of-range value. */
 lope_status lope_set_option(const char* name, int64_t value);
 
+/* The FP64 reduction of lope_reduce without any memory from the caller or
+ * the allocator: for callers that cannot provide scratch memory, such as code
+ * whose device memory is entirely owned by another allocator, or loops where
+ * an allocation call (which may synchronise the device) is not acceptable.
+ * The paper has no counterpart; this is a property of the library only.
+ * The per-block partial sums live in a 512 KiB array that is part of the
+ * library image (held on every GPU that loads the library until the process
+ * exits).  n must not exceed 2^28 elements (LOPE_ERR_INVALID otherwise).
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls on a device share the
+ * array, so calls that overlap on the GPU race: order them on one stream or
+ * synchronise between them.  Every element of the array that a call reads was
+ * written earlier in that call, so results never depend on previous calls.
+ * Arguments and result as lope_reduce. */
+lope_status lope_reduce_noalloc(int op, lope_dtype dtype, const void* x, const void* y, int64_t n,
+                                double* result_dev, void* cuda_stream);
+
 /* Synchronise the stream, then report (and clear) a device-side error flag set
  * by a bounded wait that gave up: LOPE_ERR_TIMEOUT, else LOPE_OK. */
 lope_status lope_sync_status(void* cuda_stream);

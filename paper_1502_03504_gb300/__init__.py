@@ -47,6 +47,7 @@ from ._lib import (  # noqa: F401  (C ABI names)
     lope_last_error,
     lope_launch_count,
     lope_reduce,
+    lope_reduce_noalloc,
     lope_reduce_scratch_bytes,
     lope_set_option,
     lope_set_boundary,

@@ -71,6 +71,7 @@ _SIGS = {
     "lope_adjoint": (_INT, [_P, _P, _P, _P, _I64, _I64, _P, _DP, _DP, _P, _SZ, _P]),
     "lope_reduce_scratch_bytes": (_SZ, []),
     "lope_reduce": (_INT, [_INT, _INT, _P, _P, _I64, _P, _P, _P]),
+    "lope_reduce_noalloc": (_INT, [_INT, _INT, _P, _P, _I64, _P, _P]),
     "lope_sync_status": (_INT, [_P]),
     "lope_set_option": (_INT, [ctypes.c_char_p, _I64]),
     "lope_launch_count": (_I64, []),
@@ -232,6 +233,12 @@ def lope_reduce(op, dtype, x, y, n, result_dev, scratch, stream):
 
 def lope_set_option(name: str, value: int):
     _check(load().lope_set_option(name.encode(), int(value)))
+
+
+def lope_reduce_noalloc(op, dtype, x, y, n, result_dev, stream):
+    """FP64 reduction whose partial sums live in the library's own static
+    device array: no scratch buffer from the caller (see include/lope.h)."""
+    _check(load().lope_reduce_noalloc(op, dtype, x, y, int(n), result_dev, stream))
 
 
 def lope_sync_status(stream):

@@ -496,6 +496,8 @@ void count_launches(int64_t n) {
 
 using namespace lope;
 
+lope_status lope_fail_external(lope_status st, const char* msg) { return fail(st, msg); }
+
 // ====================================================================== C ABI
 extern "C" {
 

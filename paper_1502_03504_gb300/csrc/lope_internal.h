@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "lope.h"
+
 namespace lope {
 
 // Stencil kinds (builtin names of lope_stencil_create_builtin).
@@ -110,3 +112,6 @@ size_t trap_smem_bytes(int dtype, int nf, int tile_x, int tile_y, int halo);
 void count_launches(int64_t n);
 
 }  // namespace lope
+
+// Record the last-error message of the calling thread (defined in api.cu).
+lope_status lope_fail_external(lope_status st, const char* msg);
