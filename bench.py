@@ -177,14 +177,24 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-def traffic_record(kernel_src):
+KERNEL_SOURCES = ("k_tma.cu", "device_common.cuh", "lope_internal.h")
+
+
+def kernel_source_hash():
+    """Hash of the sources the TMA kernels are compiled from."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1502_03504_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record():
     """Per-launch DRAM bytes from the committed ncu summary, if it matches the source."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             rec = json.load(fh)
-        with open(kernel_src, "rb") as fh:
-            h = hashlib.sha256(fh.read()).hexdigest()[:16]
-        if rec.get("source_sha256_16") == h:
+        if rec.get("source_sha256_16") == kernel_source_hash():
             return rec
     except Exception:
         pass
@@ -312,7 +322,7 @@ def main():
     launch2_s = t2 / 1e3 / T2
     ach3 = alg3 / launch3_s / 1e9
     ach2 = alg2 / launch2_s / 1e9
-    tr = traffic_record(os.path.join(ROOT, "paper_1502_03504_gb300", "csrc", "k_tma.cu"))
+    tr = traffic_record()
     roofline = {"bound": "hbm", "achieved": ach3, "peak": peak, "unit": "GB/s",
                 "frac": ach3 / peak, "traffic": tr["diff7_512_bytes_per_launch"] if tr else None,
                 "kernel": "tma3d_kernel<OpDiff7, float> (512^3, one sweep per launch)",

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -39,6 +40,7 @@ thread_local std::string g_last_error = "no error";
 std::atomic<int64_t> g_wait_limit_ms{1000};
 std::atomic<int64_t> g_skip_arrive{-1};
 thread_local bool g_capturing = false;
+thread_local int64_t g_captured = 0;  // kernels recorded by the capture in progress
 std::atomic<int64_t> g_launches{0};
 
 lope_status fail(lope_status st, const std::string& msg) {
@@ -254,7 +256,7 @@ GraphKey graph_key(const Geom& g, const StencilDesc& s, const Choice& c, const v
 }
 
 template <class F>
-lope_status run_graph(const GraphKey& key, int64_t kernels, cudaStream_t st, F&& body) {
+lope_status run_graph(const GraphKey& key, cudaStream_t st, F&& body) {
   DevState* d = nullptr;
   lope_status rs = dev_state(&d);
   if (rs != LOPE_OK) return rs;
@@ -269,18 +271,19 @@ lope_status run_graph(const GraphKey& key, int64_t kernels, cudaStream_t st, F&&
     cudaError_t e = cudaStreamBeginCapture(d->capture, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     g_capturing = true;
-    cudaError_t eb = body(d->capture);
+    g_captured = 0;
+    lope_status sb = body(d->capture);
     g_capturing = false;
     e = cudaStreamEndCapture(d->capture, &graph);
-    if (eb != cudaSuccess) {
+    if (sb != LOPE_OK) {
       if (graph) cudaGraphDestroy(graph);
-      return cuda_fail(eb, "capturing launches");
+      return sb;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(&ent.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-    ent.kernels = kernels;
+    ent.kernels = g_captured;
     std::lock_guard<std::mutex> lk(g_graph_mu);
     if (g_graphs.size() > 256) {
       for (auto& kv : g_graphs) cudaGraphExecDestroy(kv.second.exec);
@@ -319,8 +322,9 @@ lope_status apply_impl(const lope_grid* grid, const lope_stencil* st, const void
   const int gmode = cfg ? cfg->graph : 0;
   const bool use_graph = gmode == 1 || (gmode == 0 && L >= 8 && npts(g) <= (int64_t(1) << 22));
   if (use_graph) {
-    return run_graph(graph_key(g, s, c, in, out, work, nsteps), L, stream, [&](cudaStream_t cs) {
-      return issue(g, s, c, in, out, work, nsteps, d->err, cs);
+    return run_graph(graph_key(g, s, c, in, out, work, nsteps), stream, [&](cudaStream_t cs) {
+      cudaError_t e = issue(g, s, c, in, out, work, nsteps, d->err, cs);
+      return e == cudaSuccess ? LOPE_OK : cuda_fail(e, "capturing launches");
     });
   }
   cudaError_t e = issue(g, s, c, in, out, work, nsteps, d->err, stream);
@@ -469,6 +473,24 @@ lope_status reverse_impl(const lope_grid* grid, const lope_stencil* st, const vo
   return LOPE_OK;
 }
 
+// Key of a captured adjoint sequence: everything that the launches depend on.
+GraphKey adjoint_key(int kind, const lope_grid* grid, const lope_stencil* st,
+                     std::initializer_list<const void*> ptrs, int64_t nsteps, int64_t K) {
+  GraphKey k;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  k.push_back(-1000 - kind);
+  k.push_back(dev);
+  const int64_t* gw = reinterpret_cast<const int64_t*>(&grid->g);
+  k.insert(k.end(), gw, gw + sizeof(Geom) / 8);
+  const int64_t* sw = reinterpret_cast<const int64_t*>(&st->s);
+  k.insert(k.end(), sw, sw + sizeof(StencilDesc) / 8);
+  for (const void* p : ptrs) k.push_back(int64_t(reinterpret_cast<uintptr_t>(p)));
+  k.push_back(nsteps);
+  k.push_back(K);
+  return k;
+}
+
 // ------------------------------------------------------------------ batch
 struct BatchPlan {
   std::vector<BatchGrid> host;
@@ -489,7 +511,8 @@ size_t batch_ws_bytes(int n) { return 256 + (size_t(n) * sizeof(BatchGrid) + 255
 }  // namespace
 
 void count_launches(int64_t n) {
-  if (!g_capturing) g_launches.fetch_add(n);
+  if (g_capturing) g_captured += n;
+  else g_launches.fetch_add(n);
 }
 
 }  // namespace lope
@@ -835,8 +858,12 @@ lope_status lope_forward_ckpt(const lope_grid* grid, const lope_stencil* stencil
   if (!u0 || !uT || !workspace || !aligned16(workspace)) return fail(LOPE_ERR_INVALID, "bad pointer");
   const AdjLayout L = adj_layout(grid->g, nsteps, checkpoint_every);
   if (workspace_bytes < L.total) return fail(LOPE_ERR_ALLOC, "workspace too small");
-  return forward_ckpt_impl(grid, stencil, u0, uT, nsteps, checkpoint_every,
-                           static_cast<char*>(workspace), L, static_cast<cudaStream_t>(cuda_stream));
+  char* ws = static_cast<char*>(workspace);
+  return run_graph(adjoint_key(0, grid, stencil, {u0, uT, workspace}, nsteps, checkpoint_every),
+                   static_cast<cudaStream_t>(cuda_stream), [&](cudaStream_t cs) {
+                     return forward_ckpt_impl(grid, stencil, u0, uT, nsteps, checkpoint_every, ws,
+                                              L, cs);
+                   });
 }
 
 lope_status lope_vjp(const lope_grid* grid, const lope_stencil* stencil, const void* u0,
@@ -855,14 +882,19 @@ lope_status lope_vjp(const lope_grid* grid, const lope_stencil* stencil, const v
   if ((rs = dev_state(&d)) != LOPE_OK) return rs;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   char* ws = static_cast<char*>(workspace);
-  if (!reuse_checkpoints) {
-    // u_T itself is not needed; it lands in the last checkpoint slot.
-    void* uT = ws + L.off_ckpt + size_t(L.nseg - 1) * L.field;
-    if ((rs = forward_ckpt_impl(grid, stencil, u0, uT, nsteps, checkpoint_every, ws, L, st)) != LOPE_OK)
-      return rs;
-  }
-  return reverse_impl(grid, stencil, u0, grad_uT, nsteps, checkpoint_every, grad_u0,
-                      grad_coeff_dev, ws, L, d->err, st);
+  const GraphKey key = adjoint_key(reuse_checkpoints ? 1 : 2, grid, stencil,
+                                   {u0, grad_uT, grad_u0, grad_coeff_dev, workspace}, nsteps,
+                                   checkpoint_every);
+  return run_graph(key, st, [&](cudaStream_t cs) {
+    if (!reuse_checkpoints) {
+      // u_T itself is not needed; it lands in the last checkpoint slot.
+      void* uT = ws + L.off_ckpt + size_t(L.nseg - 1) * L.field;
+      lope_status r = forward_ckpt_impl(grid, stencil, u0, uT, nsteps, checkpoint_every, ws, L, cs);
+      if (r != LOPE_OK) return r;
+    }
+    return reverse_impl(grid, stencil, u0, grad_uT, nsteps, checkpoint_every, grad_u0,
+                        grad_coeff_dev, ws, L, d->err, cs);
+  });
 }
 
 lope_status lope_adjoint(const lope_grid* grid, const lope_stencil* stencil, const void* u0,
@@ -880,19 +912,25 @@ lope_status lope_adjoint(const lope_grid* grid, const lope_stencil* stencil, con
   if ((rs = dev_state(&d)) != LOPE_OK) return rs;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   char* ws = static_cast<char*>(workspace);
-  void* uT = ws + L.off_ckpt + size_t(L.nseg - 1) * L.field;
-  if ((rs = forward_ckpt_impl(grid, stencil, u0, uT, nsteps, checkpoint_every, ws, L, st)) != LOPE_OK)
-    return rs;
   double* scal = reinterpret_cast<double*>(ws + L.off_scal);
-  double* partials = reinterpret_cast<double*>(ws + L.off_part);
-  void* lamT = ws + L.off_tmp;  // the forward work buffer is free now
-  cudaError_t e = launch_loss_seed(grid->g.dtype, uT, target, lamT, npts(grid->g), partials, &scal[0], st);
-  if (e != cudaSuccess) return cuda_fail(e, "loss kernel");
-  if ((rs = reverse_impl(grid, stencil, u0, lamT, nsteps, checkpoint_every, grad_u0, &scal[1], ws, L,
-                         d->err, st)) != LOPE_OK)
-    return rs;
+  rs = run_graph(adjoint_key(3, grid, stencil, {u0, target, grad_u0, workspace}, nsteps,
+                             checkpoint_every),
+                 st, [&](cudaStream_t cs) {
+                   void* uT = ws + L.off_ckpt + size_t(L.nseg - 1) * L.field;
+                   lope_status r = forward_ckpt_impl(grid, stencil, u0, uT, nsteps,
+                                                     checkpoint_every, ws, L, cs);
+                   if (r != LOPE_OK) return r;
+                   double* partials = reinterpret_cast<double*>(ws + L.off_part);
+                   void* lamT = ws + L.off_tmp;  // the forward work buffer is free now
+                   cudaError_t e = launch_loss_seed(grid->g.dtype, uT, target, lamT,
+                                                    npts(grid->g), partials, &scal[0], cs);
+                   if (e != cudaSuccess) return cuda_fail(e, "loss kernel");
+                   return reverse_impl(grid, stencil, u0, lamT, nsteps, checkpoint_every, grad_u0,
+                                       &scal[1], ws, L, d->err, cs);
+                 });
+  if (rs != LOPE_OK) return rs;
   double host[2] = {0.0, 0.0};
-  e = cudaMemcpyAsync(host, scal, sizeof(host), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaMemcpyAsync(host, scal, sizeof(host), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "reading loss and dL/dc");
   if (loss) *loss = host[0];

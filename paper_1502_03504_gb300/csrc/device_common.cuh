@@ -79,14 +79,19 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+// One try_wait with a suspend-time hint: the thread may sleep in hardware
+// until the phase completes or about kSuspendNs pass, instead of spinning and
+// taking issue slots from the warps that have work.
+constexpr uint32_t kSuspendNs = 20000;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -98,7 +103,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   uint64_t t0 = global_ns();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u && global_ns() - t0 > kWaitLimitNs) {
+    if ((it & 15u) == 15u && global_ns() - t0 > kWaitLimitNs) {
       raise_error(err, kErrTimeout);
       return false;
     }
@@ -133,51 +138,63 @@ __device__ __forceinline__ int wrap(int q, int n) {
   return q < 0 ? q + n : q;
 }
 
+// A coefficient kept in both precisions, converted once on the host (round
+// to nearest), so FP32 kernels never convert FP64 values per point.
+struct Coef {
+  double d;
+  float f;
+  Coef() = default;
+  __host__ __device__ Coef(double v) : d(v), f(float(v)) {}
+  __device__ __forceinline__ float get(float) const { return f; }
+  __device__ __forceinline__ double get(double) const { return d; }
+};
+
 // ---------------------------------------------------------------- local functions
 //
 // Each local function writes only its own element(s) and reads U(f,dx,dy,dz)
 // through an accessor that hides where the halo values come from (shared
 // memory tile, register queue, global memory with boundary logic).  This is
 // the LOPe contract (Sec. 2.2, Fig. 1): the function never sees where its
-// element sits in the grid.  The `red` argument is an FP64 accumulator used
-// only by the adjoint functions.
+// element sits in the grid.  The `red` argument (compute precision) receives
+// a per-point term that only the adjoint functions produce; the kernels sum
+// those terms over a few points and then accumulate in FP64.
 
 struct OpJacobi5 {  // Fig. 1 with a coefficient: u + c (E + W + N + S - 4u)
   static constexpr int NDIM = 2, R = 1, NF = 1;
   static constexpr bool REDUCES = false, STAR = true;
-  double c;
+  Coef c;
   template <class C, class A>
-  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], double&) const {
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], C&) const {
     C u = U(0, 0, 0, 0);
     C nb = add(add(U(0, -1, 0, 0), U(0, 1, 0, 0)), add(U(0, 0, -1, 0), U(0, 0, 1, 0)));
-    o[0] = fma_(C(c), fma_(C(-4), u, nb), u);
+    o[0] = fma_(c.get(C()), fma_(C(-4), u, nb), u);
   }
 };
 
 struct OpDiff7 {  // u + c (sum of the six face neighbours - 6u)
   static constexpr int NDIM = 3, R = 1, NF = 1;
   static constexpr bool REDUCES = false, STAR = true;
-  double c;
+  Coef c;
   template <class C, class A>
-  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], double&) const {
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], C&) const {
     C u = U(0, 0, 0, 0);
     C nb = add(add(add(U(0, -1, 0, 0), U(0, 1, 0, 0)), add(U(0, 0, -1, 0), U(0, 0, 1, 0))),
                add(U(0, 0, 0, -1), U(0, 0, 0, 1)));
-    o[0] = fma_(C(c), fma_(C(-6), u, nb), u);
+    o[0] = fma_(c.get(C()), fma_(C(-6), u, nb), u);
   }
 };
 
 struct OpStar9r2 {  // u + c (L4x u + L4y u), L4 = (-1/12, 4/3, -5/2, 4/3, -1/12)
   static constexpr int NDIM = 2, R = 2, NF = 1;
   static constexpr bool REDUCES = false, STAR = true;
-  double c;
+  Coef c;
   template <class C, class A>
-  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], double&) const {
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], C&) const {
     C u = U(0, 0, 0, 0);
     C s1 = add(add(U(0, -1, 0, 0), U(0, 1, 0, 0)), add(U(0, 0, -1, 0), U(0, 0, 1, 0)));
     C s2 = add(add(U(0, -2, 0, 0), U(0, 2, 0, 0)), add(U(0, 0, -2, 0), U(0, 0, 2, 0)));
     C lap = fma_(C(4.0 / 3.0), s1, fma_(C(-1.0 / 12.0), s2, mul(C(-5), u)));
-    o[0] = fma_(C(c), lap, u);
+    o[0] = fma_(c.get(C()), lap, u);
   }
 };
 
@@ -186,14 +203,14 @@ struct OpStar9r2 {  // u + c (L4x u + L4y u), L4 = (-1/12, 4/3, -5/2, 4/3, -1/12
 struct OpSwe {
   static constexpr int NDIM = 2, R = 1, NF = 3;
   static constexpr bool REDUCES = false, STAR = true;
-  double dtH, dtg;
+  Coef mdtH, mdtg;  // -dt*H and -dt*g
   template <class C, class A>
-  __device__ __forceinline__ void operator()(const A& U, C (&o)[3], double&) const {
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[3], C&) const {
     C h = U(0, 0, 0, 0), u = U(1, 0, 0, 0), v = U(2, 0, 0, 0);
     C div = add(sub(u, U(1, -1, 0, 0)), sub(v, U(2, 0, -1, 0)));
-    o[0] = fma_(C(-dtH), div, h);
-    o[1] = fma_(C(-dtg), sub(U(0, 1, 0, 0), h), u);
-    o[2] = fma_(C(-dtg), sub(U(0, 0, 1, 0), h), v);
+    o[0] = fma_(mdtH.get(C()), div, h);
+    o[1] = fma_(mdtg.get(C()), sub(U(0, 1, 0, 0), h), u);
+    o[2] = fma_(mdtg.get(C()), sub(U(0, 0, 1, 0), h), v);
   }
 };
 
@@ -203,16 +220,16 @@ template <int ND, int RR>
 struct OpStarLinear {
   static constexpr int NDIM = ND, R = RR, NF = 1;
   static constexpr bool REDUCES = false, STAR = true;
-  double w[3][2 * RR + 1];
+  Coef w[3][2 * RR + 1];
   template <class C, class A>
-  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], double&) const {
-    C s = mul(C(w[0][RR]), U(0, 0, 0, 0));
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], C&) const {
+    C s = mul(w[0][RR].get(C()), U(0, 0, 0, 0));
 #pragma unroll
     for (int d = -RR; d <= RR; ++d) {
       if (d == 0) continue;
-      s = fma_(C(w[0][d + RR]), U(0, d, 0, 0), s);
-      s = fma_(C(w[1][d + RR]), U(0, 0, d, 0), s);
-      if (ND == 3) s = fma_(C(w[2][d + RR]), U(0, 0, 0, d), s);
+      s = fma_(w[0][d + RR].get(C()), U(0, d, 0, 0), s);
+      s = fma_(w[1][d + RR].get(C()), U(0, 0, d, 0), s);
+      if (ND == 3) s = fma_(w[2][d + RR].get(C()), U(0, 0, 0, d), s);
     }
     o[0] = s;
   }
@@ -225,9 +242,9 @@ struct OpBoxLinear {
   static constexpr bool REDUCES = false, STAR = false;
   static constexpr int SIDE = 2 * RR + 1;
   static constexpr int ZS = ND == 3 ? SIDE : 1;
-  double w[ZS * SIDE * SIDE];
+  Coef w[ZS * SIDE * SIDE];
   template <class C, class A>
-  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], double&) const {
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], C&) const {
     C s = C(0);
     constexpr int ZR = ND == 3 ? RR : 0;
 #pragma unroll
@@ -236,7 +253,7 @@ struct OpBoxLinear {
       for (int dy = -RR; dy <= RR; ++dy)
 #pragma unroll
         for (int dx = -RR; dx <= RR; ++dx)
-          s = fma_(C(w[((dz + ZR) * SIDE + dy + RR) * SIDE + dx + RR]), U(0, dx, dy, dz), s);
+          s = fma_(w[((dz + ZR) * SIDE + dy + RR) * SIDE + dx + RR].get(C()), U(0, dx, dy, dz), s);
     o[0] = s;
   }
 };
@@ -254,10 +271,10 @@ struct OpAdjDiffusion {
   static constexpr int R = KIND == kStar9r2 ? 2 : 1;
   static constexpr int NF = 1;
   static constexpr bool REDUCES = true, STAR = true;
-  double c;
+  Coef c;
   const T* ut;
   template <class C, class A>
-  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], double& red) const {
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[1], C& red) const {
     C l = U(0, 0, 0, 0);
     C lt;  // (L^T lambda) at the local element
     if (KIND == kJacobi5) {
@@ -272,8 +289,8 @@ struct OpAdjDiffusion {
       C s2 = add(add(U(0, 2, 0, 0), U(0, -2, 0, 0)), add(U(0, 0, 2, 0), U(0, 0, -2, 0)));
       lt = fma_(C(4.0 / 3.0), s1, fma_(C(-1.0 / 12.0), s2, mul(C(-5), l)));
     }
-    o[0] = fma_(C(c), lt, l);
-    red = __fma_rn(double(lt), double(to_c(__ldg(ut + U.gidx()))), red);
+    o[0] = fma_(c.get(C()), lt, l);
+    red = fma_(lt, to_c(__ldg(ut + U.gidx())), red);
   }
 };
 

@@ -100,7 +100,9 @@ __global__ void __launch_bounds__(256) direct_kernel(Op op, Geom g, const T* in0
        p += int64_t(gridDim.x) * blockDim.x) {
     GlobalAcc<T, Op::NF> acc{src, g, p / (g.n[1] * g.n[2]), (p / g.n[2]) % g.n[1], p % g.n[2]};
     C o[Op::NF];
-    op(acc, o, red);
+    C r1 = C(0);
+    op(acc, o, r1);
+    red += double(r1);
 #pragma unroll
     for (int f = 0; f < Op::NF; ++f) dst[f][p] = from_c<T>(o[f]);
   }
@@ -173,7 +175,7 @@ template <class T> cudaError_t dispatch_t(const StepArgs& a, bool trap, int* blo
     case kJacobi5: return run_any<OpJacobi5, T>(a, {s.prm[0]}, trap, blocks);
     case kStar9r2: return run_any<OpStar9r2, T>(a, {s.prm[0]}, trap, blocks);
     case kDiff7: return run_any<OpDiff7, T>(a, {s.prm[0]}, trap, blocks);
-    case kSwe: return run_any<OpSwe, T>(a, {s.prm[0] * s.prm[2], s.prm[0] * s.prm[1]}, trap, blocks);
+    case kSwe: return run_any<OpSwe, T>(a, {-s.prm[0] * s.prm[2], -s.prm[0] * s.prm[1]}, trap, blocks);
     case kLinear:
       if (s.star) {
         if (s.ndim == 2 && s.radius == 1) return run_any<OpStarLinear<2, 1>, T>(a, star_op<2, 1>(s), trap, blocks);

@@ -31,13 +31,18 @@ namespace lope {
 
 namespace {
 
-constexpr int kTy = 32;  // tile rows
-constexpr int kRy = 8;   // rows per consumer thread
+// Tile shape per storage type, rank and field count: TX columns (TX times the
+// element size is a multiple of 128 bytes), TY rows, RY rows per consumer
+// thread (TX * TY / RY consumer threads plus one producer warp), S stages.
+template <class T> struct TmaTx { static constexpr int TX = 64; };
+template <> struct TmaTx<double> { static constexpr int TX = 32; };
 
-template <class T> struct TmaCfg;
-template <> struct TmaCfg<float> { static constexpr int TX = 64, S2 = 4, S3 = 6; };
-template <> struct TmaCfg<double> { static constexpr int TX = 32, S2 = 4, S3 = 6; };
-template <> struct TmaCfg<__nv_bfloat16> { static constexpr int TX = 64, S2 = 4, S3 = 6; };
+template <class T, int RANK, int NF> struct TmaCfg {
+  static constexpr int TX = TmaTx<T>::TX;
+  static constexpr int TY = (RANK == 2 && NF == 1) ? 64 : 32;
+  static constexpr int RY = RANK == 2 ? 16 : 8;
+  static constexpr int S = RANK == 3 ? 8 : 3;
+};
 
 template <int NF> struct TmaMaps {
   CUtensorMap wide[NF];  // box {W, TY+2R}: tile, CW halo columns each side, R halo rows each side
@@ -67,11 +72,11 @@ template <class Op, class T> struct TmaParams {
 // replace (the periodic halo, BC=CYCLIC of Sec. 3.2); every tap is then a
 // shared load at a compile-time offset from the local element.  Star stencils
 // never read the corner cells, which stay as loaded.
-template <class T, int TX, int R, int NF> struct Layout {
+template <class T, int TX, int TY, int R, int NF> struct Layout {
   static constexpr int CW = 16 / int(sizeof(T));
   static constexpr int W = TX + 2 * CW;
-  static constexpr uint32_t WIDE_B = (kTy + 2 * R) * W * sizeof(T);
-  static constexpr uint32_t COL_B = kTy * CW * sizeof(T);
+  static constexpr uint32_t WIDE_B = (TY + 2 * R) * W * sizeof(T);
+  static constexpr uint32_t COL_B = TY * CW * sizeof(T);
   static constexpr uint32_t ROW_B = R * W * sizeof(T);
   static constexpr uint32_t A(uint32_t b) { return (b + 127) / 128 * 128; }
   static constexpr uint32_t OFF_COLL = A(WIDE_B);
@@ -89,13 +94,13 @@ struct TileInfo {
   bool yl, yh;  // low / high halo rows wrap
 };
 
-template <class T, int TX, int R>
+template <class T, int TX, int TY, int R>
 __device__ __forceinline__ TileInfo classify(int x0, int y0, int nx, int ny, int per_x, int per_y) {
   TileInfo t;
   t.x0 = x0;
   t.y0 = y0;
   t.nvx = min(TX, nx - x0);
-  t.nvy = min(kTy, ny - y0);
+  t.nvy = min(TY, ny - y0);
   t.xl = per_x && x0 == 0;
   t.xr = per_x && x0 + t.nvx == nx;
   t.yl = per_y && y0 < R;
@@ -107,9 +112,9 @@ __device__ __forceinline__ TileInfo classify(int x0, int y0, int nx, int ny, int
 // from b[f] (the local element in the wide box); y taps and the centre come
 // from the thread's column registers col[f][R + dy]; z taps (3D) from the
 // register queue q[f][R + dz].
-template <class T, int TX, int R, int NF, int NQ, int NC>
+template <class T, int TX, int TY, int R, int NF, int NQ, int NC>
 struct StageAcc {
-  using L = Layout<T, TX, R, NF>;
+  using L = Layout<T, TX, TY, R, NF>;
   using C = C_t<T>;
   const T* b[NF];
   const C (*col)[NC];  // col[f] + r, so col[f][R + dy] is row r + dy
@@ -132,11 +137,11 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* m, int x,
 }
 
 // Issue the copies of one tile/plane of every field into stage `st`.
-template <class T, int TX, int R, int NF, int RANK>
+template <class T, int TX, int TY, int R, int NF, int RANK>
 __device__ __forceinline__ void issue_plane(const TmaMaps<NF>& maps, unsigned char* st,
                                             uint64_t* bar, const TileInfo& t, int z, int nx,
                                             int ny) {
-  using L = Layout<T, TX, R, NF>;
+  using L = Layout<T, TX, TY, R, NF>;
   const uint32_t per_field = L::WIDE_B + (uint32_t(t.xl) + uint32_t(t.xr)) * L::COL_B +
                              (uint32_t(t.yl) + uint32_t(t.yh)) * L::ROW_B;
   mbar_arrive_expect_tx(bar, NF * per_field);
@@ -156,10 +161,10 @@ __device__ __forceinline__ void issue_plane(const TmaMaps<NF>& maps, unsigned ch
 // the shared-memory writes before the stage's next TMA refill, and wait until
 // every consumer warp has written its share (mbarrier `fixb`, bounded wait).
 // Returns false if the wait gave up.
-template <class T, int TX, int R, int NF, int NCONS>
+template <class T, int TX, int TY, int R, int NF, int NCONS>
 __device__ __forceinline__ bool fix_halo(unsigned char* st, const TileInfo& t, int ny,
                                          uint64_t* fixb, uint32_t parity, int* err) {
-  using L = Layout<T, TX, R, NF>;
+  using L = Layout<T, TX, TY, R, NF>;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     T* w = reinterpret_cast<T*>(st + f * L::FIELD_B);
@@ -216,23 +221,24 @@ __device__ __forceinline__ void block_accumulate(double v, double* partials, dou
   }
 }
 
-// kRy outputs of one column of a staged tile/plane.  col[f][i] holds the
-// column's values for tile rows cy0 - R + i, i in [0, kRy + 2R).
-template <class Op, class T, int TX, int NQ, int NC>
+// RY outputs of one column of a staged tile/plane.  col[f][i] holds the
+// column's values for tile rows cy0 - R + i, i in [0, RY + 2R).
+template <class Op, class T, int TX, int TY, int RY, int NQ, int NC>
 __device__ __forceinline__ void column_rows(const Op& op, const unsigned char* st, T* const* out,
                                             int64_t zoff, int nx, const TileInfo& t, int cx,
                                             int cy0, const C_t<T> (*col)[NC],
                                             const C_t<T> (*q)[Op::NF][NQ], double& red) {
   using C = C_t<T>;
   constexpr int R = Op::R, NF = Op::NF;
-  using L = Layout<T, TX, R, NF>;
+  using L = Layout<T, TX, TY, R, NF>;
   const bool xvalid = cx < t.nvx;
   const int64_t base = zoff + int64_t(t.y0 + cy0) * nx + t.x0 + cx;
   const int64_t gclamp = zoff + int64_t(t.y0) * nx + t.x0;  // a valid element for clamped reads
+  C rsum = C(0);  // adjoint terms of this column, summed in compute precision
 #pragma unroll
-  for (int r = 0; r < kRy; ++r) {
+  for (int r = 0; r < RY; ++r) {
     const bool valid = xvalid && cy0 + r < t.nvy;
-    StageAcc<T, TX, R, NF, NQ, NC> acc;
+    StageAcc<T, TX, TY, R, NF, NQ, NC> acc;
 #pragma unroll
     for (int f = 0; f < NF; ++f)
       acc.b[f] = reinterpret_cast<const T*>(st + f * L::FIELD_B) + (R + cy0 + r) * L::W + L::CW + cx;
@@ -241,24 +247,25 @@ __device__ __forceinline__ void column_rows(const Op& op, const unsigned char* s
     acc.g = valid ? base + int64_t(r) * nx : gclamp;
     acc.q = q ? q[r] : nullptr;
     C o[NF];
-    double r1 = 0.0;
+    C r1 = C(0);
     op(acc, o, r1);
     if (valid) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) out[f][base + int64_t(r) * nx] = from_c<T>(o[f]);
-      red += r1;
+      rsum = add(rsum, r1);
     }
   }
+  if (Op::REDUCES) red += double(rsum);
 }
 
 // ------------------------------------------------------------------ 2D tiles
-template <class Op, class T, int TX, int S>
-__global__ void __launch_bounds__(TX * (kTy / kRy) + 32)
+template <class Op, class T, int TX, int TY, int RY, int S>
+__global__ void __launch_bounds__(TX * (TY / RY) + 32)
     tma2d_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
   using C = C_t<T>;
-  constexpr int R = Op::R, NF = Op::NF, NC = kRy + 2 * R;
-  using L = Layout<T, TX, R, NF>;
-  constexpr int NCONS = TX * (kTy / kRy);
+  constexpr int R = Op::R, NF = Op::NF, NC = RY + 2 * R;
+  using L = Layout<T, TX, TY, R, NF>;
+  constexpr int NCONS = TX * (TY / RY);
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = align128(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * L::STAGE_B);
@@ -292,9 +299,9 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32)
           break;
         }
         if (abort_flag) break;
-        const TileInfo t = classify<T, TX, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * kTy, p.nx,
+        const TileInfo t = classify<T, TX, TY, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx,
                                               p.ny, p.per_x, p.per_y);
-        issue_plane<T, TX, R, NF, 2>(maps, smem + s * L::STAGE_B, &full[s], t, 0, p.nx, p.ny);
+        issue_plane<T, TX, TY, R, NF, 2>(maps, smem + s * L::STAGE_B, &full[s], t, 0, p.nx, p.ny);
       }
       if (abort_flag) {  // let copies already issued land before the block exits
         for (int k = max(0, i - S); k < i; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
@@ -303,7 +310,7 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32)
     return;
   }
 
-  const int cx = tid % TX, cy0 = (tid / TX) * kRy, lane = tid % 32;
+  const int cx = tid % TX, cy0 = (tid / TX) * RY, lane = tid % 32;
   double red = 0.0;
   uint32_t fixph = 0;  // bit s: phase parity of fixb[s]
   int i = 0;
@@ -313,11 +320,11 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32)
       abort_flag = 1;
       break;
     }
-    const TileInfo t = classify<T, TX, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * kTy, p.nx, p.ny,
+    const TileInfo t = classify<T, TX, TY, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx, p.ny,
                                           p.per_x, p.per_y);
     unsigned char* st = smem + s * L::STAGE_B;
     if (t.xl || t.xr || t.yl || t.yh) {
-      const bool fixed = fix_halo<T, TX, R, NF, NCONS>(st, t, p.ny, &fixb[s], (fixph >> s) & 1u, p.err);
+      const bool fixed = fix_halo<T, TX, TY, R, NF, NCONS>(st, t, p.ny, &fixb[s], (fixph >> s) & 1u, p.err);
       fixph ^= 1u << s;
       if (!fixed) {
         abort_flag = 1;
@@ -330,7 +337,7 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32)
 #pragma unroll
       for (int k = 0; k < NC; ++k)
         col[f][k] = to_c(reinterpret_cast<const T*>(st + f * L::FIELD_B)[(cy0 + k) * L::W + L::CW + cx]);
-    column_rows<Op, T, TX, 1, NC>(p.op, st, p.out, 0, p.nx, t, cx, cy0, col, nullptr, red);
+    column_rows<Op, T, TX, TY, RY, 1, NC>(p.op, st, p.out, 0, p.nx, t, cx, cy0, col, nullptr, red);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
@@ -338,13 +345,13 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32)
 }
 
 // ------------------------------------------------------------------ 3D z-march
-template <class Op, class T, int TX, int S>
-__global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
+template <class Op, class T, int TX, int TY, int RY, int S>
+__global__ void __launch_bounds__(TX * (TY / RY) + 32, 2)
     tma3d_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
   using C = C_t<T>;
-  constexpr int R = Op::R, NF = Op::NF, NQ = 2 * R + 1, NC = kRy + 2 * R;
-  using L = Layout<T, TX, R, NF>;
-  constexpr int NCONS = TX * (kTy / kRy);
+  constexpr int R = Op::R, NF = Op::NF, NQ = 2 * R + 1, NC = RY + 2 * R;
+  using L = Layout<T, TX, TY, R, NF>;
+  constexpr int NCONS = TX * (TY / RY);
   static_assert(S >= R + 2, "ring too short for the z window");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = align128(smem_raw);
@@ -357,7 +364,7 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
   const int tid = threadIdx.x;
   const int ntiles = p.tiles_x * p.tiles_y;
   const int tile = blockIdx.x % ntiles, zc = blockIdx.x / ntiles;
-  const TileInfo t = classify<T, TX, R>((tile % p.tiles_x) * TX, (tile / p.tiles_x) * kTy, p.nx,
+  const TileInfo t = classify<T, TX, TY, R>((tile % p.tiles_x) * TX, (tile / p.tiles_x) * TY, p.nx,
                                         p.ny, p.per_x, p.per_y);
   const bool fix = t.xl || t.xr || t.yl || t.yh;
   const int z0 = zc * p.zchunk, z1 = min(p.nz, z0 + p.zchunk);
@@ -390,7 +397,7 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
         if (abort_flag) break;
         int z = z0 - R + j;
         if (p.per_z) z = wrap(z, p.nz);
-        issue_plane<T, TX, R, NF, 3>(maps, smem + s * L::STAGE_B, &full[s], t, z, p.nx, p.ny);
+        issue_plane<T, TX, TY, R, NF, 3>(maps, smem + s * L::STAGE_B, &full[s], t, z, p.nx, p.ny);
       }
       if (abort_flag) {
         for (int k = max(0, j - S); k < j; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
@@ -399,9 +406,9 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
     return;
   }
 
-  const int cx = tid % TX, cy0 = (tid / TX) * kRy, lane = tid % 32;
+  const int cx = tid % TX, cy0 = (tid / TX) * RY, lane = tid % 32;
   const int64_t plane = int64_t(p.nx) * p.ny;
-  C q[kRy][NF][NQ];
+  C q[RY][NF][NQ];
   double red = 0.0;
   bool ok = true;
 
@@ -418,12 +425,12 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
       return false;
     }
     unsigned char* st = smem + s * L::STAGE_B;
-    if (fix && !fix_halo<T, TX, R, NF, NCONS>(st, t, p.ny, &fixb[s], (j / S) & 1, p.err)) {
+    if (fix && !fix_halo<T, TX, TY, R, NF, NCONS>(st, t, p.ny, &fixb[s], (j / S) & 1, p.err)) {
       abort_flag = 1;
       return false;
     }
 #pragma unroll
-    for (int r = 0; r < kRy; ++r)
+    for (int r = 0; r < RY; ++r)
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
 #pragma unroll
@@ -453,12 +460,12 @@ __global__ void __launch_bounds__(TX * (kTy / kRy) + 32, 2)
 #pragma unroll
       for (int k = 0; k < R; ++k) {
         col[f][k] = to_c(w[(cy0 + k) * L::W + L::CW + cx]);
-        col[f][R + kRy + k] = to_c(w[(cy0 + R + kRy + k) * L::W + L::CW + cx]);
+        col[f][R + RY + k] = to_c(w[(cy0 + R + RY + k) * L::W + L::CW + cx]);
       }
 #pragma unroll
-      for (int r = 0; r < kRy; ++r) col[f][R + r] = q[r][f][R];
+      for (int r = 0; r < RY; ++r) col[f][R + r] = q[r][f][R];
     }
-    column_rows<Op, T, TX, NQ, NC>(p.op, st, p.out, int64_t(z0 + m) * plane, p.nx, t, cx, cy0, col,
+    column_rows<Op, T, TX, TY, RY, NQ, NC>(p.op, st, p.out, int64_t(z0 + m) * plane, p.nx, t, cx, cy0, col,
                                    q, red);
     release(jc);
     if (jn >= np - R) release(jn);  // above z1-1: centres only
@@ -514,15 +521,15 @@ int sm_count() {
 
 template <class Op, class T, int RANK>
 struct TmaRunner {
-  static constexpr int TX = TmaCfg<T>::TX;
-  static constexpr int S = RANK == 2 ? (Op::NF == 1 ? TmaCfg<T>::S2 : 3) : TmaCfg<T>::S3;
-  using L = Layout<T, TX, Op::R, Op::NF>;
-  static constexpr int THREADS = TX * (kTy / kRy) + 32;
+  using Cfg = TmaCfg<T, RANK, Op::NF>;
+  static constexpr int TX = Cfg::TX, TY = Cfg::TY, RY = Cfg::RY, S = Cfg::S;
+  using L = Layout<T, TX, TY, Op::R, Op::NF>;
+  static constexpr int THREADS = TX * (TY / RY) + 32;
   static constexpr size_t SMEM = size_t(S) * L::STAGE_B + 3 * S * sizeof(uint64_t) + 128;
 
   static auto kernel() {
-    if constexpr (RANK == 2) return &tma2d_kernel<Op, T, TX, S>;
-    else return &tma3d_kernel<Op, T, TX, S>;
+    if constexpr (RANK == 2) return &tma2d_kernel<Op, T, TX, TY, RY, S>;
+    else return &tma3d_kernel<Op, T, TX, TY, RY, S>;
   }
 
   static int occupancy() {
@@ -548,7 +555,7 @@ struct TmaRunner {
     p.per_y = g.bc[1][0] == kPeriodic;
     p.per_z = g.bc[0][0] == kPeriodic;
     p.tiles_x = (p.nx + TX - 1) / TX;
-    p.tiles_y = (p.ny + kTy - 1) / kTy;
+    p.tiles_y = (p.ny + TY - 1) / TY;
     const int ntiles = p.tiles_x * p.tiles_y;
     const int slots = occupancy() * sm_count();
     if (RANK == 2) {
@@ -580,9 +587,9 @@ struct TmaRunner {
     const int64_t n[3] = {a.g.n[2], a.g.n[1], a.g.n[0]};
     for (int f = 0; f < Op::NF; ++f) {
       cudaError_t e;
-      if ((e = encode<T>(&maps.wide[f], a.in[f], RANK, n, L::W, kTy + 2 * Op::R)) ||
+      if ((e = encode<T>(&maps.wide[f], a.in[f], RANK, n, L::W, TY + 2 * Op::R)) ||
           (e = encode<T>(&maps.rows[f], a.in[f], RANK, n, L::W, Op::R)) ||
-          (e = encode<T>(&maps.cols[f], a.in[f], RANK, n, L::CW, kTy)))
+          (e = encode<T>(&maps.cols[f], a.in[f], RANK, n, L::CW, TY)))
         return e;
     }
     occupancy();
@@ -606,7 +613,7 @@ template <class T> cudaError_t dispatch_t(const StepArgs& a, int* blocks) {
     case kJacobi5: return TmaRunner<OpJacobi5, T, 2>::run(a, {s.prm[0]}, blocks);
     case kStar9r2: return TmaRunner<OpStar9r2, T, 2>::run(a, {s.prm[0]}, blocks);
     case kDiff7: return TmaRunner<OpDiff7, T, 3>::run(a, {s.prm[0]}, blocks);
-    case kSwe: return TmaRunner<OpSwe, T, 2>::run(a, {s.prm[0] * s.prm[2], s.prm[0] * s.prm[1]}, blocks);
+    case kSwe: return TmaRunner<OpSwe, T, 2>::run(a, {-s.prm[0] * s.prm[2], -s.prm[0] * s.prm[1]}, blocks);
     case kLinear: {
       if (s.ndim == 2 && s.radius == 1) {
         OpStarLinear<2, 1> op;

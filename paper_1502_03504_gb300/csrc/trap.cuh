@@ -57,6 +57,8 @@ __device__ __forceinline__ bool outside_dirichlet(const TrapGrid& g, int gy, int
 }
 
 // One tile: k sweeps from src to dst.  smem holds 2 * NF * H * W values of C.
+// Threads walk the window as a 2D grid (threadIdx.x along x in steps of 32,
+// the rest of the block along y), so no cell index is divided.
 template <class Op, class T>
 __device__ __forceinline__ void trap_tile(const Op& op, const T* const* src, T* const* dst,
                                           const TrapGrid& g, int x0, int y0, int TX, int TY,
@@ -65,45 +67,57 @@ __device__ __forceinline__ void trap_tile(const Op& op, const T* const* src, T* 
   constexpr int R = Op::R, NF = Op::NF;
   const int h = R * k;
   const int W = TX + 2 * h, H = TY + 2 * h, HW = W * H;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32, ny_t = blockDim.x / 32;
   C* b0 = smem;
   C* b1 = smem + NF * HW;
-  for (int idx = threadIdx.x; idx < HW; idx += blockDim.x) {
-    const int i = idx % W, j = idx / W;
-    const int gx = x0 - h + i, gy = y0 - h + j;
+  // The whole window lies inside the grid: no boundary rule, no wrap.
+  const bool inside = x0 - h >= 0 && y0 - h >= 0 && x0 + TX + h <= g.nx && y0 + TY + h <= g.ny;
+  for (int j = ty; j < H; j += ny_t) {
+    const int gy = y0 - h + j;
+    for (int i = tx; i < W; i += 32) {
+      const int gx = x0 - h + i;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) b0[f * HW + idx] = halo_read<T>(src[f], g, gy, gx);
+      for (int f = 0; f < NF; ++f)
+        b0[f * HW + j * W + i] = inside ? to_c(__ldcg(src[f] + int64_t(gy) * g.nx + gx))
+                                        : halo_read<T>(src[f], g, gy, gx);
+    }
   }
   __syncthreads();
   for (int s = 1; s <= k; ++s) {
     const C* cur = (s & 1) ? b0 : b1;
     C* nxt = (s & 1) ? b1 : b0;
-    const int lo = s * R, wi = W - 2 * lo, hi = H - 2 * lo;
-    for (int idx = threadIdx.x; idx < wi * hi; idx += blockDim.x) {
-      const int i = lo + idx % wi, j = lo + idx / wi;
-      const int gx = x0 - h + i, gy = y0 - h + j;
-      double v;
-      if (outside_dirichlet(g, gy, gx, &v)) {
+    const int lo = s * R;
+    for (int j = lo + ty; j < H - lo; j += ny_t) {
+      const int gy = y0 - h + j;
+      for (int i = lo + tx; i < W - lo; i += 32) {
+        const int gx = x0 - h + i;
+        double v;
+        if (!inside && outside_dirichlet(g, gy, gx, &v)) {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) nxt[f * HW + j * W + i] = C(v);
-        continue;
+          for (int f = 0; f < NF; ++f) nxt[f * HW + j * W + i] = C(v);
+          continue;
+        }
+        TrapAcc<C, NF> acc{cur, W, HW, i, j};
+        C o[NF];
+        C unused = C(0);
+        op(acc, o, unused);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) nxt[f * HW + j * W + i] = to_storage_precision<T>(o[f]);
       }
-      TrapAcc<C, NF> acc{cur, W, HW, i, j};
-      C o[NF];
-      double unused = 0.0;
-      op(acc, o, unused);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) nxt[f * HW + j * W + i] = to_storage_precision<T>(o[f]);
     }
     __syncthreads();
   }
   const C* fin = (k & 1) ? b1 : b0;
-  for (int idx = threadIdx.x; idx < TX * TY; idx += blockDim.x) {
-    const int i = idx % TX, j = idx / TX;
-    const int gx = x0 + i, gy = y0 + j;
-    if (gx < g.nx && gy < g.ny) {
+  for (int j = ty; j < TY; j += ny_t) {
+    const int gy = y0 + j;
+    if (gy >= g.ny) break;
+    for (int i = tx; i < TX; i += 32) {
+      const int gx = x0 + i;
+      if (gx < g.nx) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f)
-        dst[f][int64_t(gy) * g.nx + gx] = from_c<T>(fin[f * HW + (j + h) * W + (i + h)]);
+        for (int f = 0; f < NF; ++f)
+          dst[f][int64_t(gy) * g.nx + gx] = from_c<T>(fin[f * HW + (j + h) * W + (i + h)]);
+      }
     }
   }
   __syncthreads();
