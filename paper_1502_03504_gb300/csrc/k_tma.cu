@@ -68,10 +68,11 @@ template <class Op, class T> struct TmaParams {
 //          Out-of-range cells arrive as zeros (the Dirichlet-0 halo).
 //   colL, colR   TY x CW slots: wrapped halo columns (periodic x edge tiles)
 //   rowLo, rowHi R x W slots: wrapped halo rows (periodic y edge tiles)
-// After a stage arrives, consumers copy the wrapped slots over the zeros they
-// replace (the periodic halo, BC=CYCLIC of Sec. 3.2); every tap is then a
-// shared load at a compile-time offset from the local element.  Star stencils
-// never read the corner cells, which stay as loaded.
+// Consumers read every tap at a compile-time offset from the local element in
+// the wide box.  Where the periodic halo wraps (BC=CYCLIC of Sec. 3.2), the
+// wrapped halo rows feed the column registers from the row slots, and the
+// warps that read the wrapped halo columns first copy them from the column
+// slots into the box.  Star stencils never read the corner cells.
 template <class T, int TX, int TY, int R, int NF> struct Layout {
   static constexpr int CW = 16 / int(sizeof(T));
   static constexpr int W = TX + 2 * CW;
@@ -114,7 +115,6 @@ __device__ __forceinline__ TileInfo classify(int x0, int y0, int nx, int ny, int
 // register queue q[f][R + dz].
 template <class T, int TX, int TY, int R, int NF, int NQ, int NC>
 struct StageAcc {
-  using L = Layout<T, TX, TY, R, NF>;
   using C = C_t<T>;
   const T* b[NF];
   const C (*col)[NC];  // col[f] + r, so col[f][R + dy] is row r + dy
@@ -128,6 +128,53 @@ struct StageAcc {
   }
   __device__ __forceinline__ int64_t gidx() const { return g; }
 };
+
+// Periodic x edge: copy the wrapped halo columns that this warp's own lanes
+// will read (rows cy0 .. cy0+RY-1) from the column slots into the wide box.
+// Left-halo readers (cx < R) and right-halo readers (nvx-R <= cx < nvx) each
+// sit in a single warp, so a warp-level barrier is enough; the proxy fence
+// orders these shared-memory writes before the stage's next TMA refill.
+template <class T, int TX, int TY, int R, int NF, int RY>
+__device__ __forceinline__ void fix_x_warp(unsigned char* st, const TileInfo& t, int cx, int cy0) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const int lane = threadIdx.x % 32, cxw = cx - lane;  // first column of this warp
+  const bool left = t.xl && cxw == 0;
+  const bool right = t.xr && cxw <= t.nvx - 1 && t.nvx - 1 < cxw + 32;
+  if (!left && !right) return;
+  if (lane < R * RY) {
+    const int d = lane / RY, r = lane % RY;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T* w = reinterpret_cast<T*>(st + f * L::FIELD_B);
+      const T* sl = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_COLL);
+      const T* sr = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_COLR);
+      if (left) w[(R + cy0 + r) * L::W + L::CW - 1 - d] = sl[(cy0 + r) * L::CW + L::CW - 1 - d];
+      if (right) w[(R + cy0 + r) * L::W + L::CW + t.nvx + d] = sr[(cy0 + r) * L::CW + d];
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+}
+
+// Value for the column registers: tile row tr (which may lie in the halo) of
+// column cx, taken from the wide box or, where the periodic halo wraps, from
+// the wrapped row slots.
+template <class T, int TX, int TY, int R, int NF>
+__device__ __forceinline__ C_t<T> column_value(const unsigned char* st, int f, const TileInfo& t,
+                                               int tr, int cx, int ny, bool yw) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const unsigned char* fb = st + f * L::FIELD_B;
+  if (yw) {
+    if (t.yl && tr < 0)  // the low slot holds rows ny-R .. ny-1; y0 = 0 here
+      return to_c(reinterpret_cast<const T*>(fb + L::OFF_ROWLO)[(tr + R) * L::W + L::CW + cx]);
+    const int gy = t.y0 + tr;
+    // The high slot holds rows 0 .. R-1.  Rows further out are read only for
+    // rows below the grid edge, whose results are discarded: clamp in range.
+    if (t.yh && gy >= ny)
+      return to_c(reinterpret_cast<const T*>(fb + L::OFF_ROWHI)[min(gy - ny, R - 1) * L::W + L::CW + cx]);
+  }
+  return to_c(reinterpret_cast<const T*>(fb)[(R + tr) * L::W + L::CW + cx]);
+}
 
 template <int RANK>
 __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* m, int x, int y, int z,
@@ -155,50 +202,6 @@ __device__ __forceinline__ void issue_plane(const TmaMaps<NF>& maps, unsigned ch
     if (t.yl) tma_load<RANK>(w + L::OFF_ROWLO, &maps.rows[f], xw, ny - R, z, bar);
     if (t.yh) tma_load<RANK>(w + L::OFF_ROWHI, &maps.rows[f], xw, 0, z, bar);
   }
-}
-
-// Copy wrapped halo slots over the zero-filled cells of the wide box, order
-// the shared-memory writes before the stage's next TMA refill, and wait until
-// every consumer warp has written its share (mbarrier `fixb`, bounded wait).
-// Returns false if the wait gave up.
-template <class T, int TX, int TY, int R, int NF, int NCONS>
-__device__ __forceinline__ bool fix_halo(unsigned char* st, const TileInfo& t, int ny,
-                                         uint64_t* fixb, uint32_t parity, int* err) {
-  using L = Layout<T, TX, TY, R, NF>;
-#pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    T* w = reinterpret_cast<T*>(st + f * L::FIELD_B);
-    if (t.xl || t.xr) {
-      const T* sl = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_COLL);
-      const T* sr = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_COLR);
-      for (int idx = threadIdx.x; idx < t.nvy * L::CW; idx += NCONS) {
-        const int row = idx / L::CW, c = idx % L::CW;
-        if (t.xl) w[(R + row) * L::W + c] = sl[row * L::CW + c];
-        if (t.xr) w[(R + row) * L::W + L::CW + t.nvx + c] = sr[row * L::CW + c];
-      }
-    }
-    if (t.yl || t.yh) {
-      const T* lo = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_ROWLO);
-      const T* hi = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_ROWHI);
-      for (int idx = threadIdx.x; idx < 2 * R * L::W; idx += NCONS) {
-        const int j = idx / L::W, c = idx % L::W;
-        if (j < R) {
-          // low halo row j holds global row y0 - R + j (< 0 only when y0 = 0);
-          // the low slot holds rows ny - R .. ny - 1
-          if (t.yl && t.y0 - R + j < 0) w[j * L::W + c] = lo[(t.y0 + j) * L::W + c];
-        } else {
-          const int jj = j - R;  // high halo row jj holds global row y0 + nvy + jj
-          const int gy = t.y0 + t.nvy + jj;
-          // the high slot holds rows 0 .. R - 1
-          if (t.yh && gy >= ny) w[(R + t.nvy + jj) * L::W + c] = hi[(gy - ny) * L::W + c];
-        }
-      }
-    }
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  __syncwarp();
-  if (threadIdx.x % 32 == 0) mbar_arrive(fixb);
-  return mbar_wait_bounded(fixb, parity, err);
 }
 
 __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
@@ -258,8 +261,25 @@ __device__ __forceinline__ void column_rows(const Op& op, const unsigned char* s
   if (Op::REDUCES) red += double(rsum);
 }
 
+// One staged 2D tile: wrapped x halo patched by the warps that read it,
+// column registers (wrapped halo rows from the row slots when YW), then rows.
+template <bool YW, bool WRAP, class Op, class T, int TX, int TY, int RY>
+__device__ __forceinline__ void tile2d(const Op& op, unsigned char* st, T* const* out, int nx,
+                                       int ny, const TileInfo& t, int cx, int cy0, double& red) {
+  using C = C_t<T>;
+  constexpr int R = Op::R, NF = Op::NF, NC = RY + 2 * R;
+  if (WRAP && (t.xl || t.xr)) fix_x_warp<T, TX, TY, R, NF, RY>(st, t, cx, cy0);
+  C col[NF][NC];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+      col[f][k] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 - R + k, cx, ny, YW);
+  column_rows<Op, T, TX, TY, RY, 1, NC>(op, st, out, 0, nx, t, cx, cy0, col, nullptr, red);
+}
+
 // ------------------------------------------------------------------ 2D tiles
-template <class Op, class T, int TX, int TY, int RY, int S>
+template <class Op, class T, int TX, int TY, int RY, int S, bool WRAP>
 __global__ void __launch_bounds__(TX * (TY / RY) + 32)
     tma2d_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
   using C = C_t<T>;
@@ -270,7 +290,6 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32)
   unsigned char* smem = align128(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * L::STAGE_B);
   uint64_t* empty = full + S;
-  uint64_t* fixb = empty + S;
   __shared__ volatile int abort_flag;
   __shared__ double red_scratch[NCONS / 32];
 
@@ -279,7 +298,6 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32)
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NCONS / 32);
-      mbar_init(&fixb[s], NCONS / 32);
     }
     abort_flag = 0;
     fence_mbar_init();
@@ -300,7 +318,7 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32)
         }
         if (abort_flag) break;
         const TileInfo t = classify<T, TX, TY, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx,
-                                              p.ny, p.per_x, p.per_y);
+                                              p.ny, WRAP && p.per_x, WRAP && p.per_y);
         issue_plane<T, TX, TY, R, NF, 2>(maps, smem + s * L::STAGE_B, &full[s], t, 0, p.nx, p.ny);
       }
       if (abort_flag) {  // let copies already issued land before the block exits
@@ -312,7 +330,6 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32)
 
   const int cx = tid % TX, cy0 = (tid / TX) * RY, lane = tid % 32;
   double red = 0.0;
-  uint32_t fixph = 0;  // bit s: phase parity of fixb[s]
   int i = 0;
   for (int u = blockIdx.x; u < p.nunits; u += gridDim.x, ++i) {
     const int s = i % S;
@@ -320,24 +337,13 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32)
       abort_flag = 1;
       break;
     }
-    const TileInfo t = classify<T, TX, TY, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx, p.ny,
-                                          p.per_x, p.per_y);
+    const TileInfo t = classify<T, TX, TY, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx,
+                                              p.ny, WRAP && p.per_x, WRAP && p.per_y);
     unsigned char* st = smem + s * L::STAGE_B;
-    if (t.xl || t.xr || t.yl || t.yh) {
-      const bool fixed = fix_halo<T, TX, TY, R, NF, NCONS>(st, t, p.ny, &fixb[s], (fixph >> s) & 1u, p.err);
-      fixph ^= 1u << s;
-      if (!fixed) {
-        abort_flag = 1;
-        break;
-      }
-    }
-    C col[NF][NC];
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-#pragma unroll
-      for (int k = 0; k < NC; ++k)
-        col[f][k] = to_c(reinterpret_cast<const T*>(st + f * L::FIELD_B)[(cy0 + k) * L::W + L::CW + cx]);
-    column_rows<Op, T, TX, TY, RY, 1, NC>(p.op, st, p.out, 0, p.nx, t, cx, cy0, col, nullptr, red);
+    if (WRAP && (t.yl || t.yh))
+      tile2d<true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
+    else
+      tile2d<false, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
@@ -345,11 +351,83 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32)
 }
 
 // ------------------------------------------------------------------ 3D z-march
-template <class Op, class T, int TX, int TY, int RY, int S>
-__global__ void __launch_bounds__(TX * (TY / RY) + 32, 2)
-    tma3d_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
+// Consumer side of the z-march for one tile.  YW: the tile's periodic y halo
+// wraps, so those rows come from the row slots.  XF: x-edge tiles patch their
+// wrapped halo columns per warp.
+template <bool YW, bool XF, class Op, class T, int TX, int TY, int RY, int S>
+__device__ __forceinline__ void march3d(const TmaParams<Op, T>& p, unsigned char* smem,
+                                        uint64_t* full, uint64_t* empty, volatile int* abort_flag,
+                                        const TileInfo& t, int z0, int z1, int np, double& red) {
   using C = C_t<T>;
   constexpr int R = Op::R, NF = Op::NF, NQ = 2 * R + 1, NC = RY + 2 * R;
+  using L = Layout<T, TX, TY, R, NF>;
+  const int tid = threadIdx.x;
+  const int cx = tid % TX, cy0 = (tid / TX) * RY, lane = tid % 32;
+  const int64_t plane = int64_t(p.nx) * p.ny;
+  C q[RY][NF][NQ];
+  bool ok = true;
+
+  auto release = [&](int j) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[j % S]);
+  };
+  // Wait for staged plane j and push its centre values onto each queue.
+  auto shift_in = [&](int j) -> bool {
+    const int s = j % S;
+    if (!mbar_wait_bounded(&full[s], (j / S) & 1, p.err) || *abort_flag) {
+      *abort_flag = 1;
+      return false;
+    }
+    unsigned char* st = smem + s * L::STAGE_B;
+    if (XF) fix_x_warp<T, TX, TY, R, NF, RY>(st, t, cx, cy0);
+#pragma unroll
+    for (int r = 0; r < RY; ++r)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+#pragma unroll
+        for (int k = 0; k < NQ - 1; ++k) q[r][f][k] = q[r][f][k + 1];
+        q[r][f][NQ - 1] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 + r, cx, p.ny, YW);
+      }
+    return true;
+  };
+
+  for (int j = 0; j < 2 * R && ok; ++j) {
+    ok = shift_in(j);
+    if (ok && (j < R || j >= np - R)) release(j);  // outside [z0, z1): centres only
+  }
+  for (int m = 0; ok && m < z1 - z0; ++m) {
+    const int jn = m + 2 * R;
+    ok = shift_in(jn);
+    if (!ok) break;
+    const int jc = m + R;  // plane of the outputs
+    const unsigned char* st = smem + (jc % S) * L::STAGE_B;
+    // column registers of the output plane: strip rows from the queue, the
+    // R rows on either side from the stage
+    C col[NF][NC];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        col[f][k] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 - R + k, cx, p.ny, YW);
+        col[f][R + RY + k] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 + RY + k, cx, p.ny, YW);
+      }
+#pragma unroll
+      for (int r = 0; r < RY; ++r) col[f][R + r] = q[r][f][R];
+    }
+    column_rows<Op, T, TX, TY, RY, NQ, NC>(p.op, st, p.out, int64_t(z0 + m) * plane, p.nx, t, cx,
+                                           cy0, col, q, red);
+    release(jc);
+    if (jn >= np - R) release(jn);  // above z1-1: centres only
+  }
+}
+
+// WRAP: compile the periodic-halo handling (x or y axis periodic).  Grids
+// without a periodic x/y axis use the instance without it, whose consumer
+// code fits the register budget of two blocks per SM.
+template <class Op, class T, int TX, int TY, int RY, int S, bool WRAP>
+__global__ void __launch_bounds__(TX * (TY / RY) + 32, 2)
+    tma3d_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
+  constexpr int R = Op::R, NF = Op::NF;
   using L = Layout<T, TX, TY, R, NF>;
   constexpr int NCONS = TX * (TY / RY);
   static_assert(S >= R + 2, "ring too short for the z window");
@@ -357,7 +435,6 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32, 2)
   unsigned char* smem = align128(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * L::STAGE_B);
   uint64_t* empty = full + S;
-  uint64_t* fixb = empty + S;
   __shared__ volatile int abort_flag;
   __shared__ double red_scratch[NCONS / 32];
 
@@ -365,8 +442,7 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32, 2)
   const int ntiles = p.tiles_x * p.tiles_y;
   const int tile = blockIdx.x % ntiles, zc = blockIdx.x / ntiles;
   const TileInfo t = classify<T, TX, TY, R>((tile % p.tiles_x) * TX, (tile / p.tiles_x) * TY, p.nx,
-                                        p.ny, p.per_x, p.per_y);
-  const bool fix = t.xl || t.xr || t.yl || t.yh;
+                                            p.ny, WRAP && p.per_x, WRAP && p.per_y);
   const int z0 = zc * p.zchunk, z1 = min(p.nz, z0 + p.zchunk);
   const int np = (z1 - z0) + 2 * R;  // planes staged by this block
 
@@ -374,7 +450,6 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32, 2)
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NCONS / 32);
-      mbar_init(&fixb[s], NCONS / 32);
     }
     abort_flag = 0;
     fence_mbar_init();
@@ -399,76 +474,26 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32, 2)
         if (p.per_z) z = wrap(z, p.nz);
         issue_plane<T, TX, TY, R, NF, 3>(maps, smem + s * L::STAGE_B, &full[s], t, z, p.nx, p.ny);
       }
-      if (abort_flag) {
+      if (abort_flag) {  // let copies already issued land before the block exits
         for (int k = max(0, j - S); k < j; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
       }
     }
     return;
   }
 
-  const int cx = tid % TX, cy0 = (tid / TX) * RY, lane = tid % 32;
-  const int64_t plane = int64_t(p.nx) * p.ny;
-  C q[RY][NF][NQ];
   double red = 0.0;
-  bool ok = true;
-
-  auto release = [&](int j) {
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[j % S]);
-  };
-  // Wait for staged plane j, put its wrapped halos in place, and push its
-  // centre values onto each queue.
-  auto shift_in = [&](int j) -> bool {
-    const int s = j % S;
-    if (!mbar_wait_bounded(&full[s], (j / S) & 1, p.err) || abort_flag) {
-      abort_flag = 1;
-      return false;
-    }
-    unsigned char* st = smem + s * L::STAGE_B;
-    if (fix && !fix_halo<T, TX, TY, R, NF, NCONS>(st, t, p.ny, &fixb[s], (j / S) & 1, p.err)) {
-      abort_flag = 1;
-      return false;
-    }
-#pragma unroll
-    for (int r = 0; r < RY; ++r)
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-#pragma unroll
-        for (int k = 0; k < NQ - 1; ++k) q[r][f][k] = q[r][f][k + 1];
-        q[r][f][NQ - 1] =
-            to_c(reinterpret_cast<const T*>(st + f * L::FIELD_B)[(R + cy0 + r) * L::W + L::CW + cx]);
-      }
-    return true;
-  };
-
-  for (int j = 0; j < 2 * R && ok; ++j) {
-    ok = shift_in(j);
-    if (ok && (j < R || j >= np - R)) release(j);  // outside [z0, z1): centres only
-  }
-  for (int m = 0; ok && m < z1 - z0; ++m) {
-    const int jn = m + 2 * R;
-    ok = shift_in(jn);
-    if (!ok) break;
-    const int jc = m + R;  // plane of the outputs
-    const unsigned char* st = smem + (jc % S) * L::STAGE_B;
-    // column registers of the output plane: strip rows from the queue, the
-    // R rows on either side from shared memory
-    C col[NF][NC];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const T* w = reinterpret_cast<const T*>(st + f * L::FIELD_B);
-#pragma unroll
-      for (int k = 0; k < R; ++k) {
-        col[f][k] = to_c(w[(cy0 + k) * L::W + L::CW + cx]);
-        col[f][R + RY + k] = to_c(w[(cy0 + R + RY + k) * L::W + L::CW + cx]);
-      }
-#pragma unroll
-      for (int r = 0; r < RY; ++r) col[f][R + r] = q[r][f][R];
-    }
-    column_rows<Op, T, TX, TY, RY, NQ, NC>(p.op, st, p.out, int64_t(z0 + m) * plane, p.nx, t, cx, cy0, col,
-                                   q, red);
-    release(jc);
-    if (jn >= np - R) release(jn);  // above z1-1: centres only
+  if constexpr (WRAP) {
+    const bool yw = t.yl || t.yh, xf = t.xl || t.xr;
+    if (yw && xf)
+      march3d<true, true, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1, np, red);
+    else if (yw)
+      march3d<true, false, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1, np, red);
+    else if (xf)
+      march3d<false, true, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1, np, red);
+    else
+      march3d<false, false, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1, np, red);
+  } else {
+    march3d<false, false, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1, np, red);
   }
   if (Op::REDUCES) block_accumulate<NCONS>(red, p.partials, red_scratch);
 }
@@ -525,25 +550,26 @@ struct TmaRunner {
   static constexpr int TX = Cfg::TX, TY = Cfg::TY, RY = Cfg::RY, S = Cfg::S;
   using L = Layout<T, TX, TY, Op::R, Op::NF>;
   static constexpr int THREADS = TX * (TY / RY) + 32;
-  static constexpr size_t SMEM = size_t(S) * L::STAGE_B + 3 * S * sizeof(uint64_t) + 128;
+  static constexpr size_t SMEM = size_t(S) * L::STAGE_B + 2 * S * sizeof(uint64_t) + 128;
 
-  static auto kernel() {
-    if constexpr (RANK == 2) return &tma2d_kernel<Op, T, TX, TY, RY, S>;
-    else return &tma3d_kernel<Op, T, TX, TY, RY, S>;
+  template <bool WRAP> static auto kernel_w() {
+    if constexpr (RANK == 2) return &tma2d_kernel<Op, T, TX, TY, RY, S, WRAP>;
+    else return &tma3d_kernel<Op, T, TX, TY, RY, S, WRAP>;
   }
 
-  static int occupancy() {
+  template <bool WRAP> static int occupancy_w() {
     static int occ = -1;
     if (occ < 0) {
-      cudaFuncSetAttribute(kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM));
+      cudaFuncSetAttribute(kernel_w<WRAP>(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM));
       int o = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel(), THREADS, SMEM) !=
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel_w<WRAP>(), THREADS, SMEM) !=
           cudaSuccess)
         o = 1;
       occ = o > 0 ? o : 1;
     }
     return occ;
   }
+  static int occupancy(bool wrap) { return wrap ? occupancy_w<true>() : occupancy_w<false>(); }
 
   template <class P>
   static void geometry(const StepArgs& a, P& p, int* blocks) {
@@ -557,7 +583,7 @@ struct TmaRunner {
     p.tiles_x = (p.nx + TX - 1) / TX;
     p.tiles_y = (p.ny + TY - 1) / TY;
     const int ntiles = p.tiles_x * p.tiles_y;
-    const int slots = occupancy() * sm_count();
+    const int slots = occupancy(p.per_x || p.per_y) * sm_count();
     if (RANK == 2) {
       p.nunits = ntiles;
       p.zchunk = 1;
@@ -592,8 +618,8 @@ struct TmaRunner {
           (e = encode<T>(&maps.cols[f], a.in[f], RANK, n, L::CW, TY)))
         return e;
     }
-    occupancy();
-    kernel()<<<blocks, THREADS, SMEM, a.stream>>>(maps, p);
+    if (p.per_x || p.per_y) kernel_w<true>()<<<blocks, THREADS, SMEM, a.stream>>>(maps, p);
+    else kernel_w<false>()<<<blocks, THREADS, SMEM, a.stream>>>(maps, p);
     count_launches(1);
     return cudaGetLastError();
   }
