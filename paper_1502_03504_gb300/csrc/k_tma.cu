@@ -386,7 +386,9 @@ __device__ __forceinline__ void march3d(const TmaParams<Op, T>& p, unsigned char
       for (int f = 0; f < NF; ++f) {
 #pragma unroll
         for (int k = 0; k < NQ - 1; ++k) q[r][f][k] = q[r][f][k + 1];
-        q[r][f][NQ - 1] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 + r, cx, p.ny, YW);
+        // strip rows wrap only on a ragged periodic tile
+        q[r][f][NQ - 1] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 + r, cx, p.ny,
+                                                         YW && t.nvy < TY);
       }
     return true;
   };
@@ -544,6 +546,9 @@ int sm_count() {
   return n;
 }
 
+constexpr int kZWaves = 3;
+constexpr int kMinChunk = 48;
+
 template <class Op, class T, int RANK>
 struct TmaRunner {
   using Cfg = TmaCfg<T, RANK, Op::NF>;
@@ -589,8 +594,14 @@ struct TmaRunner {
       p.zchunk = 1;
       *blocks = std::min(ntiles, slots);
     } else {
-      // Split z so that the blocks fill the resident slots once.
-      int nzc = std::max(1, slots / ntiles);
+      // Split z into chunks.  About kZWaves waves of blocks keep every
+      // resident slot busy (later blocks take the slots of blocks that finish
+      // early; edge tiles of periodic grids cost more per plane), but chunks
+      // stay at least kMinChunk planes long (each chunk stages 2R extra
+      // planes); short grids get at most one wave (a few blocks past a full
+      // wave would double the time).
+      const int one_wave = std::max(1, slots / ntiles);
+      int nzc = std::max(one_wave, std::min((kZWaves * slots) / ntiles, p.nz / kMinChunk));
       nzc = std::min(nzc, p.nz);
       p.zchunk = (p.nz + nzc - 1) / nzc;
       nzc = (p.nz + p.zchunk - 1) / p.zchunk;

@@ -83,3 +83,19 @@ def test_periodic_axis_shorter_than_radius(lope):
     s = lope.Stencil.builtin("star9r2", 0.1)
     with pytest.raises(lope.LopeError, match="periodic axis"):
         lope.lope_apply(g.handle, s.handle, [16], [32], None, 1, None)
+
+
+def test_set_option_validation(lope):
+    with pytest.raises(lope.LopeError, match="unknown option"):
+        lope.lope_set_option("no_such_option", 1)
+    with pytest.raises(lope.LopeError, match="range"):
+        lope.lope_set_option("wait_limit_ms", 0)
+    lope.lope_set_option("wait_limit_ms", 1000)
+    lope.lope_set_option("batch_skip_arrive", -1)
+
+
+def test_noalloc_reduce_rejects_bad_arguments_without_gpu(lope):
+    with pytest.raises(lope.LopeError, match="2\\^28"):
+        lope.lope_reduce_noalloc(0, lope.DTYPES["f32"], 16, 0, (1 << 28) + 1, 32, None)
+    with pytest.raises(lope.LopeError, match="bad reduction"):
+        lope.lope_reduce_noalloc(7, lope.DTYPES["f32"], 16, 0, 10, 32, None)

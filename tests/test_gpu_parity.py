@@ -317,3 +317,41 @@ def test_full_size_swe_4096_200_sampled(lope, orc, dtype):
     pts = [(0, 0), (4095, 4095), (2048, 17), (9, 3000)]
     _sampled_check(lope, orc, "swe_cgrid", [dt, gr, H], shape, [0, 0], T, 1, dtype, 3, outs,
                    list(stored), pts, tol)
+
+
+# ------------------------------------------------------------------ planner / autotuner
+def test_autotune_choice_is_bitwise_equal(lope):
+    shape = (300, 512)
+    u0, _ = to_device(LI.uniform_field(15, shape), "f32")
+    g = _grid(lope, shape, "f32", 1, [0, 0])
+    st = lope.Stencil.builtin("jacobi5", 0.2)
+    ref = _run(lope, g, st, u0, 12, _launch(lope, TMA))
+    out, work = torch.empty_like(u0), torch.empty_like(u0)
+    best, ms = lope.autotune(g, st, u0, out, work, 12)
+    assert best.path in (TMA, TRAP, DIRECT) and ms > 0
+    # the remembered choice is what lope_apply now uses; any choice is bitwise equal
+    assert torch.equal(_run(lope, g, st, u0, 12), ref)
+
+
+def test_bf16_tma_jacobi5_vs_oracle(lope, orc):
+    shape, c, T = (96, 128), 0.2, 10
+    u0, u0s = to_device(LI.uniform_field(16, shape), "bf16")
+    g = _grid(lope, shape, "bf16", 1, [0, 1])
+    st = lope.Stencil.builtin("jacobi5", c)
+    want = orc.apply(u0s, "jacobi5", [c], T, bc=[0, 1])
+    for launch in (_launch(lope, TMA), _launch(lope, TRAP, 64, 16, 3), _launch(lope, DIRECT)):
+        got = to_host(_run(lope, g, st, u0, T, launch))
+        assert np.max(np.abs(got - want)) <= bound_bf16(T, 1.0, 7), launch
+
+
+def test_graph_replay_matches_direct_launches(lope):
+    shape = (256, 256)
+    u0, _ = to_device(LI.uniform_field(17, shape), "f32")
+    g = _grid(lope, shape, "f32", 1, [1, 1])
+    st = lope.Stencil.builtin("jacobi5", 0.2)
+    direct = _run(lope, g, st, u0, 40, _launch(lope, TMA, graph=-1))
+    out, work = torch.empty_like(u0), torch.empty_like(u0)
+    for _ in range(3):  # capture once, replay twice
+        lope.apply(g, st, u0, out=out, work=work, nsteps=40, launch=_launch(lope, TMA, graph=1))
+    torch.cuda.synchronize()
+    assert torch.equal(out, direct)
