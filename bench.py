@@ -51,6 +51,17 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(value, pg, device):
+    """Largest value over all ranks (the job's wall time is its slowest rank)."""
+    if pg is None:
+        return value
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -211,7 +222,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--profile", default=None,
                     help="run one kernel workload for --steps launches and exit (for ncu): "
-                         "diff7:N, diff7p:N, star9r2:N, jacobi5:N, swe:N, swebf16:N")
+                         "diff7:N, diff7p:N, star9r2:N, jacobi5:N, swe:N, swebf16:N, with an "
+                         "optional boundary spec per axis, slowest first, e.g. diff7:512:DDP "
+                         "(D Dirichlet 0, P periodic)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -283,33 +296,50 @@ def main():
     ms = start.elapsed_time(end)
     t3 = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
     t2 = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, pg, dev)
     upd_step = UPD3 + UPD2
     value = upd_step * args.steps * ws / (ms / 1e3)
 
-    # ---------------- end to end: host buffers, copies inside the timed region
+    # ---------------- end to end: host buffers, copies inside the timed region.
+    # Copies run on a second stream and overlap the other grid's sweeps:
+    # H2D(3D) -> sweeps(3D) -> D2H(3D), H2D(2D) -> sweeps(2D) -> D2H(2D).
     h_o3 = torch.empty_like(u3_h).pin_memory()
     h_o2 = torch.empty_like(u2_h).pin_memory()
+    copy = torch.cuda.Stream(dev)
     e2e_steps = max(2, args.steps // 4)
+
+    def ev_():
+        return torch.cuda.Event()
+
+    def e2e_step():
+        in3, in2, done3, done2 = ev_(), ev_(), ev_(), ev_()
+        with torch.cuda.stream(copy):
+            copy.wait_stream(stream)  # previous step's sweeps no longer read u3/u2
+            u3.copy_(u3_h, non_blocking=True)
+            in3.record(copy)
+            u2.copy_(u2_h, non_blocking=True)
+            in2.record(copy)
+        stream.wait_event(in3)
+        L.apply(g3, s3, u3, out=o3, work=w3, nsteps=T3)
+        done3.record(stream)
+        stream.wait_event(in2)
+        L.apply(g2, s2, u2, out=o2, work=w2, nsteps=T2)
+        done2.record(stream)
+        with torch.cuda.stream(copy):
+            copy.wait_event(done3)
+            h_o3.copy_(o3, non_blocking=True)
+            copy.wait_event(done2)
+            h_o2.copy_(o2, non_blocking=True)
+        stream.wait_stream(copy)  # the step ends when its results are on the host
+
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(e2e_steps):
-        u3.copy_(u3_h, non_blocking=True)
-        u2.copy_(u2_h, non_blocking=True)
-        step()
-        h_o3.copy_(o3, non_blocking=True)
-        h_o2.copy_(o2, non_blocking=True)
+        e2e_step()
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if pg:
-        t = torch.tensor([e2e_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
     e2e = {"value": upd_step * e2e_steps * ws / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": u3.numel() * 4 + u2.numel() * 4,
            "d2h_bytes_per_step": o3.numel() * 4 + o2.numel() * 4}
@@ -380,14 +410,19 @@ def run_profile(args):
     from paper_1502_03504_gb300 import build as B
 
     B.build()
-    name, n = args.profile.split(":")
-    n = int(n)
+    parts = args.profile.split(":")
+    name = parts[0]
+    dims = [int(x) for x in parts[1].split("x")]
+    n = dims[0]
+    spec = parts[2] if len(parts) > 2 else None
     dev = torch.device("cuda", 0)
     if name in ("diff7", "diff7p"):
-        shape, st, halo, pts = (n, n, n), L.Stencil.builtin("diff7", C3), 1, n ** 3
+        shape = tuple(dims) if len(dims) == 3 else (n, n, n)
+        st, halo, pts = L.Stencil.builtin("diff7", C3), 1, int(np.prod(shape))
         kind, nf, dtype, bpp = ("dirichlet" if name == "diff7" else "periodic"), 1, "f32", 8
     elif name in ("star9r2", "jacobi5"):
-        shape, halo, pts = (n, n), 2 if name == "star9r2" else 1, n * n
+        shape = tuple(dims) if len(dims) == 2 else (n, n)
+        halo, pts = 2 if name == "star9r2" else 1, int(np.prod(shape))
         st = L.Stencil.builtin(name, 0.1 if name == "star9r2" else 0.2)
         kind, nf, dtype, bpp = "periodic", 1, "f32", 8
     elif name in ("swe", "swebf16"):
@@ -398,7 +433,9 @@ def run_profile(args):
     else:
         raise SystemExit(f"unknown profile case {name}")
     g = L.Grid(shape, dtype, halo=halo, nfields=nf)
-    if kind == "dirichlet":
+    if spec:
+        g.set_boundaries([0 if c == "P" else 1 for c in spec])
+    elif kind == "dirichlet":
         g.set_boundary(kind="dirichlet", value=0.0)
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dtype]
     fields = [torch.from_numpy(LI.uniform(1001, pts, k * pts).astype(np.float32).reshape(shape))

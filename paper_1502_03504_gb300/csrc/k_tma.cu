@@ -261,20 +261,71 @@ __device__ __forceinline__ void column_rows(const Op& op, const unsigned char* s
   if (Op::REDUCES) red += double(rsum);
 }
 
+// The R column values above (lo) and below (hi) a thread's strip of RY rows.
+// `simple` (decided once per tile): the tile is not ragged in y and its high
+// halo, if it wraps, wraps whole; then only row group 0 reads the low row slot
+// and only the last row group the high one, a warp-uniform choice.  Other
+// wrapped tiles take column_value for each row.
+template <class T, int TX, int TY, int R, int NF, int RY, bool YW>
+__device__ __forceinline__ void edge_rows(const unsigned char* st, int f, const TileInfo& t, int cx,
+                                          int cy0, int ny, bool simple, C_t<T>* lo, C_t<T>* hi) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const unsigned char* fb = st + f * L::FIELD_B;
+  const T* box = reinterpret_cast<const T*>(fb);
+  if (!YW) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      lo[k] = to_c(box[(cy0 + k) * L::W + L::CW + cx]);
+      hi[k] = to_c(box[(cy0 + R + RY + k) * L::W + L::CW + cx]);
+    }
+  } else if (simple) {
+    const T* lsrc = (t.yl && cy0 == 0) ? reinterpret_cast<const T*>(fb + L::OFF_ROWLO)
+                                       : box + cy0 * L::W;
+    const T* hsrc = (t.yh && cy0 + RY == TY) ? reinterpret_cast<const T*>(fb + L::OFF_ROWHI)
+                                             : box + (cy0 + R + RY) * L::W;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      lo[k] = to_c(lsrc[k * L::W + L::CW + cx]);
+      hi[k] = to_c(hsrc[k * L::W + L::CW + cx]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      lo[k] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 - R + k, cx, ny, true);
+      hi[k] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 + RY + k, cx, ny, true);
+    }
+  }
+}
+
+template <int TY>
+__device__ __forceinline__ bool simple_y(const TileInfo& t, int ny) {
+  return t.nvy == TY && (!t.yh || t.y0 + TY == ny);
+}
+
 // One staged 2D tile: wrapped x halo patched by the warps that read it,
 // column registers (wrapped halo rows from the row slots when YW), then rows.
-template <bool YW, bool WRAP, class Op, class T, int TX, int TY, int RY>
+template <bool YW, bool SIMPLE, bool WRAP, class Op, class T, int TX, int TY, int RY>
 __device__ __forceinline__ void tile2d(const Op& op, unsigned char* st, T* const* out, int nx,
                                        int ny, const TileInfo& t, int cx, int cy0, double& red) {
   using C = C_t<T>;
   constexpr int R = Op::R, NF = Op::NF, NC = RY + 2 * R;
+  using L = Layout<T, TX, TY, R, NF>;
   if (WRAP && (t.xl || t.xr)) fix_x_warp<T, TX, TY, R, NF, RY>(st, t, cx, cy0);
+  constexpr bool simple = !YW || SIMPLE;
   C col[NF][NC];
 #pragma unroll
-  for (int f = 0; f < NF; ++f)
+  for (int f = 0; f < NF; ++f) {
+    edge_rows<T, TX, TY, R, NF, RY, YW>(st, f, t, cx, cy0, ny, simple, &col[f][0], &col[f][R + RY]);
+    const T* box = reinterpret_cast<const T*>(st + f * L::FIELD_B);
+    if (simple) {
 #pragma unroll
-    for (int k = 0; k < NC; ++k)
-      col[f][k] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 - R + k, cx, ny, YW);
+      for (int r = 0; r < RY; ++r) col[f][R + r] = to_c(box[(R + cy0 + r) * L::W + L::CW + cx]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < RY; ++r)
+        col[f][R + r] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 + r, cx, ny, true);
+    }
+  }
   column_rows<Op, T, TX, TY, RY, 1, NC>(op, st, out, 0, nx, t, cx, cy0, col, nullptr, red);
 }
 
@@ -340,10 +391,12 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32)
     const TileInfo t = classify<T, TX, TY, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx,
                                               p.ny, WRAP && p.per_x, WRAP && p.per_y);
     unsigned char* st = smem + s * L::STAGE_B;
-    if (WRAP && (t.yl || t.yh))
-      tile2d<true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
+    if (!WRAP || !(t.yl || t.yh))
+      tile2d<false, true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
+    else if (simple_y<TY>(t, p.ny))
+      tile2d<true, true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
     else
-      tile2d<false, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
+      tile2d<true, false, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
@@ -354,7 +407,7 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32)
 // Consumer side of the z-march for one tile.  YW: the tile's periodic y halo
 // wraps, so those rows come from the row slots.  XF: x-edge tiles patch their
 // wrapped halo columns per warp.
-template <bool YW, bool XF, class Op, class T, int TX, int TY, int RY, int S>
+template <bool YW, bool XF, bool SIMPLE, class Op, class T, int TX, int TY, int RY, int S>
 __device__ __forceinline__ void march3d(const TmaParams<Op, T>& p, unsigned char* smem,
                                         uint64_t* full, uint64_t* empty, volatile int* abort_flag,
                                         const TileInfo& t, int z0, int z1, int np, double& red) {
@@ -364,6 +417,7 @@ __device__ __forceinline__ void march3d(const TmaParams<Op, T>& p, unsigned char
   const int tid = threadIdx.x;
   const int cx = tid % TX, cy0 = (tid / TX) * RY, lane = tid % 32;
   const int64_t plane = int64_t(p.nx) * p.ny;
+  constexpr bool simple = !YW || SIMPLE;  // strip rows never wrap
   C q[RY][NF][NQ];
   bool ok = true;
 
@@ -383,13 +437,23 @@ __device__ __forceinline__ void march3d(const TmaParams<Op, T>& p, unsigned char
 #pragma unroll
     for (int r = 0; r < RY; ++r)
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
+      for (int f = 0; f < NF; ++f)
 #pragma unroll
         for (int k = 0; k < NQ - 1; ++k) q[r][f][k] = q[r][f][k + 1];
-        // strip rows wrap only on a ragged periodic tile
-        q[r][f][NQ - 1] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 + r, cx, p.ny,
-                                                         YW && t.nvy < TY);
+    if (simple) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T* box = reinterpret_cast<const T*>(st + f * L::FIELD_B);
+#pragma unroll
+        for (int r = 0; r < RY; ++r) q[r][f][NQ - 1] = to_c(box[(R + cy0 + r) * L::W + L::CW + cx]);
       }
+    } else {  // ragged periodic tile: strip rows past the grid edge wrap
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+          q[r][f][NQ - 1] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 + r, cx, p.ny, true);
+    }
     return true;
   };
 
@@ -408,11 +472,8 @@ __device__ __forceinline__ void march3d(const TmaParams<Op, T>& p, unsigned char
     C col[NF][NC];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-#pragma unroll
-      for (int k = 0; k < R; ++k) {
-        col[f][k] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 - R + k, cx, p.ny, YW);
-        col[f][R + RY + k] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 + RY + k, cx, p.ny, YW);
-      }
+      edge_rows<T, TX, TY, R, NF, RY, YW>(st, f, t, cx, cy0, p.ny, simple, &col[f][0],
+                                          &col[f][R + RY]);
 #pragma unroll
       for (int r = 0; r < RY; ++r) col[f][R + r] = q[r][f][R];
     }
@@ -484,19 +545,25 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32, 2)
   }
 
   double red = 0.0;
+#define LOPE_MARCH(YW, XF, SIMPLE) \
+  march3d<YW, XF, SIMPLE, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1, np, red)
   if constexpr (WRAP) {
     const bool yw = t.yl || t.yh, xf = t.xl || t.xr;
-    if (yw && xf)
-      march3d<true, true, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1, np, red);
-    else if (yw)
-      march3d<true, false, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1, np, red);
-    else if (xf)
-      march3d<false, true, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1, np, red);
-    else
-      march3d<false, false, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1, np, red);
+    const bool simple = simple_y<TY>(t, p.ny);
+    if (!yw) {
+      if (xf) LOPE_MARCH(false, true, true);
+      else LOPE_MARCH(false, false, true);
+    } else if (simple) {
+      if (xf) LOPE_MARCH(true, true, true);
+      else LOPE_MARCH(true, false, true);
+    } else {
+      if (xf) LOPE_MARCH(true, true, false);
+      else LOPE_MARCH(true, false, false);
+    }
   } else {
-    march3d<false, false, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1, np, red);
+    LOPE_MARCH(false, false, true);
   }
+#undef LOPE_MARCH
   if (Op::REDUCES) block_accumulate<NCONS>(red, p.partials, red_scratch);
 }
 
