@@ -44,6 +44,55 @@ __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, 
 __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Two FP32 values in one 64-bit register, operated on by the packed f32x2
+// instructions of sm_100-family GPUs (each lane is an IEEE round-to-nearest
+// operation, so a pair gives bitwise the results of two scalar operations).
+// Local functions written against add/sub/mul/fma_ and C(constant) run
+// unchanged on pairs: a kernel then computes two adjacent columns at once.
+struct F2 {
+  uint64_t v;
+  F2() = default;
+  __device__ __forceinline__ explicit F2(float a) {
+    asm("mov.b64 %0, {%1, %1};" : "=l"(v) : "f"(a));
+  }
+  __device__ __forceinline__ static F2 make(float lo, float hi) {
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+  }
+  __device__ __forceinline__ float lo() const {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return a;
+  }
+  __device__ __forceinline__ float hi() const {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return b;
+  }
+};
+
+__device__ __forceinline__ F2 add(F2 a, F2 b) {
+  F2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+__device__ __forceinline__ F2 sub(F2 a, F2 b) {
+  F2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+__device__ __forceinline__ F2 mul(F2 a, F2 b) {
+  F2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+__device__ __forceinline__ F2 fma_(F2 a, F2 b, F2 c) {
+  F2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return d;
+}
+
 // ---------------------------------------------------------------- timers / waits
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
@@ -160,6 +209,7 @@ struct Coef {
   __host__ __device__ Coef(double v) : d(v), f(float(v)) {}
   __device__ __forceinline__ float get(float) const { return f; }
   __device__ __forceinline__ double get(double) const { return d; }
+  __device__ __forceinline__ F2 get(F2) const { return F2(f); }
 };
 
 // ---------------------------------------------------------------- local functions

@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "device_common.cuh"
 
@@ -37,10 +38,10 @@ namespace {
 template <class T> struct TmaTx { static constexpr int TX = 64; };
 template <> struct TmaTx<double> { static constexpr int TX = 32; };
 
-template <class T, int RANK, int NF> struct TmaCfg {
+template <class T, int RANK, int NF, bool PAIR> struct TmaCfg {
   static constexpr int TX = TmaTx<T>::TX;
   static constexpr int TY = (RANK == 2 && NF == 1) ? 64 : 32;
-  static constexpr int RY = RANK == 2 ? 16 : 8;
+  static constexpr int RY = PAIR ? (NF == 1 ? 8 : 4) : (RANK == 2 ? 16 : 8);
   static constexpr int S = RANK == 3 ? 8 : 3;
 };
 
@@ -329,14 +330,135 @@ __device__ __forceinline__ void tile2d(const Op& op, unsigned char* st, T* const
   column_rows<Op, T, TX, TY, RY, 1, NC>(op, st, out, 0, nx, t, cx, cy0, col, nullptr, red);
 }
 
-// ------------------------------------------------------------------ 2D tiles
-template <class Op, class T, int TX, int TY, int RY, int S, bool WRAP>
-__global__ void __launch_bounds__(TX * (TY / RY) + 32)
-    tma2d_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
-  using C = C_t<T>;
+// ------------------------------------------------------------------ column pairs
+// Paired consumers (FP32/BF16 storage): each thread computes two adjacent
+// columns cx2, cx2+1 with the packed f32x2 instructions.  Pair loads and
+// stores are 8 bytes (FP32) or 4 bytes (BF16) and aligned, since cx2, CW and
+// the box width are even.  x taps of radius <= 2 come from the aligned pairs
+// left (cx2-2, cx2-1) and right (cx2+2, cx2+3) of the centre pair.
+__device__ __forceinline__ F2 ld_pair(const float* p) {
+  F2 r;
+  r.v = *reinterpret_cast<const uint64_t*>(p);
+  return r;
+}
+__device__ __forceinline__ F2 ld_pair(const __nv_bfloat16* p) {
+  const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  return F2::make(f.x, f.y);
+}
+__device__ __forceinline__ void st_pair(float* p, F2 v) { *reinterpret_cast<uint64_t*>(p) = v.v; }
+__device__ __forceinline__ void st_pair(__nv_bfloat16* p, F2 v) {
+  __nv_bfloat162 b;
+  b.x = __float2bfloat16_rn(v.lo());
+  b.y = __float2bfloat16_rn(v.hi());
+  *reinterpret_cast<__nv_bfloat162*>(p) = b;
+}
+
+template <class T, int TX, int TY, int R, int NF, int NC>
+struct PairAcc {
+  static_assert(R <= 2, "paired taps reach two columns");
+  const T* b[NF];      // centre pair of this row in the wide box
+  const F2 (*col)[NC];
+  int r;
+  int64_t g;
+  __device__ __forceinline__ F2 operator()(int f, int dx, int dy, int) const {
+    if (dx == 0) return col[f][r + R + dy];
+    if (dx == -2) return ld_pair(b[f] - 2);
+    if (dx == 2) return ld_pair(b[f] + 2);
+    const F2 c = col[f][r + R];
+    if (dx == -1) return F2::make(ld_pair(b[f] - 2).hi(), c.lo());
+    return F2::make(c.hi(), ld_pair(b[f] + 2).lo());
+  }
+  __device__ __forceinline__ int64_t gidx() const { return g; }
+};
+
+// Pair value of tile row tr for the column registers: from the wide box or,
+// where the periodic y halo wraps, from the row slots (as column_value).
+template <class T, int TX, int TY, int R, int NF>
+__device__ __forceinline__ F2 column_pair(const unsigned char* st, int f, const TileInfo& t, int tr,
+                                          int cx2, int ny) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const unsigned char* fb = st + f * L::FIELD_B;
+  if (t.yl && tr < 0)
+    return ld_pair(reinterpret_cast<const T*>(fb + L::OFF_ROWLO) + (tr + R) * L::W + L::CW + cx2);
+  const int gy = t.y0 + tr;
+  if (t.yh && gy >= ny)
+    return ld_pair(reinterpret_cast<const T*>(fb + L::OFF_ROWHI) + min(gy - ny, R - 1) * L::W +
+                   L::CW + cx2);
+  return ld_pair(reinterpret_cast<const T*>(fb) + (R + tr) * L::W + L::CW + cx2);
+}
+
+// Copy the wrapped halo columns of rows cy0 .. cy0+RY-1 from the column slots
+// into the wide box (as fix_x_warp); `left`/`right` say which sides this warp
+// reads.
+template <class T, int TX, int TY, int R, int NF, int RY>
+__device__ __forceinline__ void fix_x_rows(unsigned char* st, const TileInfo& t, int cy0, bool left,
+                                           bool right) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const int lane = threadIdx.x % 32;
+  if (lane < R * RY) {
+    const int d = lane / RY, r = lane % RY;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T* w = reinterpret_cast<T*>(st + f * L::FIELD_B);
+      const T* sl = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_COLL);
+      const T* sr = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_COLR);
+      if (left) w[(R + cy0 + r) * L::W + L::CW - 1 - d] = sl[(cy0 + r) * L::CW + L::CW - 1 - d];
+      if (right) w[(R + cy0 + r) * L::W + L::CW + t.nvx + d] = sr[(cy0 + r) * L::CW + d];
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+}
+
+// One staged 2D tile on paired consumers: a warp covers a whole row group of
+// TX = 64 columns, so it owns both wrapped halo column blocks of its rows.
+// YW: the tile's periodic y halo wraps; all such tiles take the general
+// column_pair path (2D edge tiles are a few percent of the tiles).
+template <bool YW, bool WRAP, class Op, class T, int TX, int TY, int RY>
+__device__ __forceinline__ void tile2d_pair(const Op& op, unsigned char* st, T* const* out, int nx,
+                                            int ny, const TileInfo& t, int cx2, int cy0) {
   constexpr int R = Op::R, NF = Op::NF, NC = RY + 2 * R;
   using L = Layout<T, TX, TY, R, NF>;
-  constexpr int NCONS = TX * (TY / RY);
+  static_assert(TX == 64, "a warp of pairs spans the tile");
+  if (WRAP && (t.xl || t.xr)) fix_x_rows<T, TX, TY, R, NF, RY>(st, t, cy0, t.xl, t.xr);
+  F2 col[NF][NC];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const T* box = reinterpret_cast<const T*>(st + f * L::FIELD_B);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      if (YW) col[f][k] = column_pair<T, TX, TY, R, NF>(st, f, t, cy0 - R + k, cx2, ny);
+      else col[f][k] = ld_pair(box + (cy0 + k) * L::W + L::CW + cx2);
+    }
+  }
+  const bool xvalid = cx2 < t.nvx;  // nvx is even: a pair is all valid or all invalid
+  const int64_t base = int64_t(t.y0 + cy0) * nx + t.x0 + cx2;
+#pragma unroll
+  for (int r = 0; r < RY; ++r) {
+    PairAcc<T, TX, TY, R, NF, NC> acc;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      acc.b[f] = reinterpret_cast<const T*>(st + f * L::FIELD_B) + (R + cy0 + r) * L::W + L::CW + cx2;
+    acc.col = col;
+    acc.r = r;
+    acc.g = 0;
+    F2 o[NF];
+    F2 unused(0.f);
+    op(acc, o, unused);
+    if (xvalid && cy0 + r < t.nvy) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) st_pair(out[f] + base + int64_t(r) * nx, o[f]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ 2D tiles
+template <class Op, class T, int TX, int TY, int RY, int S, bool WRAP, bool PAIR>
+__global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32)
+    tma2d_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
+  constexpr int R = Op::R, NF = Op::NF;
+  using L = Layout<T, TX, TY, R, NF>;
+  constexpr int NCONS = (PAIR ? TX / 2 : TX) * (TY / RY);
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = align128(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * L::STAGE_B);
@@ -379,7 +501,8 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32)
     return;
   }
 
-  const int cx = tid % TX, cy0 = (tid / TX) * RY, lane = tid % 32;
+  constexpr int CPR = PAIR ? TX / 2 : TX;  // consumer threads per row group
+  const int cx = (tid % CPR) * (PAIR ? 2 : 1), cy0 = (tid / CPR) * RY, lane = tid % 32;
   double red = 0.0;
   int i = 0;
   for (int u = blockIdx.x; u < p.nunits; u += gridDim.x, ++i) {
@@ -391,12 +514,19 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32)
     const TileInfo t = classify<T, TX, TY, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx,
                                               p.ny, WRAP && p.per_x, WRAP && p.per_y);
     unsigned char* st = smem + s * L::STAGE_B;
-    if (!WRAP || !(t.yl || t.yh))
-      tile2d<false, true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
-    else if (simple_y<TY>(t, p.ny))
-      tile2d<true, true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
-    else
-      tile2d<true, false, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
+    // 2D edge tiles are a few percent of the tiles: one general instance for
+    // all of them keeps the persistent loop's code small.
+    if constexpr (PAIR) {
+      if (!WRAP || !(t.yl || t.yh))
+        tile2d_pair<false, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0);
+      else
+        tile2d_pair<true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0);
+    } else {
+      if (!WRAP || !(t.yl || t.yh))
+        tile2d<false, true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
+      else
+        tile2d<true, false, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
@@ -618,14 +748,17 @@ constexpr int kMinChunk = 48;
 
 template <class Op, class T, int RANK>
 struct TmaRunner {
-  using Cfg = TmaCfg<T, RANK, Op::NF>;
+  // Paired consumers for 2D FP32/BF16 local functions without reductions.
+  static constexpr bool PAIR = RANK == 2 && !std::is_same<T, double>::value && !Op::REDUCES &&
+                               Op::R <= 2 && TmaTx<T>::TX == 64;
+  using Cfg = TmaCfg<T, RANK, Op::NF, PAIR>;
   static constexpr int TX = Cfg::TX, TY = Cfg::TY, RY = Cfg::RY, S = Cfg::S;
   using L = Layout<T, TX, TY, Op::R, Op::NF>;
-  static constexpr int THREADS = TX * (TY / RY) + 32;
+  static constexpr int THREADS = (PAIR ? TX / 2 : TX) * (TY / RY) + 32;
   static constexpr size_t SMEM = size_t(S) * L::STAGE_B + 2 * S * sizeof(uint64_t) + 128;
 
   template <bool WRAP> static auto kernel_w() {
-    if constexpr (RANK == 2) return &tma2d_kernel<Op, T, TX, TY, RY, S, WRAP>;
+    if constexpr (RANK == 2) return &tma2d_kernel<Op, T, TX, TY, RY, S, WRAP, PAIR>;
     else return &tma3d_kernel<Op, T, TX, TY, RY, S, WRAP>;
   }
 
