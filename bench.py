@@ -416,10 +416,11 @@ def run_profile(args):
     n = dims[0]
     spec = parts[2] if len(parts) > 2 else None
     dev = torch.device("cuda", 0)
-    if name in ("diff7", "diff7p"):
+    if name in ("diff7", "diff7p", "diff7bf16"):
         shape = tuple(dims) if len(dims) == 3 else (n, n, n)
         st, halo, pts = L.Stencil.builtin("diff7", C3), 1, int(np.prod(shape))
-        kind, nf, dtype, bpp = ("dirichlet" if name == "diff7" else "periodic"), 1, "f32", 8
+        kind, nf = ("periodic" if name == "diff7p" else "dirichlet"), 1
+        dtype, bpp = ("bf16", 4) if name == "diff7bf16" else ("f32", 8)
     elif name in ("star9r2", "jacobi5"):
         shape = tuple(dims) if len(dims) == 2 else (n, n)
         halo, pts = 2 if name == "star9r2" else 1, int(np.prod(shape))

@@ -41,7 +41,7 @@ template <> struct TmaTx<double> { static constexpr int TX = 32; };
 template <class T, int RANK, int NF, bool PAIR> struct TmaCfg {
   static constexpr int TX = TmaTx<T>::TX;
   static constexpr int TY = (RANK == 2 && NF == 1) ? 64 : 32;
-  static constexpr int RY = PAIR ? (NF == 1 ? 8 : 4) : (RANK == 2 ? 16 : 8);
+  static constexpr int RY = PAIR ? ((RANK == 2 && NF == 1) ? 8 : 4) : (RANK == 2 ? 16 : 8);
   static constexpr int S = RANK == 3 ? 8 : 3;
 };
 
@@ -371,6 +371,25 @@ struct PairAcc {
   __device__ __forceinline__ int64_t gidx() const { return g; }
 };
 
+// 3D variant: z taps come from the register queue of packed pairs.
+template <class T, int TX, int TY, int R, int NF, int NC, int NQ>
+struct PairAcc3 {
+  const T* b[NF];
+  const F2 (*col)[NC];
+  int r;
+  const F2 (*q)[NQ];
+  __device__ __forceinline__ F2 operator()(int f, int dx, int dy, int dz) const {
+    if (dz != 0) return q[f][R + dz];
+    if (dx == 0) return col[f][r + R + dy];
+    if (dx == -2) return ld_pair(b[f] - 2);
+    if (dx == 2) return ld_pair(b[f] + 2);
+    const F2 c = col[f][r + R];
+    if (dx == -1) return F2::make(ld_pair(b[f] - 2).hi(), c.lo());
+    return F2::make(c.hi(), ld_pair(b[f] + 2).lo());
+  }
+  __device__ __forceinline__ int64_t gidx() const { return 0; }
+};
+
 // Pair value of tile row tr for the column registers: from the wide box or,
 // where the periodic y halo wraps, from the row slots (as column_value).
 template <class T, int TX, int TY, int R, int NF>
@@ -614,15 +633,112 @@ __device__ __forceinline__ void march3d(const TmaParams<Op, T>& p, unsigned char
   }
 }
 
+// Paired consumer side of the z-march (FP32/BF16 storage): each thread owns
+// two adjacent columns and RY rows; the z queue and the column registers
+// hold packed pairs.  A warp spans the tile width (TX = 64), so it patches
+// both wrapped halo column blocks of its own rows.
+template <bool YW, bool XF, bool SIMPLE, class Op, class T, int TX, int TY, int RY, int S>
+__device__ __forceinline__ void march3d_pair(const TmaParams<Op, T>& p, unsigned char* smem,
+                                             uint64_t* full, uint64_t* empty,
+                                             volatile int* abort_flag, const TileInfo& t, int z0,
+                                             int z1, int np) {
+  constexpr int R = Op::R, NF = Op::NF, NQ = 2 * R + 1, NC = RY + 2 * R;
+  using L = Layout<T, TX, TY, R, NF>;
+  static_assert(TX == 64, "a warp of pairs spans the tile");
+  const int tid = threadIdx.x;
+  const int cx2 = (tid % 32) * 2, cy0 = (tid / 32) * RY, lane = tid % 32;
+  const int64_t plane = int64_t(p.nx) * p.ny;
+  constexpr bool simple = !YW || SIMPLE;  // strip rows never wrap
+  F2 q[RY][NF][NQ];
+  bool ok = true;
+
+  auto release = [&](int j) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[j % S]);
+  };
+  auto shift_in = [&](int j) -> bool {
+    const int s = j % S;
+    if (!mbar_wait_bounded(&full[s], (j / S) & 1, p.err) || *abort_flag) {
+      *abort_flag = 1;
+      return false;
+    }
+    unsigned char* st = smem + s * L::STAGE_B;
+    if (XF) fix_x_rows<T, TX, TY, R, NF, RY>(st, t, cy0, t.xl, t.xr);
+#pragma unroll
+    for (int r = 0; r < RY; ++r)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+#pragma unroll
+        for (int k = 0; k < NQ - 1; ++k) q[r][f][k] = q[r][f][k + 1];
+        if (simple)
+          q[r][f][NQ - 1] = ld_pair(reinterpret_cast<const T*>(st + f * L::FIELD_B) +
+                                    (R + cy0 + r) * L::W + L::CW + cx2);
+        else
+          q[r][f][NQ - 1] = column_pair<T, TX, TY, R, NF>(st, f, t, cy0 + r, cx2, p.ny);
+      }
+    return true;
+  };
+
+  for (int j = 0; j < 2 * R && ok; ++j) {
+    ok = shift_in(j);
+    if (ok && (j < R || j >= np - R)) release(j);  // outside [z0, z1): centres only
+  }
+  const bool xvalid = cx2 < t.nvx;
+  for (int m = 0; ok && m < z1 - z0; ++m) {
+    const int jn = m + 2 * R;
+    ok = shift_in(jn);
+    if (!ok) break;
+    const int jc = m + R;  // plane of the outputs
+    const unsigned char* st = smem + (jc % S) * L::STAGE_B;
+    F2 col[NF][NC];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const T* box = reinterpret_cast<const T*>(st + f * L::FIELD_B);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        if (YW) {
+          col[f][k] = column_pair<T, TX, TY, R, NF>(st, f, t, cy0 - R + k, cx2, p.ny);
+          col[f][R + RY + k] = column_pair<T, TX, TY, R, NF>(st, f, t, cy0 + RY + k, cx2, p.ny);
+        } else {
+          col[f][k] = ld_pair(box + (cy0 + k) * L::W + L::CW + cx2);
+          col[f][R + RY + k] = ld_pair(box + (cy0 + R + RY + k) * L::W + L::CW + cx2);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RY; ++r) col[f][R + r] = q[r][f][R];
+    }
+    const int64_t base = int64_t(z0 + m) * plane + int64_t(t.y0 + cy0) * p.nx + t.x0 + cx2;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      PairAcc3<T, TX, TY, R, NF, NC, NQ> acc;
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        acc.b[f] = reinterpret_cast<const T*>(st + f * L::FIELD_B) + (R + cy0 + r) * L::W + L::CW + cx2;
+      acc.col = col;
+      acc.r = r;
+      acc.q = q[r];
+      F2 o[NF];
+      F2 unused(0.f);
+      p.op(acc, o, unused);
+      if (xvalid && cy0 + r < t.nvy) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) st_pair(p.out[f] + base + int64_t(r) * p.nx, o[f]);
+      }
+    }
+    release(jc);
+    if (jn >= np - R) release(jn);  // above z1-1: centres only
+  }
+}
+
 // WRAP: compile the periodic-halo handling (x or y axis periodic).  Grids
 // without a periodic x/y axis use the instance without it, whose consumer
 // code fits the register budget of two blocks per SM.
-template <class Op, class T, int TX, int TY, int RY, int S, bool WRAP>
-__global__ void __launch_bounds__(TX * (TY / RY) + 32, 2)
+template <class Op, class T, int TX, int TY, int RY, int S, bool WRAP, bool PAIR>
+__global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32, 2)
     tma3d_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
   constexpr int R = Op::R, NF = Op::NF;
   using L = Layout<T, TX, TY, R, NF>;
-  constexpr int NCONS = TX * (TY / RY);
+  constexpr int NCONS = (PAIR ? TX / 2 : TX) * (TY / RY);
   static_assert(S >= R + 2, "ring too short for the z window");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = align128(smem_raw);
@@ -675,8 +791,15 @@ __global__ void __launch_bounds__(TX * (TY / RY) + 32, 2)
   }
 
   double red = 0.0;
-#define LOPE_MARCH(YW, XF, SIMPLE) \
-  march3d<YW, XF, SIMPLE, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1, np, red)
+#define LOPE_MARCH(YW, XF, SIMPLE)                                                               \
+  do {                                                                                           \
+    if constexpr (PAIR)                                                                          \
+      march3d_pair<YW, XF, SIMPLE, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t,   \
+                                                         z0, z1, np);                            \
+    else                                                                                         \
+      march3d<YW, XF, SIMPLE, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0,    \
+                                                    z1, np, red);                                \
+  } while (0)
   if constexpr (WRAP) {
     const bool yw = t.yl || t.yh, xf = t.xl || t.xr;
     const bool simple = simple_y<TY>(t, p.ny);
@@ -748,9 +871,9 @@ constexpr int kMinChunk = 48;
 
 template <class Op, class T, int RANK>
 struct TmaRunner {
-  // Paired consumers for 2D FP32/BF16 local functions without reductions.
-  static constexpr bool PAIR = RANK == 2 && !std::is_same<T, double>::value && !Op::REDUCES &&
-                               Op::R <= 2 && TmaTx<T>::TX == 64;
+  // Paired consumers for FP32/BF16 local functions without reductions.
+  static constexpr bool PAIR = !std::is_same<T, double>::value && !Op::REDUCES && Op::R <= 2 &&
+                               TmaTx<T>::TX == 64;
   using Cfg = TmaCfg<T, RANK, Op::NF, PAIR>;
   static constexpr int TX = Cfg::TX, TY = Cfg::TY, RY = Cfg::RY, S = Cfg::S;
   using L = Layout<T, TX, TY, Op::R, Op::NF>;
@@ -759,7 +882,7 @@ struct TmaRunner {
 
   template <bool WRAP> static auto kernel_w() {
     if constexpr (RANK == 2) return &tma2d_kernel<Op, T, TX, TY, RY, S, WRAP, PAIR>;
-    else return &tma3d_kernel<Op, T, TX, TY, RY, S, WRAP>;
+    else return &tma3d_kernel<Op, T, TX, TY, RY, S, WRAP, PAIR>;
   }
 
   template <bool WRAP> static int occupancy_w() {
