@@ -50,7 +50,8 @@ enum {
   OR_JACOBI5 = 1,  /* 2D: u + c (E + W + N + S - 4u)                          */
   OR_DIFF7 = 2,    /* 3D: u + c (sum of 6 face neighbours - 6u)               */
   OR_STAR9R2 = 3,  /* 2D: u + c (L4x u + L4y u), 4th-order 1D Laplacians      */
-  OR_SWE = 4       /* 2D, 3 fields (h,u,v): linearised C-grid shallow water   */
+  OR_SWE = 4,      /* 2D, 3 fields (h,u,v): linearised C-grid shallow water   */
+  OR_SWEFLUX = 5   /* 2D, 3 fields (eta,u,v): nonlinear flux-form C-grid SWE  */
 };
 
 enum { OR_OK = 0, OR_ERR = 1 };
@@ -73,7 +74,7 @@ typedef struct {
 typedef struct {
   int kind;
   int radius;             /* for OR_LINEAR                                    */
-  const double* prm;      /* c, or (dt, g, H) for OR_SWE                       */
+  const double* prm;      /* c, or (dt, g, H) for OR_SWE, (dt, g, f, H) for OR_SWEFLUX */
   const double* w;        /* OR_LINEAR weights, (2r+1)^ndim, slowest first    */
 } or_stencil;
 
@@ -141,6 +142,39 @@ static void lf_swe(const or_acc* a, const double* prm, double* out) {
   out[2] = U(a, 2, 0, 0, 0) - dt * gr * (U(a, 0, 0, +1, 0) - U(a, 0, 0, 0, 0));
 }
 
+/* Nonlinear shallow water on an Arakawa C-grid, forward Euler, unit spacing.
+ * Fields: eta = h - H (surface elevation about the mean depth H) at the cell
+ * centre, u on the east face and v on the north face of cell (i,j).  This is a
+ * non-linear physics operator with products of halo values, the kind of local
+ * function the paper's Limitations paragraph (Sec. 5) names.
+ *   mass:     eta' = eta - dt [ (F(i) - F(i-1)) + (G(j) - G(j-1)) ],
+ *             F = (H + mean of eta across the east face) u,
+ *             G = (H + mean of eta across the north face) v;
+ *   momentum: u' = u + dt [ f vbar - g d_x eta - u D_x u - vbar D_y u ],
+ *             v' = v + dt [ -f ubar - g d_y eta - ubar D_x v - v D_y v ],
+ * with d the one-sided difference to the next centre, D the centred
+ * difference (half the span), vbar the mean of the four v faces around the u
+ * face (reads the corner U(+1,-1)) and ubar the mean of the four u faces
+ * around the v face (reads the corner U(-1,+1)). */
+static void lf_swe_flux(const or_acc* a, const double* prm, double* out) {
+  double dt = prm[0], gr = prm[1], fc = prm[2], H = prm[3];
+  double e = U(a, 0, 0, 0, 0), eE = U(a, 0, +1, 0, 0), eW = U(a, 0, -1, 0, 0);
+  double eN = U(a, 0, 0, +1, 0), eS = U(a, 0, 0, -1, 0);
+  double u = U(a, 1, 0, 0, 0), uW = U(a, 1, -1, 0, 0), uE = U(a, 1, +1, 0, 0);
+  double uN = U(a, 1, 0, +1, 0), uS = U(a, 1, 0, -1, 0), uWN = U(a, 1, -1, +1, 0);
+  double v = U(a, 2, 0, 0, 0), vS = U(a, 2, 0, -1, 0), vN = U(a, 2, 0, +1, 0);
+  double vE = U(a, 2, +1, 0, 0), vW = U(a, 2, -1, 0, 0), vES = U(a, 2, +1, -1, 0);
+  double F_e = (H + 0.5 * (e + eE)) * u;
+  double F_w = (H + 0.5 * (eW + e)) * uW;
+  double G_n = (H + 0.5 * (e + eN)) * v;
+  double G_s = (H + 0.5 * (eS + e)) * vS;
+  double vbar = 0.25 * ((v + vE) + (vS + vES));
+  double ubar = 0.25 * ((u + uW) + (uN + uWN));
+  out[0] = e - dt * ((F_e - F_w) + (G_n - G_s));
+  out[1] = u + dt * (fc * vbar - gr * (eE - e) - u * 0.5 * (uE - uW) - vbar * 0.5 * (uN - uS));
+  out[2] = v + dt * (-fc * ubar - gr * (eN - e) - ubar * 0.5 * (vE - vW) - v * 0.5 * (vN - vS));
+}
+
 static void lf_linear(const or_acc* a, int ndim, int r, const double* w, double* out) {
   int zr = ndim == 3 ? r : 0;
   int side = 2 * r + 1;
@@ -171,7 +205,7 @@ static double lf_dcoef(const or_acc* a, int kind) {
   }
 }
 
-static int nfields_of(int kind) { return kind == OR_SWE ? 3 : 1; }
+static int nfields_of(int kind) { return (kind == OR_SWE || kind == OR_SWEFLUX) ? 3 : 1; }
 
 static int make_grid(or_grid* g, int ndim, const int64_t* ext, const int* bc, const double* bval) {
   if (ndim != 2 && ndim != 3) return OR_ERR;
@@ -217,6 +251,7 @@ static void sweep(const or_grid* g, const or_stencil* s, double* const* in, doub
             case OR_DIFF7: lf_diff7(&a, s->prm, r); break;
             case OR_STAR9R2: lf_star9r2(&a, s->prm, r); break;
             case OR_SWE: lf_swe(&a, s->prm, r); break;
+            case OR_SWEFLUX: lf_swe_flux(&a, s->prm, r); break;
             default: lf_linear(&a, g->ndim, s->radius, s->w, r); break;
           }
           int64_t idx = (z * n1 + y) * n2 + x;
@@ -227,7 +262,8 @@ static void sweep(const or_grid* g, const or_stencil* s, double* const* in, doub
 
 static int check_stencil(const or_grid* g, const or_stencil* s) {
   switch (s->kind) {
-    case OR_JACOBI5: case OR_STAR9R2: case OR_SWE: return g->ndim == 2 ? OR_OK : OR_ERR;
+    case OR_JACOBI5: case OR_STAR9R2: case OR_SWE: case OR_SWEFLUX:
+      return g->ndim == 2 ? OR_OK : OR_ERR;
     case OR_DIFF7: return g->ndim == 3 ? OR_OK : OR_ERR;
     case OR_LINEAR: return (s->radius >= 0 && s->w) ? OR_OK : OR_ERR;
     default: return OR_ERR;
@@ -261,6 +297,67 @@ int oracle_apply(int ndim, const int64_t* ext, const int* bc, const double* bval
     memcpy(out[k], cur[k], sizeof(double) * n);
     free(cur[k]);
     free(nxt[k]);
+  }
+  return OR_OK;
+}
+
+/* Multi-stage time stepping over the local function.  The local function is
+ * itself one forward-Euler step E(u) = u + dt F(u); the strong-stability-
+ * preserving Runge-Kutta schemes of Shu and Osher (J. Comput. Phys. 77, 1988)
+ * are convex combinations of Euler steps, so every stage is a sweep of the
+ * same local function followed by a pointwise combination with the state at
+ * the start of the step:
+ *   stages = 2:  u1 = E(u);  u+ = 1/2 u + 1/2 E(u1)
+ *   stages = 3:  u1 = E(u);  u2 = 3/4 u + 1/4 E(u1);  u+ = 1/3 u + 2/3 E(u2)
+ *   stages = 1:  u+ = E(u)   (plain application)
+ * The intermediate states u1, u2 are the "intermediate results resulting from
+ * multiple intermediate update steps" that the paper's Limitations paragraph
+ * (Sec. 5) says LOPe does not store; each stage refreshes the halo from its
+ * own input, as the Euler sweep does. */
+static void combine(double* dst, double a, const double* base, double b, const double* e,
+                    int64_t n) {
+  for (int64_t i = 0; i < n; i++) dst[i] = a * base[i] + b * e[i];
+}
+
+int oracle_apply_rk(int ndim, const int64_t* ext, const int* bc, const double* bval, int kind,
+                    const double* prm, int radius, const double* weights, int stages,
+                    const double* const* in, double* const* out, int64_t nsteps, int nthreads) {
+  or_grid g;
+  if (make_grid(&g, ndim, ext, bc, bval) != OR_OK) return OR_ERR;
+  or_stencil s = {kind, radius, prm, weights};
+  if (check_stencil(&g, &s) != OR_OK) return OR_ERR;
+  if (stages < 1 || stages > 3) return OR_ERR;
+  int nf = nfields_of(kind);
+  int64_t n = npoints(&g);
+  double *u[OR_MAXF], *st[OR_MAXF], *e[OR_MAXF];
+  for (int k = 0; k < nf; k++) {
+    u[k] = (double*)malloc(sizeof(double) * n);
+    st[k] = (double*)malloc(sizeof(double) * n);
+    e[k] = (double*)malloc(sizeof(double) * n);
+    if (!u[k] || !st[k] || !e[k]) return OR_ERR;
+    memcpy(u[k], in[k], sizeof(double) * n);
+  }
+  for (int64_t t = 0; t < nsteps; t++) {
+    if (stages == 1) {
+      sweep(&g, &s, u, e, nthreads);
+      for (int k = 0; k < nf; k++) memcpy(u[k], e[k], sizeof(double) * n);
+      continue;
+    }
+    sweep(&g, &s, u, st, nthreads); /* u1 = E(u) */
+    sweep(&g, &s, st, e, nthreads); /* E(u1) */
+    if (stages == 2) {
+      for (int k = 0; k < nf; k++) combine(u[k], 0.5, u[k], 0.5, e[k], n);
+    } else {
+      for (int k = 0; k < nf; k++) combine(st[k], 0.75, u[k], 0.25, e[k], n); /* u2 */
+      sweep(&g, &s, st, e, nthreads);                                         /* E(u2) */
+      for (int k = 0; k < nf; k++) combine(u[k], 1.0 / 3.0, u[k], 2.0 / 3.0, e[k], n);
+    }
+  }
+  for (int k = 0; k < nf; k++) {
+    memcpy(out[k], u[k], sizeof(double) * n);
+    free(u[k]);
+    free(st[k]);
+    free(e[k]);
   }
   return OR_OK;
 }
@@ -342,7 +439,7 @@ int oracle_vjp(int ndim, const int64_t* ext, const int* bc, const double* bval, 
   or_grid g;
   if (make_grid(&g, ndim, ext, bc, bval) != OR_OK) return OR_ERR;
   or_stencil s = {kind, radius, prm, weights};
-  if (kind == OR_SWE || check_stencil(&g, &s) != OR_OK) return OR_ERR;
+  if (kind == OR_SWE || kind == OR_SWEFLUX || check_stencil(&g, &s) != OR_OK) return OR_ERR;
   int64_t n = npoints(&g);
   double w[125];
   int r = oracle_weights(kind, prm, ndim, radius, weights, w, 125);

@@ -16,7 +16,10 @@ import numpy as np
 
 BC_PERIODIC = 0
 BC_DIRICHLET = 1
-KIND = {"linear": 0, "jacobi5": 1, "diff7": 2, "star9r2": 3, "swe_cgrid": 4}
+KIND = {"linear": 0, "jacobi5": 1, "diff7": 2, "star9r2": 3, "swe_cgrid": 4, "swe_flux": 5}
+# Time-stepping schemes: stages of the strong-stability-preserving Runge-Kutta
+# methods built from the local function (1 = the local function itself).
+SCHEME_STAGES = {"euler": 1, "rk2": 2, "rk3": 3}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lope_oracle.c")
@@ -50,6 +53,10 @@ def _load():
             lib.oracle_apply.restype = ctypes.c_int
             lib.oracle_apply.argtypes = [ctypes.c_int, _I64, _I, _D, ctypes.c_int, _D, ctypes.c_int,
                                          _D, _DD, _DD, ctypes.c_int64, ctypes.c_int]
+            lib.oracle_apply_rk.restype = ctypes.c_int
+            lib.oracle_apply_rk.argtypes = [ctypes.c_int, _I64, _I, _D, ctypes.c_int, _D,
+                                            ctypes.c_int, _D, ctypes.c_int, _DD, _DD,
+                                            ctypes.c_int64, ctypes.c_int]
             lib.oracle_vjp.restype = ctypes.c_int
             lib.oracle_vjp.argtypes = [ctypes.c_int, _I64, _I, _D, ctypes.c_int, _D, ctypes.c_int,
                                        _D, _D, _D, ctypes.c_int64, _D, _D, ctypes.c_int]
@@ -104,11 +111,14 @@ def max_threads() -> int:
 
 
 def apply(fields, kind, params=None, nsteps=1, bc=None, bval=None, weights_table=None,
-          nthreads=1):
+          nthreads=1, scheme="euler"):
     """Apply the local function ``nsteps`` times in FP64.
 
-    ``fields`` is one array or a list of arrays (3 for "swe_cgrid"), all of the
-    grid's shape (slowest axis first).  Returns arrays of the same structure.
+    ``fields`` is one array or a list of arrays (3 for "swe_cgrid" and
+    "swe_flux"), all of the grid's shape (slowest axis first).  Returns arrays
+    of the same structure.  ``scheme`` "rk2"/"rk3" takes ``nsteps`` steps of the
+    strong-stability-preserving Runge-Kutta method whose stages are sweeps of
+    the local function (see oracle_apply_rk).
     """
     lib = _load()
     single = isinstance(fields, np.ndarray)
@@ -120,9 +130,15 @@ def apply(fields, kind, params=None, nsteps=1, bc=None, bval=None, weights_table
     outs = [np.empty_like(a) for a in ins]
     in_arr = (_D * len(ins))(*[_dptr(a) for a in ins])
     out_arr = (_D * len(outs))(*[_dptr(a) for a in outs])
-    rc = lib.oracle_apply(ndim, ext.ctypes.data_as(_I64), bcs.ctypes.data_as(_I), _dptr(bvs), k,
-                          _dptr(prm), radius, _dptr(w), in_arr, out_arr, int(nsteps),
-                          int(nthreads))
+    stages = SCHEME_STAGES[scheme]
+    if stages == 1:
+        rc = lib.oracle_apply(ndim, ext.ctypes.data_as(_I64), bcs.ctypes.data_as(_I), _dptr(bvs),
+                              k, _dptr(prm), radius, _dptr(w), in_arr, out_arr, int(nsteps),
+                              int(nthreads))
+    else:
+        rc = lib.oracle_apply_rk(ndim, ext.ctypes.data_as(_I64), bcs.ctypes.data_as(_I),
+                                 _dptr(bvs), k, _dptr(prm), radius, _dptr(w), stages, in_arr,
+                                 out_arr, int(nsteps), int(nthreads))
     if rc != 0:
         raise ValueError("oracle_apply rejected its arguments")
     return outs[0] if single else outs
