@@ -10,7 +10,9 @@ flush is needed between steps.
 Extra forms (outside the timed region, reported under "forms"): the batched
 launch (512 uneven 2D grids, 20 steps) against per-grid launches, the forward +
 adjoint (256^3, 100 steps, checkpoint every 10) against the plain forward,
-the shallow-water multi-field form in FP32 and BF16, and the FP64 256^2 case.
+the shallow-water multi-field forms (linear, and nonlinear flux form with a box
+halo) in FP32 and BF16, SSP-RK3 steps of the nonlinear form (fused against one
+launch per stage), and the FP64 256^2 case.
 
 --impl reference times the FP64 oracle on the host cores instead (bounded
 samples of the same workload mix).  Under torchrun every rank runs its own
@@ -188,7 +190,7 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-KERNEL_SOURCES = ("k_tma.cu", "device_common.cuh", "lope_internal.h")
+KERNEL_SOURCES = ("k_tma.cu", "tma_kernels.cuh", "device_common.cuh", "lope_internal.h")
 
 
 def kernel_source_hash():
@@ -372,7 +374,8 @@ def main():
     if not args.main_only and rank == 0:
         del u3_h, u2_h, h_o3, h_o2
         for name, fn in (("fp64_256", form_fp64), ("swe_4096", form_swe), ("batched_512", form_batch),
-                         ("fwd_adjoint_256", form_adjoint)):
+                         ("fwd_adjoint_256", form_adjoint), ("swe_flux_4096", form_swe_flux),
+                         ("rk3_swe_flux_4096", form_rk3)):
             try:
                 forms[name] = fn(L, LI, torch, dev, peak)
             except Exception as e:  # reported, never hidden
@@ -431,6 +434,11 @@ def run_profile(args):
         st = L.Stencil.builtin("swe_cgrid", 0.02, 1.0, 1.0)
         kind, nf = "periodic", 3
         dtype, bpp = ("f32", 24) if name == "swe" else ("bf16", 12)
+    elif name in ("sweflux", "swefluxbf16"):
+        shape, halo, pts = (n, n), 1, n * n
+        st = L.Stencil.builtin("swe_flux", 0.02, 1.0, 0.5, 1.0)
+        kind, nf = "periodic", 3
+        dtype, bpp = ("f32", 24) if name == "sweflux" else ("bf16", 12)
     else:
         raise SystemExit(f"unknown profile case {name}")
     g = L.Grid(shape, dtype, halo=halo, nfields=nf)
@@ -500,6 +508,72 @@ def form_swe(L, LI, torch, dev, peak):
     res["bf16_speedup_vs_f32"] = res["f32"]["ms"] / res["bf16"]["ms"]
     res["workload"] = "C-grid shallow water (h,u,v) 4096^2 periodic x200; BF16 stores eta = h - 1"
     return res
+
+
+def _flux_fields(LI, torch, dev, n, dtype, seed):
+    h, u, v = LI.swe_fields(seed, (n, n))
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    return [torch.from_numpy(LI.to_storage(x, dtype)).to(dev).to(tdt) for x in (h - 1.0, u, v)]
+
+
+def form_swe_flux(L, LI, torch, dev, peak):
+    """Nonlinear flux-form shallow water (box halo, corner taps), 4096^2 x 3
+    fields, periodic, 200 forward-Euler steps, FP32 and BF16 storage."""
+    n, T = 4096, 200
+    res = {}
+    for dtype in ("f32", "bf16"):
+        f = _flux_fields(LI, torch, dev, n, dtype, 1009)
+        o = [torch.empty_like(x) for x in f]
+        w = [torch.empty_like(x) for x in f]
+        g = L.Grid((n, n), dtype, halo=1, nfields=3)
+        s = L.Stencil.builtin("swe_flux", 0.02, 1.0, 0.5, 1.0)
+        ms = _time(torch, lambda: L.apply(g, s, f, out=o, work=w, nsteps=T), reps=3)
+        esz = 4 if dtype == "f32" else 2
+        gbps = 6 * esz * n * n * T / (ms / 1e3) / 1e9
+        res[dtype] = {"ms": ms, "point_updates_per_s": n * n * T / (ms / 1e3),
+                      "alg_GBps": gbps, "frac_of_peak": gbps / peak}
+        del f, o, w
+    res["bf16_speedup_vs_f32"] = res["f32"]["ms"] / res["bf16"]["ms"]
+    res["workload"] = ("nonlinear flux-form C-grid shallow water (eta,u,v) 4096^2 periodic x200, "
+                       "dt 0.02, g 1, f 0.5, H 1; TMA tiles with box halo")
+    return res
+
+
+def form_rk3(L, LI, torch, dev, peak):
+    """SSP-RK3 steps of the nonlinear shallow water, 4096^2 x 3 FP32, 50 steps:
+    fused trapezoid steps (stage states in shared memory) against one launch
+    per stage (TMA tiles, stage states in HBM) and against 150 plain sweeps."""
+    n, T = 4096, 50
+    f = _flux_fields(LI, torch, dev, n, "f32", 1105)
+    o = [torch.empty_like(x) for x in f]
+    w = [torch.empty((2, n, n), dtype=x.dtype, device=dev) for x in f]
+    g = L.Grid((n, n), "f32", halo=1, nfields=3)
+    s = L.Stencil.builtin("swe_flux", 0.02, 1.0, 0.5, 1.0).set_scheme("rk3")
+    best = None
+    for tx, ty in ((64, 32), (64, 16), (128, 16), (32, 32)):
+        for k in (1, 2):
+            cfg = L.Launch(2, tx, ty, k, -1)
+            try:
+                ms = _time(torch, lambda: L.apply(g, s, f, out=o, work=w, nsteps=T, launch=cfg), reps=2)
+            except Exception:
+                continue
+            if best is None or ms < best[0]:
+                best = (ms, tx, ty, k)
+    ms_fused, tx, ty, k = best
+    ms_stage = _time(torch, lambda: L.apply(g, s, f, out=o, work=w, nsteps=T,
+                                            launch=L.Launch(1, 0, 0, 0, -1)), reps=3)
+    e = L.Stencil.builtin("swe_flux", 0.02, 1.0, 0.5, 1.0)
+    ms_euler = _time(torch, lambda: L.apply(g, e, f, out=o, work=[x[0] for x in w], nsteps=3 * T), reps=3)
+    pts = n * n * T
+    return {"workload": "SSP-RK3 nonlinear shallow water 4096^2 x3 FP32 periodic x50 steps (150 stages)",
+            "fused_trapezoid_ms": ms_fused, "fused_choice": {"tile": [tx, ty], "tsteps": k},
+            "fused_rk_steps_per_s": pts / (ms_fused / 1e3),
+            "fused_alg_GBps": 24 * pts / (ms_fused / 1e3) / 1e9,
+            "fused_frac_of_peak": 24 * pts / (ms_fused / 1e3) / 1e9 / peak,
+            "stage_launches_ms": ms_stage, "stage_alg_GBps": 96 * pts / (ms_stage / 1e3) / 1e9,
+            "stage_frac_of_peak": 96 * pts / (ms_stage / 1e3) / 1e9 / peak,
+            "euler_150_sweeps_ms": ms_euler,
+            "fused_speedup_vs_stage_launches": ms_stage / ms_fused}
 
 
 def form_batch(L, LI, torch, dev, peak):

@@ -74,6 +74,13 @@ lope_status lope_set_boundary(lope_grid* grid, int axis, int side, lope_bc kind,
  *                                    1D Laplacian (-1/12, 4/3, -5/2, 4/3, -1/12).
  *   "swe_cgrid" 2D, 3 fields (h,u,v), params {dt, g, H}: linearised shallow
  *                                    water on an Arakawa C-grid, forward Euler.
+ *   "swe_flux"  2D, 3 fields (eta,u,v), params {dt, g, f, H}: nonlinear shallow
+ *                                    water on a C-grid (eta = h - H): flux-form
+ *                                    mass, Coriolis on four-face means (corner
+ *                                    taps), pressure gradient, centred advection;
+ *                                    forward Euler.  A non-linear physics
+ *                                    operator with a radius-1 box halo (the
+ *                                    kind Sec. 5, Limitations, names).
  * Errors: LOPE_ERR_INVALID for an unknown name or wrong parameter count. */
 lope_status lope_stencil_create_builtin(lope_stencil** stencil, const char* name,
                                         const double* params, int nparams);
@@ -81,11 +88,32 @@ lope_status lope_stencil_create_builtin(lope_stencil** stencil, const char* name
 /* General linear local function U(0,0) = sum_o w[o] U(o) over the box of
  * radius `radius` (1..2): weights has (2r+1)^ndim entries, slowest offset first,
  * i.e. weights[((dz+r)*(2r+1) + dy+r)*(2r+1) + dx+r] (dz only for ndim = 3).
- * Star-shaped tables (all off-axis entries zero) take the TMA kernels; tables
- * with corners take the shared-memory / direct kernels. */
+ * Star-shaped tables (all off-axis entries zero) take the TMA kernels; 2D
+ * tables with corners take the 2D TMA tiles too, 3D ones the direct kernel. */
 lope_status lope_stencil_create_linear(lope_stencil** stencil, int ndim, int radius,
                                        const double* weights);
 void lope_stencil_destroy(lope_stencil* stencil);
+
+/* Time-stepping scheme.  A local function is one forward-Euler step E(u) = u +
+ * dt F(u) (EULER, the default: a step is one sweep).  RK2 and RK3 are the
+ * strong-stability-preserving Runge-Kutta methods of Shu and Osher (1988)
+ * written as convex combinations of Euler steps:
+ *   RK2: u1 = E(u);  u+ = 1/2 u + 1/2 E(u1)
+ *   RK3: u1 = E(u);  u2 = 3/4 u + 1/4 E(u1);  u+ = 1/3 u + 2/3 E(u2)
+ * Each stage refreshes the halo from its own input.  The intermediate states
+ * u1, u2 are the storage of intermediate results across multiple update steps
+ * that the paper's Limitations paragraph (Sec. 5) says LOPe does not provide:
+ * the trapezoid path keeps them in shared memory, the TMA and direct paths in
+ * the work buffers.  nsteps of lope_apply then counts Runge-Kutta steps.
+ * Not supported by lope_apply_batch and the adjoint calls (UNSUPPORTED).
+ * Errors: LOPE_ERR_INVALID for an unknown scheme. */
+typedef enum { LOPE_SCHEME_EULER = 1, LOPE_SCHEME_RK2 = 2, LOPE_SCHEME_RK3 = 3 } lope_scheme;
+lope_status lope_stencil_set_scheme(lope_stencil* stencil, lope_scheme scheme);
+
+/* Number of grid states each work buffer of lope_apply must hold for this
+ * stencil's scheme: 2 for RK3 (both stage states, the second directly after
+ * the first), else 1. */
+lope_status lope_work_states(const lope_stencil* stencil, int* states);
 
 /* Apply the local function at every interior point, nsteps times (Sec. 3.2:
  * each do-concurrent sweep is followed by a halo refresh).  Every sweep reads
@@ -94,8 +122,9 @@ void lope_stencil_destroy(lope_stencil* stencil);
  * or temporal blocking.
  *   in[nfields]   read-only input state (never written)
  *   out[nfields]  final state; must not alias in
- *   work[nfields] scratch state of the same size, needed when nsteps >= 2
- *                 (may be NULL for nsteps <= 1)
+ *   work[nfields] scratch state of the same size (lope_work_states() states
+ *                 for multi-stage schemes), needed when nsteps >= 2 or the
+ *                 scheme has several stages (may be NULL for Euler, nsteps <= 1)
  * nsteps = 0 copies in to out.  The planner picks kernel, tile and temporal
  * depth (see lope_apply_with).  Errors: LOPE_ERR_INVALID (aliasing, NULL,
  * misaligned pointers, stencil radius above the declared halo, dimension
@@ -105,8 +134,8 @@ lope_status lope_apply(const lope_grid* grid, const lope_stencil* stencil, const
                        void* const* out, void* const* work, int64_t nsteps, void* cuda_stream);
 
 /* Launch choices, for tests and tuning.  Zero fields mean "planner decides".
- *   path:    0 auto, 1 TMA tiles (2D tiles / 3D z-march; star stencils, 16-byte
- *            row pitch), 2 shared-memory trapezoid tiles with temporal blocking
+ *   path:    0 auto, 1 TMA tiles (2D tiles, any stencil / 3D z-march, star
+ *            stencils; 16-byte row pitch), 2 shared-memory trapezoid tiles with temporal blocking
  *            (2D, any stencil, any shape), 3 direct (any stencil, one thread per
  *            point).
  *   tile_x, tile_y: tile shape for path 2 (tile_x in {32,64,128}, tile_y in

@@ -15,6 +15,7 @@ from ._lib import (  # noqa: F401
     BC_PERIODIC,
     DTYPES,
     LopeError,
+    SCHEMES,
     Grid,
     Launch,
     Stencil,
@@ -54,8 +55,10 @@ from ._lib import (  # noqa: F401  (C ABI names)
     lope_stencil_create_builtin,
     lope_stencil_create_linear,
     lope_stencil_destroy,
+    lope_stencil_set_scheme,
     lope_sync_status,
     lope_version,
     lope_vjp,
+    lope_work_states,
     lope_workspace_size,
 )

@@ -60,6 +60,8 @@ _SIGS = {
     "lope_stencil_create_builtin": (_INT, [ctypes.POINTER(_P), ctypes.c_char_p, _DP, _INT]),
     "lope_stencil_create_linear": (_INT, [ctypes.POINTER(_P), _INT, _INT, _DP]),
     "lope_stencil_destroy": (None, [_P]),
+    "lope_stencil_set_scheme": (_INT, [_P, _INT]),
+    "lope_work_states": (_INT, [_P, ctypes.POINTER(_INT)]),
     "lope_apply": (_INT, [_P, _P, _PP, _PP, _PP, _I64, _P]),
     "lope_apply_with": (_INT, [_P, _P, _PP, _PP, _PP, _I64, ctypes.POINTER(Launch), _P]),
     "lope_autotune": (_INT, [_P, _P, _PP, _PP, _PP, _I64, ctypes.POINTER(Launch), _DP, _P]),
@@ -159,6 +161,19 @@ def lope_stencil_create_linear(ndim: int, radius: int, weights):
     _check(load().lope_stencil_create_linear(ctypes.byref(h), ndim, radius,
                                              w.ctypes.data_as(_DP)))
     return h
+
+
+SCHEMES = {"euler": 1, "rk2": 2, "rk3": 3}
+
+
+def lope_stencil_set_scheme(h, scheme: int):
+    _check(load().lope_stencil_set_scheme(h, int(scheme)))
+
+
+def lope_work_states(h) -> int:
+    n = _INT(0)
+    _check(load().lope_work_states(h, ctypes.byref(n)))
+    return int(n.value)
 
 
 def lope_stencil_destroy(h):
@@ -311,13 +326,23 @@ class Stencil:
 
     def __init__(self, handle, ndim, radius, nfields):
         self.handle, self.ndim, self.radius, self.nfields = handle, ndim, radius, nfields
+        self.scheme = "euler"
+
+    def set_scheme(self, scheme: str):
+        """Time-stepping scheme: "euler" (the local function is the step), "rk2", "rk3"."""
+        lope_stencil_set_scheme(self.handle, SCHEMES[scheme])
+        self.scheme = scheme
+        return self
+
+    def work_states(self) -> int:
+        return lope_work_states(self.handle)
 
     @classmethod
     def builtin(cls, name, *params):
         h = lope_stencil_create_builtin(name, [float(p) for p in params])
         ndim = 3 if name == "diff7" else 2
         radius = 2 if name == "star9r2" else 1
-        return cls(h, ndim, radius, 3 if name == "swe_cgrid" else 1)
+        return cls(h, ndim, radius, 3 if name in ("swe_cgrid", "swe_flux") else 1)
 
     @classmethod
     def linear(cls, weights):
@@ -343,8 +368,13 @@ def apply(grid: Grid, stencil: Stencil, inputs, out=None, work=None, nsteps=1, l
 
     ins = _as_list(inputs)
     outs = _as_list(out) if out is not None else [torch.empty_like(t) for t in ins]
-    works = _as_list(work) if work is not None else (
-        [torch.empty_like(t) for t in ins] if nsteps >= 2 else None)
+    if work is not None:
+        works = _as_list(work)
+    elif nsteps >= 2 or stencil.scheme != "euler":
+        ns = stencil.work_states()
+        works = [torch.empty((ns,) + tuple(t.shape), dtype=t.dtype, device=t.device) for t in ins]
+    else:
+        works = None
     s = _stream(stream)
     if launch is None:
         lope_apply(grid.handle, stencil.handle, [_dptr(t) for t in ins], [_dptr(t) for t in outs],

@@ -20,7 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblope.so")
-SOURCES = ["k_tma.cu", "k_generic.cu", "k_batch.cu", "k_reduce.cu", "api.cu"]
+SOURCES = ["k_tma.cu", "k_tma_stage.cu", "k_generic.cu", "k_generic_rk.cu", "k_batch.cu",
+           "k_reduce.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

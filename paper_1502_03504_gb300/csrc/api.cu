@@ -83,7 +83,7 @@ lope_status dev_state(DevState** out) {
 }
 
 // ------------------------------------------------------------------ validation
-int stencil_nf(const StencilDesc& s) { return s.kind == kSwe ? 3 : 1; }
+int stencil_nf(const StencilDesc& s) { return (s.kind == kSwe || s.kind == kSweFlux) ? 3 : 1; }
 
 lope_status check_pair(const lope_grid* grid, const lope_stencil* st) {
   if (!grid || !st) return fail(LOPE_ERR_INVALID, "NULL grid or stencil");
@@ -100,8 +100,12 @@ lope_status check_pair(const lope_grid* grid, const lope_stencil* st) {
   return LOPE_OK;
 }
 
+// States each work buffer holds: two for the RK3 stage sequence (u1, u2), one
+// otherwise.
+int work_states(const StencilDesc& s) { return s.stages == 3 ? 2 : 1; }
+
 lope_status check_fields(const Geom& g, const void* const* in, void* const* out, void* const* work,
-                         bool need_work) {
+                         bool need_work, int wstates = 1) {
   if (!in || !out) return fail(LOPE_ERR_INVALID, "NULL field array");
   if (need_work && !work) return fail(LOPE_ERR_INVALID, "nsteps >= 2 needs work buffers");
   for (int f = 0; f < g.nf; ++f) {
@@ -109,15 +113,19 @@ lope_status check_fields(const Geom& g, const void* const* in, void* const* out,
     if (!aligned16(in[f]) || !aligned16(out[f])) return fail(LOPE_ERR_INVALID, "field pointer not 16-byte aligned");
     if (need_work && (!work[f] || !aligned16(work[f]))) return fail(LOPE_ERR_INVALID, "bad work pointer");
     const size_t bytes = size_t(npts(g)) * esize(g.dtype);
-    auto overlap = [&](const void* a, const void* b) {
+    auto overlap = [&](const void* a, size_t na, const void* b, size_t nb) {
       const char* x = static_cast<const char*>(a);
       const char* y = static_cast<const char*>(b);
-      return x < y + bytes && y < x + bytes;
+      return x < y + nb && y < x + na;
     };
+    const size_t wbytes = bytes * size_t(wstates);
     for (int h = 0; h < g.nf; ++h) {
-      if (overlap(in[f], out[h])) return fail(LOPE_ERR_INVALID, "out aliases in (double buffering required)");
-      if (need_work && (overlap(work[f], out[h]) || overlap(work[f], in[h])))
+      if (overlap(in[f], bytes, out[h], bytes))
+        return fail(LOPE_ERR_INVALID, "out aliases in (double buffering required)");
+      if (need_work && (overlap(work[f], wbytes, out[h], bytes) || overlap(work[f], wbytes, in[h], bytes)))
         return fail(LOPE_ERR_INVALID, "work aliases in or out");
+      if (need_work && h != f && overlap(work[f], wbytes, work[h], wbytes))
+        return fail(LOPE_ERR_INVALID, "work buffers of two fields overlap");
     }
   }
   return LOPE_OK;
@@ -137,7 +145,7 @@ TuneKey tune_key(const Geom& g, const StencilDesc& s) {
   for (int ax = 0; ax < 3; ++ax)
     for (int sd = 0; sd < 2; ++sd) bcs = bcs * 2 + (g.bc[ax][sd] == kDirichlet);
   return TuneKey(g.ndim, g.n[0], g.n[1], g.n[2], g.dtype, s.kind, s.radius, int(s.star), bcs,
-                 g.nf, 0);
+                 g.nf, s.stages);
 }
 
 StepArgs base_args(const Geom& g, const StencilDesc& s, int* err, cudaStream_t st) {
@@ -158,6 +166,15 @@ Choice default_choice(const Geom& g, const StencilDesc& s, int* err) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(tune_key(g, s));
     if (it != g_tune.end()) return it->second;
+  }
+  if (s.stages >= 2 && g.ndim == 2) {
+    // Multi-stage steps: the fused trapezoid keeps the stage states on chip
+    // (one read and one write per step instead of one per stage).
+    a.tile_x = 64;
+    a.tile_y = 32;
+    if (trap2d_supported(a)) return {kPathTrap, 64, 32, 1};
+    a.tile_y = 16;
+    if (trap2d_supported(a)) return {kPathTrap, 64, 16, 1};
   }
   if (tma_supported(a)) return {kPathTma, 0, 0, 1};
   if (g.ndim == 2) return {kPathTrap, 64, 32, 1};
@@ -193,15 +210,57 @@ lope_status resolve(const Geom& g, const StencilDesc& s, const void* const* in,
     case kPathDirect: ok = direct_supported(a); break;
     default: ok = false;
   }
+  if (ok && s.stages >= 2 && d.path != kPathTrap && a.ksteps != 1) ok = false;
   if (!ok) return fail(LOPE_ERR_UNSUPPORTED, "requested launch path does not support this grid/stencil/depth");
   *c = d;
   return LOPE_OK;
+}
+
+// Multi-stage steps as one launch per stage (TMA or direct kernels).  Step j
+// starts from b = in (j = 0) or out; with work state W1 (and W2, the second
+// state of each work buffer, for RK3):
+//   RK2: W1 = E(b); out = 1/2 b + 1/2 E(W1)
+//   RK3: W1 = E(b); W2 = 3/4 b + 1/4 E(W1); out = 1/3 b + 2/3 E(W2)
+// A combining stage reads b only at the element it writes, so writing out
+// while b is out is race-free.
+cudaError_t issue_stages(const Geom& g, const StencilDesc& s, const Choice& c,
+                         const void* const* in, void* const* out, void* const* work,
+                         int64_t nsteps, int* err, cudaStream_t st) {
+  const size_t fb = size_t(npts(g)) * esize(g.dtype);
+  const int S = s.stages;
+  for (int64_t j = 0; j < nsteps; ++j) {
+    const void* b[kMaxFields];
+    void* w1[kMaxFields];
+    void* w2[kMaxFields];
+    for (int f = 0; f < g.nf; ++f) {
+      b[f] = j == 0 ? in[f] : out[f];
+      w1[f] = work[f];
+      w2[f] = static_cast<char*>(work[f]) + fb;
+    }
+    for (int stage = 1; stage <= S; ++stage) {
+      StepArgs a = base_args(g, s, err, st);
+      a.stage = stage;
+      if (stage >= 2) rk_coeffs(S, stage, &a.rk_a, &a.rk_b);
+      for (int f = 0; f < g.nf; ++f) {
+        a.in[f] = stage == 1 ? b[f] : stage == 2 ? w1[f] : w2[f];
+        a.out[f] = stage == S ? out[f] : stage == 1 ? w1[f] : w2[f];
+        a.base[f] = b[f];
+      }
+      cudaError_t e;
+      if (c.path == kPathTma) e = stage == 1 ? launch_tma(a, nullptr) : launch_tma_stage(a);
+      else e = launch_direct(a, nullptr);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 // Issue the launch sequence: ceil(nsteps/k) launches ping-ponging between out
 // and work so that the last one writes out.
 cudaError_t issue(const Geom& g, const StencilDesc& s, const Choice& c, const void* const* in,
                   void* const* out, void* const* work, int64_t nsteps, int* err, cudaStream_t st) {
+  if (s.stages >= 2 && c.path != kPathTrap)
+    return issue_stages(g, s, c, in, out, work, nsteps, err, st);
   const int64_t L = (nsteps + c.k - 1) / c.k;
   const void* src[kMaxFields];
   for (int f = 0; f < g.nf; ++f) src[f] = in[f];
@@ -309,8 +368,11 @@ lope_status apply_impl(const lope_grid* grid, const lope_stencil* st, const void
   if ((rs = dev_state(&d)) != LOPE_OK) return rs;
   Choice c;
   if ((rs = resolve(g, s, in, cfg, d->err, &c)) != LOPE_OK) return rs;
-  const int64_t L = nsteps == 0 ? 0 : (nsteps + c.k - 1) / c.k;
-  if ((rs = check_fields(g, in, out, work, L >= 2)) != LOPE_OK) return rs;
+  int64_t L = nsteps == 0 ? 0 : (nsteps + c.k - 1) / c.k;
+  const bool staged = s.stages >= 2 && c.path != kPathTrap;  // one launch per stage
+  if (staged) L = nsteps * s.stages;
+  if ((rs = check_fields(g, in, out, work, staged ? nsteps >= 1 : L >= 2, work_states(s))) != LOPE_OK)
+    return rs;
   if (nsteps == 0) {
     for (int f = 0; f < g.nf; ++f) {
       cudaError_t e = cudaMemcpyAsync(out[f], in[f], size_t(npts(g)) * esize(g.dtype),
@@ -368,7 +430,9 @@ lope_status check_linear_for_adjoint(const lope_grid* grid, const lope_stencil* 
   lope_status rs = check_pair(grid, st);
   if (rs != LOPE_OK) return rs;
   const StencilDesc& s = st->s;
-  if (s.kind == kSwe) return fail(LOPE_ERR_UNSUPPORTED, "adjoint needs a single-field linear stencil");
+  if (s.kind == kSwe || s.kind == kSweFlux)
+    return fail(LOPE_ERR_UNSUPPORTED, "adjoint needs a single-field linear stencil");
+  if (s.stages != 1) return fail(LOPE_ERR_UNSUPPORTED, "adjoint of a multi-stage scheme is not implemented");
   if (s.kind != kLinear) {
     for (int ax = 0; ax < 3; ++ax)
       for (int sd = 0; sd < 2; ++sd)
@@ -594,12 +658,14 @@ lope_status lope_stencil_create_builtin(lope_stencil** stencil, const char* name
   std::memset(h, 0, sizeof(*h));
   StencilDesc& s = h->s;
   s.star = true;
+  s.stages = 1;
   std::string n(name);
   int want = 1;
   if (n == "jacobi5") { s.kind = kJacobi5; s.ndim = 2; s.radius = 1; }
   else if (n == "diff7") { s.kind = kDiff7; s.ndim = 3; s.radius = 1; }
   else if (n == "star9r2") { s.kind = kStar9r2; s.ndim = 2; s.radius = 2; }
   else if (n == "swe_cgrid") { s.kind = kSwe; s.ndim = 2; s.radius = 1; want = 3; }
+  else if (n == "swe_flux") { s.kind = kSweFlux; s.ndim = 2; s.radius = 1; s.star = false; want = 4; }
   else { delete h; return fail(LOPE_ERR_INVALID, "unknown builtin stencil name"); }
   if (nparams != want || !params) { delete h; return fail(LOPE_ERR_INVALID, "wrong parameter count"); }
   for (int i = 0; i < want; ++i) {
@@ -623,6 +689,7 @@ lope_status lope_stencil_create_linear(lope_stencil** stencil, int ndim, int rad
   s.kind = kLinear;
   s.ndim = ndim;
   s.radius = radius;
+  s.stages = 1;
   const int side = 2 * radius + 1, zs = ndim == 3 ? side : 1, zr = ndim == 3 ? radius : 0;
   bool star = true;
   for (int dz = 0; dz < zs; ++dz)
@@ -646,6 +713,20 @@ lope_status lope_stencil_create_linear(lope_stencil** stencil, int ndim, int rad
 }
 
 void lope_stencil_destroy(lope_stencil* stencil) { delete stencil; }
+
+lope_status lope_stencil_set_scheme(lope_stencil* stencil, lope_scheme scheme) {
+  if (!stencil) return fail(LOPE_ERR_INVALID, "NULL stencil");
+  if (scheme != LOPE_SCHEME_EULER && scheme != LOPE_SCHEME_RK2 && scheme != LOPE_SCHEME_RK3)
+    return fail(LOPE_ERR_INVALID, "unknown time-stepping scheme");
+  stencil->s.stages = int(scheme);
+  return LOPE_OK;
+}
+
+lope_status lope_work_states(const lope_stencil* stencil, int* states) {
+  if (!stencil || !states) return fail(LOPE_ERR_INVALID, "NULL argument");
+  *states = work_states(stencil->s);
+  return LOPE_OK;
+}
 
 lope_status lope_apply(const lope_grid* grid, const lope_stencil* stencil, const void* const* in,
                        void* const* out, void* const* work, int64_t nsteps, void* cuda_stream) {
@@ -727,6 +808,7 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
   if (!aligned16(workspace)) return fail(LOPE_ERR_INVALID, "workspace not 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const StencilDesc& s = stencil->s;
+  if (s.stages != 1) return fail(LOPE_ERR_UNSUPPORTED, "the batched kernel runs forward-Euler stencils only");
   const int dtype = grids[0]->g.dtype;
   for (int i = 0; i < n; ++i) {
     lope_status rs = check_pair(grids[i], stencil);

@@ -61,13 +61,13 @@ struct F2 {
     return r;
   }
   __device__ __forceinline__ float lo() const {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    float a;
+    asm("{\n\t.reg .b32 t;\n\tmov.b64 {%0, t}, %1;\n\t}" : "=f"(a) : "l"(v));
     return a;
   }
   __device__ __forceinline__ float hi() const {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    float b;
+    asm("{\n\t.reg .b32 t;\n\tmov.b64 {t, %0}, %1;\n\t}" : "=f"(b) : "l"(v));
     return b;
   }
 };
@@ -82,9 +82,14 @@ __device__ __forceinline__ F2 sub(F2 a, F2 b) {
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
   return d;
 }
+// The packed product is an FMA with a -0 addend (a*b + -0 = a*b exactly, with
+// the sign of a zero product kept): ptxas contracts a packed mul.rn followed
+// by a packed add/sub into a single FMA despite the rounding qualifier
+// (measured on sm_103a), which would round a product once less than the
+// scalar paths do; an FMA is never contracted further.
 __device__ __forceinline__ F2 mul(F2 a, F2 b) {
   F2 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(0x8000000080000000ull));
   return d;
 }
 __device__ __forceinline__ F2 fma_(F2 a, F2 b, F2 c) {
@@ -277,6 +282,60 @@ struct OpSwe {
   }
 };
 
+// Nonlinear shallow water on an Arakawa C-grid in flux form (fields eta =
+// h - H, u, v; unit spacing; forward Euler).  Mass: eta' = eta - dt [F(i) -
+// F(i-1) + G(j) - G(j-1)] with F = (H + face mean of eta) u and G likewise
+// with v.  Momentum: Coriolis on the four-face means vbar / ubar (which read
+// the corner taps U(+1,-1) of v and U(-1,+1) of u), the pressure gradient,
+// and centred advection u D_x u + vbar D_y u (resp. ubar D_x v + v D_y v).
+// A non-linear physics operator (Sec. 5, Limitations) written as one local
+// function: products of halo values, three fields, a box halo.
+//
+// Every product that feeds a sum is written as an FMA (the flux differences
+// below): the compiler may contract a packed multiply followed by a packed
+// add into one FMA on its own, so leaving no such pair keeps the packed and
+// scalar paths bitwise identical.
+struct OpSweFlux {
+  static constexpr int NDIM = 2, R = 1, NF = 3;
+  static constexpr bool REDUCES = false, STAR = false;
+  Coef dt, mdt, mg, f, mf, H, mH;  // dt, -dt, -g, f, -f, H, -H
+  template <class C, class A>
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[3], C&) const {
+    const C half = C(0.5f), quarter = C(0.25f), mhalf = C(-0.5f);
+    const C h = H.get(C()), mh = mH.get(C());
+    const C e = U(0, 0, 0, 0), eE = U(0, 1, 0, 0), eW = U(0, -1, 0, 0);
+    const C eN = U(0, 0, 1, 0), eS = U(0, 0, -1, 0);
+    const C u = U(1, 0, 0, 0), uW = U(1, -1, 0, 0), uE = U(1, 1, 0, 0);
+    const C uN = U(1, 0, 1, 0), uS = U(1, 0, -1, 0), uWN = U(1, -1, 1, 0);
+    const C v = U(2, 0, 0, 0), vS = U(2, 0, -1, 0), vN = U(2, 0, 1, 0);
+    const C vE = U(2, 1, 0, 0), vW = U(2, -1, 0, 0), vES = U(2, 1, -1, 0);
+    // F(i) - F(i-1) = hbar_E u + (-hbar_W) u_W; the negated face depth is
+    // computed with negated coefficients, which is exact.
+    const C dF = fma_(fma_(half, add(e, eE), h), u, mul(fma_(mhalf, add(eW, e), mh), uW));
+    const C dG = fma_(fma_(half, add(e, eN), h), v, mul(fma_(mhalf, add(eS, e), mh), vS));
+    o[0] = fma_(mdt.get(C()), add(dF, dG), e);
+    const C vbar = mul(quarter, add(add(v, vE), add(vS, vES)));
+    const C ubar = mul(quarter, add(add(u, uW), add(uN, uWN)));
+    const C au = mul(mhalf, fma_(u, sub(uE, uW), mul(vbar, sub(uN, uS))));
+    const C tu = fma_(f.get(C()), vbar, fma_(mg.get(C()), sub(eE, e), au));
+    o[1] = fma_(dt.get(C()), tu, u);
+    const C av = mul(mhalf, fma_(ubar, sub(vE, vW), mul(v, sub(vN, vS))));
+    const C tv = fma_(mf.get(C()), ubar, fma_(mg.get(C()), sub(eN, e), av));
+    o[2] = fma_(dt.get(C()), tv, v);
+  }
+  static OpSweFlux make(const double* prm) {
+    OpSweFlux op;
+    op.dt = prm[0];
+    op.mdt = -prm[0];
+    op.mg = -prm[1];
+    op.f = prm[2];
+    op.mf = -prm[2];
+    op.H = prm[3];
+    op.mH = -prm[3];
+    return op;
+  }
+};
+
 // General linear star stencil: w[axis][d + R], axis 0 = x (fastest), 1 = y,
 // 2 = z; the centre weight sits in w[0][R] only.
 template <int ND, int RR>
@@ -354,6 +413,43 @@ struct OpAdjDiffusion {
     }
     o[0] = fma_(c.get(C()), lt, l);
     red = fma_(lt, to_c(__ldg(ut + U.gidx())), red);
+  }
+};
+
+// Load a stored value (or an aligned pair of adjacent values) of global memory
+// in compute precision.
+__device__ __forceinline__ float ldc(const float* p, float) { return __ldg(p); }
+__device__ __forceinline__ float ldc(const __nv_bfloat16* p, float) { return __bfloat162float(p[0]); }
+__device__ __forceinline__ double ldc(const double* p, double) { return __ldg(p); }
+__device__ __forceinline__ F2 ldc(const float* p, F2) {
+  F2 r;
+  r.v = __ldg(reinterpret_cast<const unsigned long long*>(p));
+  return r;
+}
+__device__ __forceinline__ F2 ldc(const __nv_bfloat16* p, F2) {
+  const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  return F2::make(f.x, f.y);
+}
+
+// One later stage of a multi-stage (Runge-Kutta) step: out = a * base + b *
+// E(in), where E is the wrapped local function (one forward-Euler step), `in`
+// the previous stage's state (read with its halo) and `base` the state at the
+// start of the step, read only at the local element.  Because base is read
+// only where the stage writes, it may be the stage's own output buffer.
+template <class Op, class T>
+struct OpStage {
+  static constexpr int NDIM = Op::NDIM, R = Op::R, NF = Op::NF;
+  static constexpr bool REDUCES = false, STAR = Op::STAR;
+  Op op;
+  Coef a, b;
+  const T* base[kMaxFields];
+  template <class C, class A>
+  __device__ __forceinline__ void operator()(const A& U, C (&o)[NF], C& red) const {
+    C e[NF];
+    op(U, e, red);
+    const int64_t g = U.gidx();
+#pragma unroll
+    for (int f = 0; f < NF; ++f) o[f] = fma_(b.get(C()), e[f], mul(a.get(C()), ldc(base[f] + g, C())));
   }
 };
 

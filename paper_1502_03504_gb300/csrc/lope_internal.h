@@ -10,7 +10,7 @@
 namespace lope {
 
 // Stencil kinds (builtin names of lope_stencil_create_builtin).
-enum : int { kLinear = 0, kJacobi5 = 1, kDiff7 = 2, kStar9r2 = 3, kSwe = 4 };
+enum : int { kLinear = 0, kJacobi5 = 1, kDiff7 = 2, kStar9r2 = 3, kSwe = 4, kSweFlux = 5 };
 enum : int { kF64 = 0, kF32 = 1, kBF16 = 2 };
 enum : int { kPeriodic = 0, kDirichlet = 1 };
 enum : int { kPathAuto = 0, kPathTma = 1, kPathTrap = 2, kPathDirect = 3 };
@@ -39,8 +39,9 @@ struct StencilDesc {
   int kind;
   int ndim;
   int radius;
+  int stages;          // time-stepping scheme: 1 forward Euler (the function itself), 2 / 3 SSP-RK
   bool star;           // only axis-aligned taps
-  double prm[4];       // c | dt, g, H
+  double prm[4];       // c | dt, g, H | dt, g, f, H
   double box[125];     // (2r+1)^ndim weight table, slowest offset first
   double star_w[3][2 * kMaxRadius + 1];  // per axis (0 = x, 1 = y, 2 = z), centre in [0][r]
 };
@@ -55,19 +56,45 @@ struct StepArgs {
   int tile_x, tile_y;
   bool adjoint;          // run the transposed stencil (lambda halo: Dirichlet -> 0)
   const void* ut;        // adjoint: state u_t read at the local element
+  const void* base[kMaxFields];  // RK stage >= 2: state at the start of the step
+  double rk_a, rk_b;     // RK stage >= 2: out = rk_a * base + rk_b * E(in)
+  int stage;             // RK: 0/1 plain sweep of E; >= 2 combining stage (TMA/direct)
   double* partials;      // adjoint: per-block FP64 partial sums (accumulated)
   int partial_count;     // adjoint: number of partial slots available
   int* err;              // device error flag
   cudaStream_t stream;
 };
 
+// Coefficients (a, b) of stage s (1-based, s >= 2) of the strong-stability-
+// preserving Runge-Kutta schemes (Shu and Osher, 1988) with `stages` stages,
+// written as convex combinations of forward-Euler steps:
+//   RK2: u1 = E(u); u+ = 1/2 u + 1/2 E(u1)
+//   RK3: u1 = E(u); u2 = 3/4 u + 1/4 E(u1); u+ = 1/3 u + 2/3 E(u2)
+// Stage 1 is E itself (a = 0, b = 1).
+__host__ __device__ inline void rk_coeffs(int stages, int s, double* a, double* b) {
+  if (stages == 2) {
+    *a = 0.5;
+    *b = 0.5;
+  } else if (s == 2) {
+    *a = 0.75;
+    *b = 0.25;
+  } else {
+    *a = 1.0 / 3.0;
+    *b = 2.0 / 3.0;
+  }
+}
+
 // Launchers (each returns the number of blocks it used through *blocks when
 // non-NULL, so that the adjoint can size its partial-sum buffer).
 cudaError_t launch_tma(const StepArgs& a, int* blocks);
+cudaError_t launch_tma_stage(const StepArgs& a);  // a.stage >= 2 (k_tma_stage.cu)
 bool tma_supported(const StepArgs& a);
 cudaError_t launch_trap2d(const StepArgs& a);
 bool trap2d_supported(const StepArgs& a);
 cudaError_t launch_direct(const StepArgs& a, int* blocks);
+// Multi-stage forms on the generic kernels (k_generic_rk.cu): fused trapezoid
+// steps (trap) or a combining stage on the direct kernel.
+cudaError_t launch_generic_rk(const StepArgs& a, bool trap, int* blocks);
 bool direct_supported(const StepArgs& a);
 int tma_blocks(const StepArgs& a);
 int direct_blocks(const StepArgs& a);
@@ -107,7 +134,7 @@ struct BatchPlanDev {
 cudaError_t launch_batch(const BatchPlanDev& p, const StencilDesc& s, int dtype, int blocks,
                          cudaStream_t st);
 int batch_max_blocks(const StencilDesc& s, int dtype, int tile_x, int tile_y, int ksteps);
-size_t trap_smem_bytes(int dtype, int nf, int tile_x, int tile_y, int halo);
+size_t trap_smem_bytes(int dtype, int nf, int tile_x, int tile_y, int halo, int stages = 1);
 
 void count_launches(int64_t n);
 

@@ -123,4 +123,115 @@ __device__ __forceinline__ void trap_tile(const Op& op, const T* const* src, T* 
   __syncthreads();
 }
 
+// One sweep of the window region [lo, W-lo) x [lo, H-lo) for the multi-stage
+// tile: nxt = E(cur), or, when `comb`, nxt = a * base + b * E(cur) (base read
+// at the local element only).  Cells outside a Dirichlet side keep their halo
+// value.  Every value is rounded to the storage precision, as a stage written
+// to memory would be.
+template <class Op, class T>
+__device__ __forceinline__ void trap_rk_sweep(const Op& op, const C_t<T>* cur, C_t<T>* nxt,
+                                              const C_t<T>* base, bool comb, const Coef& ca,
+                                              const Coef& cb, const TrapGrid& g, int x0, int y0,
+                                              int h, int W, int H, int lo, bool inside) {
+  using C = C_t<T>;
+  constexpr int NF = Op::NF;
+  const int HW = W * H;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32, ny_t = blockDim.x / 32;
+  for (int j = lo + ty; j < H - lo; j += ny_t) {
+    const int gy = y0 - h + j;
+    for (int i = lo + tx; i < W - lo; i += 32) {
+      const int gx = x0 - h + i;
+      double v;
+      if (!inside && outside_dirichlet(g, gy, gx, &v)) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) nxt[f * HW + j * W + i] = C(v);
+        continue;
+      }
+      TrapAcc<C, NF> acc{cur, W, HW, i, j};
+      C o[NF];
+      C unused = C(0);
+      op(acc, o, unused);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        C r = o[f];
+        if (comb) r = fma_(cb.get(C()), r, mul(ca.get(C()), base[f * HW + j * W + i]));
+        nxt[f * HW + j * W + i] = to_storage_precision<T>(r);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Multi-stage (Runge-Kutta) steps fused in one tile: k steps of `stages`
+// stages, each stage one sweep of the local function E plus, from stage 2 on,
+// a pointwise combination with the state at the start of the step (the
+// strong-stability-preserving forms of Shu and Osher, see rk_coeffs).  The
+// window carries a halo of R * stages * k cells; each stage shrinks the valid
+// region by R, exactly as k * stages plain sweeps would.  The intermediate
+// stage states -- the storage the paper's Limitations paragraph (Sec. 5) says
+// LOPe does not provide -- live in shared memory only.  smem holds 3 * NF * H
+// * W values of C.
+template <class Op, class T>
+__device__ __forceinline__ void trap_tile_rk(const Op& op, const T* const* src, T* const* dst,
+                                             const TrapGrid& g, int x0, int y0, int TX, int TY,
+                                             int k, int stages, C_t<T>* smem) {
+  using C = C_t<T>;
+  constexpr int R = Op::R, NF = Op::NF;
+  const int h = R * stages * k;
+  const int W = TX + 2 * h, H = TY + 2 * h, HW = W * H;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32, ny_t = blockDim.x / 32;
+  C* bu = smem;
+  C* b1 = smem + NF * HW;
+  C* b2 = smem + 2 * NF * HW;
+  const bool inside = x0 - h >= 0 && y0 - h >= 0 && x0 + TX + h <= g.nx && y0 + TY + h <= g.ny;
+  for (int j = ty; j < H; j += ny_t) {
+    const int gy = y0 - h + j;
+    for (int i = tx; i < W; i += 32) {
+      const int gx = x0 - h + i;
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        bu[f * HW + j * W + i] = inside ? to_c(__ldcg(src[f] + int64_t(gy) * g.nx + gx))
+                                        : halo_read<T>(src[f], g, gy, gx);
+    }
+  }
+  __syncthreads();
+  Coef a2, b2c, a3, b3c;
+  {
+    double a, b;
+    rk_coeffs(stages, 2, &a, &b);
+    a2 = a;
+    b2c = b;
+    rk_coeffs(stages, 3, &a, &b);
+    a3 = a;
+    b3c = b;
+  }
+  int lo = 0;
+  for (int step = 0; step < k; ++step) {
+    lo += R;
+    trap_rk_sweep<Op, T>(op, bu, b1, nullptr, false, a2, b2c, g, x0, y0, h, W, H, lo, inside);
+    lo += R;
+    trap_rk_sweep<Op, T>(op, b1, b2, bu, true, a2, b2c, g, x0, y0, h, W, H, lo, inside);
+    if (stages == 2) {
+      C* t = bu; bu = b2; b2 = t;
+    } else {
+      lo += R;
+      trap_rk_sweep<Op, T>(op, b2, b1, bu, true, a3, b3c, g, x0, y0, h, W, H, lo, inside);
+      C* t = bu; bu = b1; b1 = t;
+    }
+  }
+  for (int j = ty; j < TY; j += ny_t) {
+    const int gy = y0 + j;
+    if (gy >= g.ny) break;
+    for (int i = tx; i < TX; i += 32) {
+      const int gx = x0 + i;
+      if (gx < g.nx) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          dst[f][int64_t(gy) * g.nx + gx] = from_c<T>(bu[f * HW + (j + h) * W + (i + h)]);
+      }
+    }
+  }
+  __syncthreads();
+}
+
 }  // namespace lope
