@@ -11,6 +11,7 @@ from .oracle import (  # noqa: F401
     KIND,
     adjoint,
     apply,
+    apply_source,
     build,
     max_threads,
     vjp,

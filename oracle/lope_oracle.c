@@ -51,7 +51,8 @@ enum {
   OR_DIFF7 = 2,    /* 3D: u + c (sum of 6 face neighbours - 6u)               */
   OR_STAR9R2 = 3,  /* 2D: u + c (L4x u + L4y u), 4th-order 1D Laplacians      */
   OR_SWE = 4,      /* 2D, 3 fields (h,u,v): linearised C-grid shallow water   */
-  OR_SWEFLUX = 5   /* 2D, 3 fields (eta,u,v): nonlinear flux-form C-grid SWE  */
+  OR_SWEFLUX = 5,  /* 2D, 3 fields (eta,u,v): nonlinear flux-form C-grid SWE  */
+  OR_USER = 6      /* a user-written local function (see oracle_apply_user)   */
 };
 
 enum { OR_OK = 0, OR_ERR = 1 };
@@ -71,9 +72,16 @@ typedef struct {
   int64_t p[3];             /* the local element                              */
 } or_acc;
 
+/* A user-written local function: reads taps through U(acc, f, dx, dy, dz) and
+ * writes out[f]; P holds its parameters. */
+typedef double (*or_tap_fn)(const void* acc, int f, int dx, int dy, int dz);
+typedef void (*or_user_fn)(const void* acc, or_tap_fn U, const double* P, double* out);
+
 typedef struct {
   int kind;
   int radius;             /* for OR_LINEAR                                    */
+  or_user_fn user;        /* for OR_USER                                      */
+  int user_nf;            /* for OR_USER                                      */
   const double* prm;      /* c, or (dt, g, H) for OR_SWE, (dt, g, f, H) for OR_SWEFLUX */
   const double* w;        /* OR_LINEAR weights, (2r+1)^ndim, slowest first    */
 } or_stencil;
@@ -206,6 +214,12 @@ static double lf_dcoef(const or_acc* a, int kind) {
 }
 
 static int nfields_of(int kind) { return (kind == OR_SWE || kind == OR_SWEFLUX) ? 3 : 1; }
+static int stencil_nf(const or_stencil* s) { return s->kind == OR_USER ? s->user_nf : nfields_of(s->kind); }
+
+/* U() in the form a user-written function calls it. */
+static double tap(const void* acc, int f, int dx, int dy, int dz) {
+  return U((const or_acc*)acc, f, dx, dy, dz);
+}
 
 static int make_grid(or_grid* g, int ndim, const int64_t* ext, const int* bc, const double* bval) {
   if (ndim != 2 && ndim != 3) return OR_ERR;
@@ -230,7 +244,7 @@ static int make_grid(or_grid* g, int ndim, const int64_t* ext, const int* bc, co
 /* One sweep: out = f(in) at every point, from the frozen snapshot `in`. */
 static void sweep(const or_grid* g, const or_stencil* s, double* const* in, double* const* out,
                   int nthreads) {
-  int nf = nfields_of(s->kind);
+  int nf = stencil_nf(s);
   int64_t n0 = g->n[0], n1 = g->n[1], n2 = g->n[2];
   int64_t outer = g->ndim == 3 ? n0 : n1;
   (void)nthreads;
@@ -252,6 +266,7 @@ static void sweep(const or_grid* g, const or_stencil* s, double* const* in, doub
             case OR_STAR9R2: lf_star9r2(&a, s->prm, r); break;
             case OR_SWE: lf_swe(&a, s->prm, r); break;
             case OR_SWEFLUX: lf_swe_flux(&a, s->prm, r); break;
+            case OR_USER: s->user(&a, tap, s->prm, r); break;
             default: lf_linear(&a, g->ndim, s->radius, s->w, r); break;
           }
           int64_t idx = (z * n1 + y) * n2 + x;
@@ -266,6 +281,7 @@ static int check_stencil(const or_grid* g, const or_stencil* s) {
       return g->ndim == 2 ? OR_OK : OR_ERR;
     case OR_DIFF7: return g->ndim == 3 ? OR_OK : OR_ERR;
     case OR_LINEAR: return (s->radius >= 0 && s->w) ? OR_OK : OR_ERR;
+    case OR_USER: return (s->user && s->user_nf >= 1 && s->user_nf <= OR_MAXF) ? OR_OK : OR_ERR;
     default: return OR_ERR;
   }
 }
@@ -277,7 +293,7 @@ int oracle_apply(int ndim, const int64_t* ext, const int* bc, const double* bval
                  double* const* out, int64_t nsteps, int nthreads) {
   or_grid g;
   if (make_grid(&g, ndim, ext, bc, bval) != OR_OK) return OR_ERR;
-  or_stencil s = {kind, radius, prm, weights};
+  or_stencil s = {kind, radius, NULL, 0, prm, weights};
   if (check_stencil(&g, &s) != OR_OK) return OR_ERR;
   int nf = nfields_of(kind);
   int64_t n = npoints(&g);
@@ -319,15 +335,13 @@ static void combine(double* dst, double a, const double* base, double b, const d
   for (int64_t i = 0; i < n; i++) dst[i] = a * base[i] + b * e[i];
 }
 
-int oracle_apply_rk(int ndim, const int64_t* ext, const int* bc, const double* bval, int kind,
-                    const double* prm, int radius, const double* weights, int stages,
-                    const double* const* in, double* const* out, int64_t nsteps, int nthreads) {
-  or_grid g;
-  if (make_grid(&g, ndim, ext, bc, bval) != OR_OK) return OR_ERR;
-  or_stencil s = {kind, radius, prm, weights};
+static int apply_scheme(const or_grid* gp, const or_stencil* sp, int stages,
+                        const double* const* in, double* const* out, int64_t nsteps, int nthreads) {
+  const or_grid g = *gp;
+  const or_stencil s = *sp;
   if (check_stencil(&g, &s) != OR_OK) return OR_ERR;
   if (stages < 1 || stages > 3) return OR_ERR;
-  int nf = nfields_of(kind);
+  int nf = stencil_nf(&s);
   int64_t n = npoints(&g);
   double *u[OR_MAXF], *st[OR_MAXF], *e[OR_MAXF];
   for (int k = 0; k < nf; k++) {
@@ -360,6 +374,27 @@ int oracle_apply_rk(int ndim, const int64_t* ext, const int* bc, const double* b
     free(e[k]);
   }
   return OR_OK;
+}
+
+int oracle_apply_rk(int ndim, const int64_t* ext, const int* bc, const double* bval, int kind,
+                    const double* prm, int radius, const double* weights, int stages,
+                    const double* const* in, double* const* out, int64_t nsteps, int nthreads) {
+  or_grid g;
+  if (make_grid(&g, ndim, ext, bc, bval) != OR_OK) return OR_ERR;
+  or_stencil s = {kind, radius, NULL, 0, prm, weights};
+  return apply_scheme(&g, &s, stages, in, out, nsteps, nthreads);
+}
+
+/* A user-written local function `fn` with nf fields (the same text the library
+ * compiles for the GPU, compiled here for the host in FP64 by oracle/oracle.py),
+ * applied nsteps times with the scheme of `stages` stages. */
+int oracle_apply_user(int ndim, const int64_t* ext, const int* bc, const double* bval, int nf,
+                      or_user_fn fn, const double* prm, int stages, const double* const* in,
+                      double* const* out, int64_t nsteps, int nthreads) {
+  or_grid g;
+  if (make_grid(&g, ndim, ext, bc, bval) != OR_OK) return OR_ERR;
+  or_stencil s = {OR_USER, 0, fn, nf, prm, NULL};
+  return apply_scheme(&g, &s, stages, in, out, nsteps, nthreads);
 }
 
 /* Weight table of a linear stencil, (2r+1)^ndim entries, slowest offset
@@ -438,7 +473,7 @@ int oracle_vjp(int ndim, const int64_t* ext, const int* bc, const double* bval, 
                const double* lamT, int64_t nsteps, double* grad_u0, double* grad_c, int nthreads) {
   or_grid g;
   if (make_grid(&g, ndim, ext, bc, bval) != OR_OK) return OR_ERR;
-  or_stencil s = {kind, radius, prm, weights};
+  or_stencil s = {kind, radius, NULL, 0, prm, weights};
   if (kind == OR_SWE || kind == OR_SWEFLUX || check_stencil(&g, &s) != OR_OK) return OR_ERR;
   int64_t n = npoints(&g);
   double w[125];

@@ -57,6 +57,10 @@ def _load():
             lib.oracle_apply_rk.argtypes = [ctypes.c_int, _I64, _I, _D, ctypes.c_int, _D,
                                             ctypes.c_int, _D, ctypes.c_int, _DD, _DD,
                                             ctypes.c_int64, ctypes.c_int]
+            lib.oracle_apply_user.restype = ctypes.c_int
+            lib.oracle_apply_user.argtypes = [ctypes.c_int, _I64, _I, _D, ctypes.c_int,
+                                              ctypes.c_void_p, _D, ctypes.c_int, _DD, _DD,
+                                              ctypes.c_int64, ctypes.c_int]
             lib.oracle_vjp.restype = ctypes.c_int
             lib.oracle_vjp.argtypes = [ctypes.c_int, _I64, _I, _D, ctypes.c_int, _D, ctypes.c_int,
                                        _D, _D, _D, ctypes.c_int64, _D, _D, ctypes.c_int]
@@ -192,3 +196,72 @@ def adjoint(u0, target, kind, params=None, nsteps=1, bc=None, bval=None, weights
     if rc != 0:
         raise ValueError("oracle_adjoint rejected its arguments")
     return float(loss[0]), g, float(gc[0])
+
+
+# ---------------------------------------------------------------- user source
+# A local function written as source (the text the library compiles for the
+# GPU) is compiled here for the host with g++, in FP64: C is double, U reads
+# the oracle's own boundary-aware accessor, and add/sub/mul/fma_ are the plain
+# double operations.  The body is the definition; nothing of the GPU path is
+# involved.
+_USER_PRELUDE = """
+namespace {
+typedef double C;
+inline double add(double a, double b) { return a + b; }
+inline double sub(double a, double b) { return a - b; }
+inline double mul(double a, double b) { return a * b; }
+inline double fma_(double a, double b, double c) { return a * b + c; }
+}
+extern "C" void lope_user_lf(const void* acc, double (*Uf)(const void*, int, int, int, int),
+                             const double* P, double* out) {
+  auto U = [&](int f, int dx, int dy, int dz = 0) -> double { return Uf(acc, f, dx, dy, dz); };
+  (void)P;
+"""
+_USER_DIR = os.path.join(_HERE, "_user")
+_user_libs = {}
+
+
+def _user_fn(body: str):
+    import hashlib
+
+    key = hashlib.sha256(body.encode()).hexdigest()[:20]
+    with _lock:
+        if key in _user_libs:
+            return _user_libs[key]
+        os.makedirs(_USER_DIR, exist_ok=True)
+        so = os.path.join(_USER_DIR, f"lf_{key}.so")
+        if not os.path.exists(so):
+            src = os.path.join(_USER_DIR, f"lf_{key}.{os.getpid()}.cpp")
+            with open(src, "w") as fh:
+                fh.write(_USER_PRELUDE + "#line 1 \"local_function\"\n" + body + "\n}\n")
+            tmp = so + f".tmp{os.getpid()}"
+            subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
+                            src, "-o", tmp], check=True)
+            os.replace(tmp, so)
+            os.remove(src)
+        lib = ctypes.CDLL(so)
+        fn = ctypes.cast(lib.lope_user_lf, ctypes.c_void_p).value
+        _user_libs[key] = (lib, fn)
+        return _user_libs[key]
+
+
+def apply_source(fields, body, params=(), nsteps=1, bc=None, bval=None, nthreads=1,
+                 scheme="euler"):
+    """Apply a user-written local function (source text) ``nsteps`` times in FP64."""
+    lib = _load()
+    _, fn = _user_fn(body)
+    single = isinstance(fields, np.ndarray)
+    fl = [fields] if single else list(fields)
+    ins = [np.ascontiguousarray(f, dtype=np.float64) for f in fl]
+    ndim, ext, bcs, bvs = _grid_args(ins[0].shape, bc, bval)
+    prm = np.zeros(8, dtype=np.float64)
+    prm[: len(params)] = params
+    outs = [np.empty_like(a) for a in ins]
+    in_arr = (_D * len(ins))(*[_dptr(a) for a in ins])
+    out_arr = (_D * len(outs))(*[_dptr(a) for a in outs])
+    rc = lib.oracle_apply_user(ndim, ext.ctypes.data_as(_I64), bcs.ctypes.data_as(_I), _dptr(bvs),
+                               len(ins), fn, _dptr(prm), SCHEME_STAGES[scheme], in_arr, out_arr,
+                               int(nsteps), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_apply_user rejected its arguments")
+    return outs[0] if single else outs
