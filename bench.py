@@ -12,7 +12,8 @@ launch (512 uneven 2D grids, 20 steps) against per-grid launches, the forward +
 adjoint (256^3, 100 steps, checkpoint every 10) against the plain forward,
 the shallow-water multi-field forms (linear, and nonlinear flux form with a box
 halo) in FP32 and BF16, SSP-RK3 steps of the nonlinear form (fused against one
-launch per stage), and the FP64 256^2 case.
+launch per stage), local functions written as source and compiled at run time
+(against the builtin, and Gray-Scott), and the FP64 256^2 case.
 
 --impl reference times the FP64 oracle on the host cores instead (bounded
 samples of the same workload mix).  Under torchrun every rank runs its own
@@ -375,7 +376,7 @@ def main():
         del u3_h, u2_h, h_o3, h_o2
         for name, fn in (("fp64_256", form_fp64), ("swe_4096", form_swe), ("batched_512", form_batch),
                          ("fwd_adjoint_256", form_adjoint), ("swe_flux_4096", form_swe_flux),
-                         ("rk3_swe_flux_4096", form_rk3)):
+                         ("rk3_swe_flux_4096", form_rk3), ("user_source", form_user_source)):
             try:
                 forms[name] = fn(L, LI, torch, dev, peak)
             except Exception as e:  # reported, never hidden
@@ -574,6 +575,55 @@ def form_rk3(L, LI, torch, dev, peak):
             "stage_frac_of_peak": 96 * pts / (ms_stage / 1e3) / 1e9 / peak,
             "euler_150_sweeps_ms": ms_euler,
             "fused_speedup_vs_stage_launches": ms_stage / ms_fused}
+
+
+# Local functions written as source (compiled at run time by the library).
+SRC_DIFF7 = """
+const C u = U(0, 0, 0, 0);
+const C nb = add(add(add(U(0, -1, 0, 0), U(0, 1, 0, 0)), add(U(0, 0, -1, 0), U(0, 0, 1, 0))),
+                 add(U(0, 0, 0, -1), U(0, 0, 0, 1)));
+out[0] = fma_(P[0], fma_(C(-6), u, nb), u);
+"""
+SRC_GRAY_SCOTT = """
+const C u = U(0, 0, 0), v = U(1, 0, 0);
+const C lu = fma_(C(-4), u, add(add(U(0, -1, 0), U(0, 1, 0)), add(U(0, 0, -1), U(0, 0, 1))));
+const C lv = fma_(C(-4), v, add(add(U(1, -1, 0), U(1, 1, 0)), add(U(1, 0, -1), U(1, 0, 1))));
+const C uvv = mul(u, mul(v, v));
+out[0] = fma_(P[0], fma_(P[1], lu, fma_(P[3], sub(C(1), u), -uvv)), u);
+out[1] = fma_(P[0], fma_(P[2], lv, fma_(-add(P[3], P[4]), v, uvv)), v);
+"""
+
+
+def form_user_source(L, LI, torch, dev, peak):
+    """User-written local functions compiled at run time: the 3D 7-point
+    diffusion written as source against the builtin (512^3 FP32 Dirichlet-0,
+    50 sweeps), and Gray-Scott reaction-diffusion (two coupled nonlinear
+    fields, no builtin) at 4096^2 FP32 periodic, 100 steps."""
+    n3, T3 = 512, 50
+    u = torch.from_numpy(LI.uniform_field(1001, (n3, n3, n3)).astype(np.float32)).to(dev)
+    o, w = torch.empty_like(u), torch.empty_like(u)
+    g = L.Grid((n3, n3, n3), "f32", halo=1)
+    g.set_boundary(kind="dirichlet", value=0.0)
+    src = L.Stencil.source(SRC_DIFF7, ndim=3, radius=1, params=[C3]).compile("f32")
+    ms_src = _time(torch, lambda: L.apply(g, src, u, out=o, work=w, nsteps=T3), reps=3)
+    ms_blt = _time(torch, lambda: L.apply(g, L.Stencil.builtin("diff7", C3), u, out=o, work=w,
+                                          nsteps=T3), reps=3)
+    del u, o, w
+    n, T = 4096, 100
+    prm = [1.0, 0.16, 0.08, 0.035, 0.065]
+    f = [torch.from_numpy((1.0 - 0.3 * LI.uniform_field(1205, (n, n))).astype(np.float32)).to(dev),
+         torch.from_numpy((0.25 * LI.uniform_field(1205, (n, n), offset=n * n)).astype(np.float32)).to(dev)]
+    fo = [torch.empty_like(x) for x in f]
+    fw = [torch.empty_like(x) for x in f]
+    g2 = L.Grid((n, n), "f32", halo=1, nfields=2)
+    gs = L.Stencil.source(SRC_GRAY_SCOTT, ndim=2, radius=1, nfields=2, params=prm).compile("f32")
+    ms_gs = _time(torch, lambda: L.apply(g2, gs, f, out=fo, work=fw, nsteps=T), reps=3)
+    gbps = 16 * n * n * T / (ms_gs / 1e3) / 1e9
+    return {"workload": "diff7 as source vs builtin (512^3 FP32 x50); Gray-Scott source 4096^2 x2 FP32 x100",
+            "diff7_source_ms": ms_src, "diff7_builtin_ms": ms_blt,
+            "source_over_builtin_time": ms_src / ms_blt,
+            "gray_scott_ms": ms_gs, "gray_scott_point_updates_per_s": n * n * T / (ms_gs / 1e3),
+            "gray_scott_alg_GBps": gbps, "gray_scott_frac_of_peak": gbps / peak}
 
 
 def form_batch(L, LI, torch, dev, peak):

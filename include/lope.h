@@ -94,6 +94,40 @@ lope_status lope_stencil_create_linear(lope_stencil** stencil, int ndim, int rad
                                        const double* weights);
 void lope_stencil_destroy(lope_stencil* stencil);
 
+/* A local function written by the user as source and compiled at run time:
+ * the analogue of the paper's compilation of CONCURRENT procedures written in
+ * the LOPe index notation (Sec. 2.2; Sec. 4 compiles them source to source),
+ * here with NVRTC straight to sm_103a code, into the same kernels the
+ * builtins use (TMA tiles / z-march, trapezoid tiles, direct kernel, and the
+ * multi-stage schemes).  `body` is the C++ body of the function.  Inside it:
+ *   C             the compute type (float for FP32/BF16 storage, double for
+ *                 FP64; on the paired TMA path a packed pair of floats);
+ *   U(f, dx, dy)  (2D) or U(f, dx, dy, dz) (3D): field f at the local offset,
+ *                 dx along the fastest axis (the paper's U(dx,dy)); offsets
+ *                 beyond `radius` are clamped to it, so the declared halo is the
+ *                 contract of Sec. 3.5 (no out-of-bounds reads);
+ *   P[0..7]       the parameters, in C;
+ *   out[f]        must be assigned for every field f < nfields;
+ *   add, sub, mul, fma_, C(x), and + - * on C values.
+ * Write every product that feeds a sum as fma_() and use add/sub/mul for the
+ * rest to get results that are bitwise equal on every kernel path (the
+ * compiler may contract packed a*b+c on its own).  box = 0 declares that the
+ * function reads only axis-aligned taps (star); box = 1 allows corner taps
+ * (2D TMA tiles; 3D box functions take the direct kernel).  The body is
+ * compiled on first use per storage type (or by lope_stencil_compile) and runs
+ * as trusted code.  Errors: LOPE_ERR_INVALID for out-of-range arguments.  A
+ * body that does not compile fails at lope_stencil_compile or at its first
+ * launch with LOPE_ERR_INVALID, and lope_last_error() gives the compiler log;
+ * without NVRTC (libnvrtc.so.13) those calls return LOPE_ERR_UNSUPPORTED. */
+lope_status lope_stencil_create_source(lope_stencil** stencil, int ndim, int radius, int nfields,
+                                       int box, const char* body, const double* params,
+                                       int nparams);
+
+/* Compile every kernel of a source stencil for one storage type now (NVRTC;
+ * no GPU needed), so that no launch compiles and a stream capture does not
+ * compile.  A no-op for builtin and linear stencils. */
+lope_status lope_stencil_compile(const lope_stencil* stencil, lope_dtype storage);
+
 /* Time-stepping scheme.  A local function is one forward-Euler step E(u) = u +
  * dt F(u) (EULER, the default: a step is one sweep).  RK2 and RK3 are the
  * strong-stability-preserving Runge-Kutta methods of Shu and Osher (1988)

@@ -53,7 +53,9 @@ from ._lib import (  # noqa: F401  (C ABI names)
     lope_set_option,
     lope_set_boundary,
     lope_stencil_create_builtin,
+    lope_stencil_compile,
     lope_stencil_create_linear,
+    lope_stencil_create_source,
     lope_stencil_destroy,
     lope_stencil_set_scheme,
     lope_sync_status,

@@ -61,6 +61,9 @@ _SIGS = {
     "lope_stencil_create_linear": (_INT, [ctypes.POINTER(_P), _INT, _INT, _DP]),
     "lope_stencil_destroy": (None, [_P]),
     "lope_stencil_set_scheme": (_INT, [_P, _INT]),
+    "lope_stencil_create_source": (_INT, [ctypes.POINTER(_P), _INT, _INT, _INT, _INT,
+                                          ctypes.c_char_p, _DP, _INT]),
+    "lope_stencil_compile": (_INT, [_P, _INT]),
     "lope_work_states": (_INT, [_P, ctypes.POINTER(_INT)]),
     "lope_apply": (_INT, [_P, _P, _PP, _PP, _PP, _I64, _P]),
     "lope_apply_with": (_INT, [_P, _P, _PP, _PP, _PP, _I64, ctypes.POINTER(Launch), _P]),
@@ -164,6 +167,20 @@ def lope_stencil_create_linear(ndim: int, radius: int, weights):
 
 
 SCHEMES = {"euler": 1, "rk2": 2, "rk3": 3}
+
+
+def lope_stencil_create_source(ndim: int, radius: int, nfields: int, box: bool, body: str,
+                               params: Sequence[float] = ()):
+    h = _P()
+    arr = (ctypes.c_double * max(1, len(params)))(*[float(p) for p in params])
+    _check(load().lope_stencil_create_source(ctypes.byref(h), int(ndim), int(radius),
+                                             int(nfields), int(bool(box)), body.encode(), arr,
+                                             len(params)))
+    return h
+
+
+def lope_stencil_compile(h, dtype: str):
+    _check(load().lope_stencil_compile(h, DTYPES[dtype]))
 
 
 def lope_stencil_set_scheme(h, scheme: int):
@@ -343,6 +360,21 @@ class Stencil:
         ndim = 3 if name == "diff7" else 2
         radius = 2 if name == "star9r2" else 1
         return cls(h, ndim, radius, 3 if name in ("swe_cgrid", "swe_flux") else 1)
+
+    @classmethod
+    def source(cls, body: str, ndim: int = 2, radius: int = 1, nfields: int = 1, params=(),
+               box: bool = False):
+        """A local function written as C++ source (see lope_stencil_create_source):
+        it reads U(f, dx, dy[, dz]) and P[i] and assigns out[f]."""
+        h = lope_stencil_create_source(ndim, radius, nfields, box, body, list(params))
+        st = cls(h, ndim, radius, nfields)
+        st.body = body
+        return st
+
+    def compile(self, dtype: str = "f32"):
+        """Compile a source stencil's kernels for a storage type now (no GPU needed)."""
+        lope_stencil_compile(self.handle, dtype)
+        return self
 
     @classmethod
     def linear(cls, weights):

@@ -21,7 +21,13 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblope.so")
 SOURCES = ["k_tma.cu", "k_tma_stage.cu", "k_generic.cu", "k_generic_rk.cu", "k_batch.cu",
-           "k_reduce.cu", "api.cu"]
+           "k_reduce.cu", "jit.cu", "api.cu"]
+# Device headers embedded in the library for run-time compiled local functions
+# (jit.cu hands them to NVRTC); they compile under nvcc and NVRTC alike.
+JIT_HEADERS = ["lope_internal.h", "device_common.cuh", "tma_device.cuh", "trap.cuh",
+               "generic_device.cuh"]
+JIT_GEN = "jit_headers.cpp"
+
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,10 +44,32 @@ def _deps():
     return files
 
 
+def _write_jit_headers() -> str:
+    """Generate the C++ file holding the device headers as string constants."""
+    delim = "LOPE_EMBED"
+    out = ["// Generated by build.py: device headers for run-time compilation.",
+           "namespace lope {", f"extern const int kJitHeaderCount = {len(JIT_HEADERS)};",
+           "extern const char* const kJitHeaderNames[] = {"]
+    out += [f'    "{h}",' for h in JIT_HEADERS]
+    out += ["};", "extern const char* const kJitHeaderTexts[] = {"]
+    for h in JIT_HEADERS:
+        with open(os.path.join(CSRC, h)) as fh:
+            text = fh.read()
+        if f"){delim}" in text:
+            raise RuntimeError(f"{h} contains the raw-string delimiter")
+        out.append(f'    R"{delim}({text}){delim}",')
+    out += ["};", "}  // namespace lope", ""]
+    path = os.path.join(BUILD, JIT_GEN)
+    with open(path, "w") as fh:
+        fh.write("\n".join(out))
+    return path
+
+
 def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+    obj = os.path.join(BUILD, os.path.splitext(os.path.basename(src))[0] + ".o")
+    path = src if os.path.isabs(src) else os.path.join(CSRC, src)
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
+           "-I", INCLUDE, "-I", CSRC, "-c", path, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -58,8 +86,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
+    sources = SOURCES + [_write_jit_headers()]
+    with cf.ThreadPoolExecutor(max_workers=len(sources)) as ex:
+        objs = list(ex.map(lambda s: _compile(s, verbose), sources))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread", "-ldl", "-lrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -30,6 +30,7 @@ struct lope_grid {
 struct lope_stencil {
   lope::StencilDesc s;
   int nf;
+  lope::JitProgram* jit;  // user-written local functions (owned)
 };
 
 namespace lope {
@@ -83,7 +84,10 @@ lope_status dev_state(DevState** out) {
 }
 
 // ------------------------------------------------------------------ validation
-int stencil_nf(const StencilDesc& s) { return (s.kind == kSwe || s.kind == kSweFlux) ? 3 : 1; }
+int stencil_nf(const StencilDesc& s) {
+  if (s.kind == kUser) return s.user_nf;
+  return (s.kind == kSwe || s.kind == kSweFlux) ? 3 : 1;
+}
 
 lope_status check_pair(const lope_grid* grid, const lope_stencil* st) {
   if (!grid || !st) return fail(LOPE_ERR_INVALID, "NULL grid or stencil");
@@ -136,7 +140,7 @@ struct Choice {
   int path, tile_x, tile_y, k;
 };
 
-using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int, int, int>;
+using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int, int, int, int64_t>;
 std::mutex g_tune_mu;
 std::map<TuneKey, Choice> g_tune;
 
@@ -145,7 +149,7 @@ TuneKey tune_key(const Geom& g, const StencilDesc& s) {
   for (int ax = 0; ax < 3; ++ax)
     for (int sd = 0; sd < 2; ++sd) bcs = bcs * 2 + (g.bc[ax][sd] == kDirichlet);
   return TuneKey(g.ndim, g.n[0], g.n[1], g.n[2], g.dtype, s.kind, s.radius, int(s.star), bcs,
-                 g.nf, s.stages);
+                 g.nf, s.stages, int64_t(reinterpret_cast<uintptr_t>(s.jit)));
 }
 
 StepArgs base_args(const Geom& g, const StencilDesc& s, int* err, cudaStream_t st) {
@@ -364,6 +368,10 @@ lope_status apply_impl(const lope_grid* grid, const lope_stencil* st, const void
   if (nsteps < 0) return fail(LOPE_ERR_INVALID, "nsteps < 0");
   const Geom& g = grid->g;
   const StencilDesc& s = st->s;
+  if (st->jit) {  // user source: compile for this storage type first (host only, cached)
+    std::string err;
+    if ((rs = jit_compile(st->jit, g.dtype, &err)) != LOPE_OK) return fail(rs, err);
+  }
   DevState* d = nullptr;
   if ((rs = dev_state(&d)) != LOPE_OK) return rs;
   Choice c;
@@ -430,7 +438,7 @@ lope_status check_linear_for_adjoint(const lope_grid* grid, const lope_stencil* 
   lope_status rs = check_pair(grid, st);
   if (rs != LOPE_OK) return rs;
   const StencilDesc& s = st->s;
-  if (s.kind == kSwe || s.kind == kSweFlux)
+  if (s.kind == kSwe || s.kind == kSweFlux || s.kind == kUser)
     return fail(LOPE_ERR_UNSUPPORTED, "adjoint needs a single-field linear stencil");
   if (s.stages != 1) return fail(LOPE_ERR_UNSUPPORTED, "adjoint of a multi-stage scheme is not implemented");
   if (s.kind != kLinear) {
@@ -712,7 +720,55 @@ lope_status lope_stencil_create_linear(lope_stencil** stencil, int ndim, int rad
   return LOPE_OK;
 }
 
-void lope_stencil_destroy(lope_stencil* stencil) { delete stencil; }
+void lope_stencil_destroy(lope_stencil* stencil) {
+  if (!stencil) return;
+  if (stencil->jit) lope::jit_destroy(stencil->jit);
+  delete stencil;
+}
+
+lope_status lope_stencil_create_source(lope_stencil** stencil, int ndim, int radius, int nfields,
+                                       int box, const char* body, const double* params,
+                                       int nparams) {
+  if (!stencil || !body) return fail(LOPE_ERR_INVALID, "NULL argument");
+  if ((ndim != 2 && ndim != 3) || radius < 1 || radius > kMaxRadius)
+    return fail(LOPE_ERR_INVALID, "ndim must be 2/3 and radius 1..2");
+  if (nfields < 1 || nfields > kMaxFields) return fail(LOPE_ERR_INVALID, "nfields must be 1..3");
+  if (nparams < 0 || nparams > kUserParams || (nparams > 0 && !params))
+    return fail(LOPE_ERR_INVALID, "at most 8 parameters");
+  for (int i = 0; i < nparams; ++i)
+    if (!std::isfinite(params[i])) return fail(LOPE_ERR_INVALID, "non-finite parameter");
+  auto* h = new (std::nothrow) lope_stencil;
+  if (!h) return fail(LOPE_ERR_ALLOC, "out of host memory");
+  std::memset(h, 0, sizeof(*h));
+  StencilDesc& s = h->s;
+  s.kind = kUser;
+  s.ndim = ndim;
+  s.radius = radius;
+  s.stages = 1;
+  s.star = box == 0;
+  s.user_nf = nfields;
+  for (int i = 0; i < nparams && i < 4; ++i) s.prm[i] = params[i];
+  lope_status rs = jit_create(body, ndim, radius, nfields, s.star, params, nparams, &h->jit);
+  if (rs != LOPE_OK) {
+    delete h;
+    return fail(rs, "out of host memory");
+  }
+  s.jit = h->jit;
+  h->nf = nfields;
+  *stencil = h;
+  return LOPE_OK;
+}
+
+lope_status lope_stencil_compile(const lope_stencil* stencil, lope_dtype storage) {
+  if (!stencil) return fail(LOPE_ERR_INVALID, "NULL stencil");
+  if (storage != LOPE_F64 && storage != LOPE_F32 && storage != LOPE_BF16)
+    return fail(LOPE_ERR_INVALID, "unknown dtype");
+  if (!stencil->jit) return LOPE_OK;  // builtin and linear stencils are compiled with the library
+  std::string err;
+  lope_status rs = jit_compile(stencil->jit, int(storage), &err);
+  if (rs != LOPE_OK) return fail(rs, err);
+  return LOPE_OK;
+}
 
 lope_status lope_stencil_set_scheme(lope_stencil* stencil, lope_scheme scheme) {
   if (!stencil) return fail(LOPE_ERR_INVALID, "NULL stencil");

@@ -3,10 +3,27 @@
 // for sm_103a), bounded waits, and the local functions themselves.
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// Run-time compilation (NVRTC): the fixed-width integer types and the opaque
+// 128-byte tensor-map type the kernels take by value, declared as the CUDA
+// headers declare them.
+typedef signed char int8_t;
+typedef short int16_t;
+typedef int int32_t;
+typedef long int64_t;
+typedef unsigned char uint8_t;
+typedef unsigned short uint16_t;
+typedef unsigned int uint32_t;
+typedef unsigned long uint64_t;
+typedef unsigned long uintptr_t;
+typedef struct alignas(64) CUtensorMap_st { unsigned long long opaque[16]; } CUtensorMap;
+#include <cuda_bf16.h>
+#else
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 #include "lope_internal.h"
 
@@ -95,6 +112,18 @@ __device__ __forceinline__ F2 mul(F2 a, F2 b) {
 __device__ __forceinline__ F2 fma_(F2 a, F2 b, F2 c) {
   F2 d;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return d;
+}
+
+// Operators on packed pairs, for local functions written with + - * (user
+// source compiled at run time); they are the explicitly rounded operations
+// above.  Negation flips the sign bits (exact).
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return add(a, b); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return sub(a, b); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return mul(a, b); }
+__device__ __forceinline__ F2 operator-(F2 a) {
+  F2 d;
+  asm("xor.b64 %0, %1, 0x8000000080000000;" : "=l"(d.v) : "l"(a.v));
   return d;
 }
 

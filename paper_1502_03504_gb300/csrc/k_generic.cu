@@ -23,10 +23,15 @@ bool trap2d_supported(const StepArgs& a) {
 bool direct_supported(const StepArgs& a) { return a.ksteps == 1; }
 
 cudaError_t launch_trap2d(const StepArgs& a) {
+  if (a.s.kind == kUser) return jit_launch(a, kPathTrap);
   if (a.s.stages >= 2) return launch_generic_rk(a, true, nullptr);
   return dispatch_generic<false>(a, true, nullptr);
 }
 cudaError_t launch_direct(const StepArgs& a, int* blocks) {
+  if (a.s.kind == kUser) {
+    if (blocks) *blocks = direct_grid(a.g);
+    return jit_launch(a, kPathDirect);
+  }
   if (a.stage >= 2) return launch_generic_rk(a, false, blocks);
   return dispatch_generic<false>(a, false, blocks);
 }

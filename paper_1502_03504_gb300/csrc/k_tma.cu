@@ -70,6 +70,7 @@ bool tma_supported(const StepArgs& a) {
   const StencilDesc& s = a.s;
   if (a.ksteps != 1 || s.radius < 1 || s.radius > 2) return false;
   if ((s.kind == kSwe || s.kind == kSweFlux) && g.ndim != 2) return false;
+  if (s.kind == kUser && (a.adjoint || !jit_tma_ok(static_cast<const JitProgram*>(s.jit)))) return false;
   if (!s.star && (g.ndim != 2 || a.adjoint)) return false;  // box stencils: 2D tiles only
   const int esz = g.dtype == kF64 ? 8 : g.dtype == kF32 ? 4 : 2;
   const int cw = 16 / esz;
@@ -90,6 +91,7 @@ bool tma_supported(const StepArgs& a) {
 }
 
 cudaError_t launch_tma(const StepArgs& a, int* blocks) {
+  if (a.s.kind == kUser) return jit_launch(a, kPathTma);
   switch (a.g.dtype) {
     case kF32: return dispatch_t<float>(a, blocks);
     case kF64: return dispatch_t<double>(a, blocks);

@@ -58,6 +58,7 @@ template <class T> cudaError_t dispatch_t(const StepArgs& a) {
 }  // namespace
 
 cudaError_t launch_tma_stage(const StepArgs& a) {
+  if (a.s.kind == kUser) return jit_launch(a, kPathTma);
   switch (a.g.dtype) {
     case kF32: return dispatch_t<float>(a);
     case kF64: return dispatch_t<double>(a);

@@ -1,16 +1,23 @@
 // Internal types shared by the host planner (api.cu) and the kernel files.
+// The part outside the host-only sections also compiles under NVRTC, for
+// run-time compiled local functions (jit.cu).
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "lope.h"
+#endif
 
 namespace lope {
 
 // Stencil kinds (builtin names of lope_stencil_create_builtin).
-enum : int { kLinear = 0, kJacobi5 = 1, kDiff7 = 2, kStar9r2 = 3, kSwe = 4, kSweFlux = 5 };
+enum : int { kLinear = 0, kJacobi5 = 1, kDiff7 = 2, kStar9r2 = 3, kSwe = 4, kSweFlux = 5, kUser = 6 };
+constexpr int kUserParams = 8;  // parameters P[0..7] of a user-written local function
 enum : int { kF64 = 0, kF32 = 1, kBF16 = 2 };
 enum : int { kPeriodic = 0, kDirichlet = 1 };
 enum : int { kPathAuto = 0, kPathTma = 1, kPathTrap = 2, kPathDirect = 3 };
@@ -44,25 +51,8 @@ struct StencilDesc {
   double prm[4];       // c | dt, g, H | dt, g, f, H
   double box[125];     // (2r+1)^ndim weight table, slowest offset first
   double star_w[3][2 * kMaxRadius + 1];  // per axis (0 = x, 1 = y, 2 = z), centre in [0][r]
-};
-
-// One launch: `ksteps` sweeps from in to out.
-struct StepArgs {
-  Geom g;
-  StencilDesc s;
-  const void* in[kMaxFields];
-  void* out[kMaxFields];
-  int ksteps;
-  int tile_x, tile_y;
-  bool adjoint;          // run the transposed stencil (lambda halo: Dirichlet -> 0)
-  const void* ut;        // adjoint: state u_t read at the local element
-  const void* base[kMaxFields];  // RK stage >= 2: state at the start of the step
-  double rk_a, rk_b;     // RK stage >= 2: out = rk_a * base + rk_b * E(in)
-  int stage;             // RK: 0/1 plain sweep of E; >= 2 combining stage (TMA/direct)
-  double* partials;      // adjoint: per-block FP64 partial sums (accumulated)
-  int partial_count;     // adjoint: number of partial slots available
-  int* err;              // device error flag
-  cudaStream_t stream;
+  int user_nf;         // kUser: number of fields
+  void* jit;           // kUser: the run-time compiled program (host object, jit.cu)
 };
 
 // Coefficients (a, b) of stage s (1-based, s >= 2) of the strong-stability-
@@ -84,6 +74,26 @@ __host__ __device__ inline void rk_coeffs(int stages, int s, double* a, double* 
   }
 }
 
+#ifndef __CUDACC_RTC__
+// One launch: `ksteps` sweeps from in to out.
+struct StepArgs {
+  Geom g;
+  StencilDesc s;
+  const void* in[kMaxFields];
+  void* out[kMaxFields];
+  int ksteps;
+  int tile_x, tile_y;
+  bool adjoint;          // run the transposed stencil (lambda halo: Dirichlet -> 0)
+  const void* ut;        // adjoint: state u_t read at the local element
+  const void* base[kMaxFields];  // RK stage >= 2: state at the start of the step
+  double rk_a, rk_b;     // RK stage >= 2: out = rk_a * base + rk_b * E(in)
+  int stage;             // RK: 0/1 plain sweep of E; >= 2 combining stage (TMA/direct)
+  double* partials;      // adjoint: per-block FP64 partial sums (accumulated)
+  int partial_count;     // adjoint: number of partial slots available
+  int* err;              // device error flag
+  cudaStream_t stream;
+};
+
 // Launchers (each returns the number of blocks it used through *blocks when
 // non-NULL, so that the adjoint can size its partial-sum buffer).
 cudaError_t launch_tma(const StepArgs& a, int* blocks);
@@ -92,6 +102,18 @@ bool tma_supported(const StepArgs& a);
 cudaError_t launch_trap2d(const StepArgs& a);
 bool trap2d_supported(const StepArgs& a);
 cudaError_t launch_direct(const StepArgs& a, int* blocks);
+// Run-time compiled local functions (jit.cu).
+struct JitProgram;
+lope_status jit_create(const char* body, int ndim, int radius, int nf, bool star,
+                       const double* prm, int nprm, JitProgram** out);
+void jit_destroy(JitProgram* jp);
+lope_status jit_compile(JitProgram* jp, int dtype, std::string* err);
+bool jit_tma_ok(const JitProgram* jp);
+// Launch one sweep / stage of a kUser stencil on path kPathTma, kPathTrap or
+// kPathDirect (a.stage >= 2: combining Runge-Kutta stage; a.s.stages >= 2 on
+// the trapezoid: fused steps).
+cudaError_t jit_launch(const StepArgs& a, int path);
+
 // Multi-stage forms on the generic kernels (k_generic_rk.cu): fused trapezoid
 // steps (trap) or a combining stage on the direct kernel.
 cudaError_t launch_generic_rk(const StepArgs& a, bool trap, int* blocks);
@@ -138,7 +160,11 @@ size_t trap_smem_bytes(int dtype, int nf, int tile_x, int tile_y, int halo, int 
 
 void count_launches(int64_t n);
 
+#endif  // __CUDACC_RTC__
+
 }  // namespace lope
 
+#ifndef __CUDACC_RTC__
 // Record the last-error message of the calling thread (defined in api.cu).
 lope_status lope_fail_external(lope_status st, const char* msg);
+#endif

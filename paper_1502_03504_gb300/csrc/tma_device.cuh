@@ -1,0 +1,890 @@
+// TMA-staged stencil kernels (device templates).  Included by tma_kernels.cuh
+// (the host-side runner) and, as embedded source, by run-time compiled local
+// functions (jit.cu); it compiles under nvcc and NVRTC alike.
+//
+// The paper's multi-level halo exchange (Sec. 3.2 HALO_TRANSFER; Sec. 3.3 on
+// halo elements being several memory hops away) becomes, on one GB300, the
+// HBM -> shared memory -> register hierarchy:
+//   * a producer warp stages halo-padded tiles into a ring of shared-memory
+//     stages with cp.async.bulk.tensor (TMA), one mbarrier per stage;
+//   * ghost cells are produced by the copy itself: out-of-range boxes are
+//     zero-filled by the TMA unit (Dirichlet 0) and periodic halos are fetched
+//     from wrapped coordinates (BC=CYCLIC, Sec. 3.2);
+//   * consumer threads run the local function, one thread per output column,
+//     RY rows each; in 3D each thread marches along z keeping the 2R+1 centre
+//     values of its column in a register queue.
+//
+// Shared-memory stage layout for one field (TX x TY tile, radius R):
+//   main  (TY + 2R) rows x TX     rows y0-R .. y0+TY+R-1 (low halo, body, high halo)
+//   left  TY rows x CW            columns x0-CW .. x0-1     (CW = 16 bytes of elements)
+//   right TY rows x CW            columns x0+nvx .. x0+nvx+CW-1
+// Star stencils never read corners, so the slots only span the body rows.
+// When the high halo of a ragged or periodic tile does not follow the body in
+// memory, it is fetched separately into the rows after TY; the accessor maps
+// row >= nvy there.
+//
+// Box stencils (corner taps, 2D only) take no slots: the wide box already
+// holds the corners of interior tiles, and on tiles whose halo wraps the
+// consumer warps rewrite the halo ring of the box from the wrapped global
+// coordinates before reading it (fill_ring_warp).
+#pragma once
+
+#include "device_common.cuh"
+
+namespace lope {
+
+namespace {
+
+// Tile shape per storage type, rank and field count: TX columns (TX times the
+// element size is a multiple of 128 bytes), TY rows, RY rows per consumer
+// thread (TX * TY / RY consumer threads plus one producer warp), S stages.
+template <class T> struct TmaTx { static constexpr int TX = 64; };
+template <> struct TmaTx<double> { static constexpr int TX = 32; };
+
+template <class T, int RANK, int NF, bool PAIR> struct TmaCfg {
+  static constexpr int TX = TmaTx<T>::TX;
+  static constexpr int TY = (RANK == 2 && NF == 1) ? 64 : 32;
+  static constexpr int RY = PAIR ? ((RANK == 2 && NF == 1) ? 8 : 4) : (RANK == 2 ? 16 : 8);
+  static constexpr int S = RANK == 3 ? 8 : 3;
+};
+
+template <int NF> struct TmaMaps {
+  CUtensorMap wide[NF];  // box {W, TY+2R}: tile, CW halo columns each side, R halo rows each side
+  CUtensorMap rows[NF];  // box {W, R}: R consecutive halo rows
+  CUtensorMap cols[NF];  // box {CW, TY}: one 16-byte column block of the body rows
+};
+
+template <class Op, class T> struct TmaParams {
+  Op op;
+  const T* in[kMaxFields];  // the staged fields (read directly only by fill_ring_warp)
+  T* out[kMaxFields];
+  int nx, ny, nz;
+  int per_x, per_y, per_z;
+  int tiles_x, tiles_y;
+  int zchunk;     // 3D: output planes per unit
+  int nunits;     // number of work units
+  double* partials;
+  int* err;
+};
+
+// Stage layout (per field, every region 128-byte aligned, as TMA requires):
+//   wide   (TY+2R) x W box, W = TX + 2 CW, loaded at (x0-CW, y0-R): the tile,
+//          CW halo columns on each side and R halo rows above and below.
+//          Out-of-range cells arrive as zeros (the Dirichlet-0 halo).
+//   colL, colR   TY x CW slots: wrapped halo columns (periodic x edge tiles)
+//   rowLo, rowHi R x W slots: wrapped halo rows (periodic y edge tiles)
+// Consumers read every tap at a compile-time offset from the local element in
+// the wide box.  Where the periodic halo wraps (BC=CYCLIC of Sec. 3.2), the
+// wrapped halo rows feed the column registers from the row slots, and the
+// warps that read the wrapped halo columns first copy them from the column
+// slots into the box.  Star stencils never read the corner cells.
+template <class T, int TX, int TY, int R, int NF> struct Layout {
+  static constexpr int CW = 16 / int(sizeof(T));
+  static constexpr int W = TX + 2 * CW;
+  static constexpr uint32_t WIDE_B = (TY + 2 * R) * W * sizeof(T);
+  static constexpr uint32_t COL_B = TY * CW * sizeof(T);
+  static constexpr uint32_t ROW_B = R * W * sizeof(T);
+  static constexpr uint32_t A(uint32_t b) { return (b + 127) / 128 * 128; }
+  static constexpr uint32_t OFF_COLL = A(WIDE_B);
+  static constexpr uint32_t OFF_COLR = OFF_COLL + A(COL_B);
+  static constexpr uint32_t OFF_ROWLO = OFF_COLR + A(COL_B);
+  static constexpr uint32_t OFF_ROWHI = OFF_ROWLO + A(ROW_B);
+  static constexpr uint32_t FIELD_B = OFF_ROWHI + A(ROW_B);
+  static constexpr uint32_t STAGE_B = NF * FIELD_B;
+};
+
+// Which halos of a tile wrap (periodic axes only).
+struct TileInfo {
+  int x0, y0, nvx, nvy;
+  bool xl, xr;  // left / right halo columns wrap
+  bool yl, yh;  // low / high halo rows wrap
+};
+
+template <class T, int TX, int TY, int R>
+__device__ __forceinline__ TileInfo classify(int x0, int y0, int nx, int ny, int per_x, int per_y) {
+  TileInfo t;
+  t.x0 = x0;
+  t.y0 = y0;
+  t.nvx = min(TX, nx - x0);
+  t.nvy = min(TY, ny - y0);
+  t.xl = per_x && x0 == 0;
+  t.xr = per_x && x0 + t.nvx == nx;
+  t.yl = per_y && y0 < R;
+  t.yh = per_y && y0 + t.nvy + R > ny;
+  return t;
+}
+
+// Local-function accessor: x taps are shared loads at compile-time offsets
+// from b[f] (the local element in the wide box); y taps and the centre come
+// from the thread's column registers col[f][R + dy]; z taps (3D) from the
+// register queue q[f][R + dz].
+template <class T, int TX, int TY, int R, int NF, int NQ, int NC>
+struct StageAcc {
+  using C = C_t<T>;
+  const T* b[NF];
+  const C (*col)[NC];  // col[f] + r, so col[f][R + dy] is row r + dy
+  int r;
+  int64_t g;
+  const C (*q)[NQ];
+  __device__ __forceinline__ C operator()(int f, int dx, int dy, int dz) const {
+    if (dz != 0) return q[f][R + dz];
+    if (dx != 0) return to_c(b[f][dy * Layout<T, TX, TY, R, NF>::W + dx]);  // dy != 0: box corner
+    return col[f][r + R + dy];
+  }
+  __device__ __forceinline__ int64_t gidx() const { return g; }
+};
+
+// Periodic x edge: copy the wrapped halo columns that this warp's own lanes
+// will read (rows cy0 .. cy0+RY-1) from the column slots into the wide box.
+// Left-halo readers (cx < R) and right-halo readers (nvx-R <= cx < nvx) each
+// sit in a single warp, so a warp-level barrier is enough; the proxy fence
+// orders these shared-memory writes before the stage's next TMA refill.
+template <class T, int TX, int TY, int R, int NF, int RY>
+__device__ __forceinline__ void fix_x_warp(unsigned char* st, const TileInfo& t, int cx, int cy0) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const int lane = threadIdx.x % 32, cxw = cx - lane;  // first column of this warp
+  const bool left = t.xl && cxw == 0;
+  const bool right = t.xr && cxw <= t.nvx - 1 && t.nvx - 1 < cxw + 32;
+  if (!left && !right) return;
+  if (lane < R * RY) {
+    const int d = lane / RY, r = lane % RY;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T* w = reinterpret_cast<T*>(st + f * L::FIELD_B);
+      const T* sl = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_COLL);
+      const T* sr = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_COLR);
+      if (left) w[(R + cy0 + r) * L::W + L::CW - 1 - d] = sl[(cy0 + r) * L::CW + L::CW - 1 - d];
+      if (right) w[(R + cy0 + r) * L::W + L::CW + t.nvx + d] = sr[(cy0 + r) * L::CW + d];
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+}
+
+// Value for the column registers: tile row tr (which may lie in the halo) of
+// column cx, taken from the wide box or, where the periodic halo wraps, from
+// the wrapped row slots.
+template <class T, int TX, int TY, int R, int NF>
+__device__ __forceinline__ C_t<T> column_value(const unsigned char* st, int f, const TileInfo& t,
+                                               int tr, int cx, int ny, bool yw) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const unsigned char* fb = st + f * L::FIELD_B;
+  if (yw) {
+    if (t.yl && tr < 0)  // the low slot holds rows ny-R .. ny-1; y0 = 0 here
+      return to_c(reinterpret_cast<const T*>(fb + L::OFF_ROWLO)[(tr + R) * L::W + L::CW + cx]);
+    const int gy = t.y0 + tr;
+    // The high slot holds rows 0 .. R-1.  Rows further out are read only for
+    // rows below the grid edge, whose results are discarded: clamp in range.
+    if (t.yh && gy >= ny)
+      return to_c(reinterpret_cast<const T*>(fb + L::OFF_ROWHI)[min(gy - ny, R - 1) * L::W + L::CW + cx]);
+  }
+  return to_c(reinterpret_cast<const T*>(fb)[(R + tr) * L::W + L::CW + cx]);
+}
+
+template <int RANK>
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* m, int x, int y, int z,
+                                         uint64_t* bar) {
+  if (RANK == 2) tma_load_2d(dst, m, x, y, bar);
+  else tma_load_3d(dst, m, x, y, z, bar);
+}
+
+// Issue the copies of one tile/plane of every field into stage `st`.  BOX:
+// the wide box alone (box stencils patch wrapped halos themselves).
+template <class T, int TX, int TY, int R, int NF, int RANK, bool BOX = false>
+__device__ __forceinline__ void issue_plane(const TmaMaps<NF>& maps, unsigned char* st,
+                                            uint64_t* bar, const TileInfo& t, int z, int nx,
+                                            int ny) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const uint32_t per_field =
+      BOX ? L::WIDE_B
+          : L::WIDE_B + (uint32_t(t.xl) + uint32_t(t.xr)) * L::COL_B +
+                (uint32_t(t.yl) + uint32_t(t.yh)) * L::ROW_B;
+  mbar_arrive_expect_tx(bar, NF * per_field);
+  const int xw = t.x0 - L::CW;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    unsigned char* w = st + f * L::FIELD_B;
+    tma_load<RANK>(w, &maps.wide[f], xw, t.y0 - R, z, bar);
+    if (BOX) continue;
+    if (t.xl) tma_load<RANK>(w + L::OFF_COLL, &maps.cols[f], nx - L::CW, t.y0, z, bar);
+    if (t.xr) tma_load<RANK>(w + L::OFF_COLR, &maps.cols[f], 0, t.y0, z, bar);
+    if (t.yl) tma_load<RANK>(w + L::OFF_ROWLO, &maps.rows[f], xw, ny - R, z, bar);
+    if (t.yh) tma_load<RANK>(w + L::OFF_ROWHI, &maps.rows[f], xw, 0, z, bar);
+  }
+}
+
+__device__ __forceinline__ unsigned char* align128(unsigned char* p) {
+  return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 127) &
+                                          ~uintptr_t(127));
+}
+
+// Sum an FP64 value over the consumer threads (named barrier 1) and add it to
+// this block's partial slot.  Fixed order: deterministic.
+template <int NCONS>
+__device__ __forceinline__ void block_accumulate(double v, double* partials, double* scratch) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) scratch[warp] = v;
+  asm volatile("bar.sync 1, %0;" ::"r"(NCONS) : "memory");
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NCONS / 32; ++w) s += scratch[w];
+    partials[blockIdx.x] += s;
+  }
+}
+
+// RY outputs of one column of a staged tile/plane.  col[f][i] holds the
+// column's values for tile rows cy0 - R + i, i in [0, RY + 2R).
+template <class Op, class T, int TX, int TY, int RY, int NQ, int NC>
+__device__ __forceinline__ void column_rows(const Op& op, const unsigned char* st, T* const* out,
+                                            int64_t zoff, int nx, const TileInfo& t, int cx,
+                                            int cy0, const C_t<T> (*col)[NC],
+                                            const C_t<T> (*q)[Op::NF][NQ], double& red) {
+  using C = C_t<T>;
+  constexpr int R = Op::R, NF = Op::NF;
+  using L = Layout<T, TX, TY, R, NF>;
+  const bool xvalid = cx < t.nvx;
+  const int64_t base = zoff + int64_t(t.y0 + cy0) * nx + t.x0 + cx;
+  const int64_t gclamp = zoff + int64_t(t.y0) * nx + t.x0;  // a valid element for clamped reads
+  C rsum = C(0);  // adjoint terms of this column, summed in compute precision
+#pragma unroll
+  for (int r = 0; r < RY; ++r) {
+    const bool valid = xvalid && cy0 + r < t.nvy;
+    StageAcc<T, TX, TY, R, NF, NQ, NC> acc;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      acc.b[f] = reinterpret_cast<const T*>(st + f * L::FIELD_B) + (R + cy0 + r) * L::W + L::CW + cx;
+    acc.col = col;
+    acc.r = r;
+    acc.g = valid ? base + int64_t(r) * nx : gclamp;
+    acc.q = q ? q[r] : nullptr;
+    C o[NF];
+    C r1 = C(0);
+    op(acc, o, r1);
+    if (valid) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) out[f][base + int64_t(r) * nx] = from_c<T>(o[f]);
+      rsum = add(rsum, r1);
+    }
+  }
+  if (Op::REDUCES) red += double(rsum);
+}
+
+// The R column values above (lo) and below (hi) a thread's strip of RY rows.
+// `simple` (decided once per tile): the tile is not ragged in y and its high
+// halo, if it wraps, wraps whole; then only row group 0 reads the low row slot
+// and only the last row group the high one, a warp-uniform choice.  Other
+// wrapped tiles take column_value for each row.
+template <class T, int TX, int TY, int R, int NF, int RY, bool YW>
+__device__ __forceinline__ void edge_rows(const unsigned char* st, int f, const TileInfo& t, int cx,
+                                          int cy0, int ny, bool simple, C_t<T>* lo, C_t<T>* hi) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const unsigned char* fb = st + f * L::FIELD_B;
+  const T* box = reinterpret_cast<const T*>(fb);
+  if (!YW) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      lo[k] = to_c(box[(cy0 + k) * L::W + L::CW + cx]);
+      hi[k] = to_c(box[(cy0 + R + RY + k) * L::W + L::CW + cx]);
+    }
+  } else if (simple) {
+    const T* lsrc = (t.yl && cy0 == 0) ? reinterpret_cast<const T*>(fb + L::OFF_ROWLO)
+                                       : box + cy0 * L::W;
+    const T* hsrc = (t.yh && cy0 + RY == TY) ? reinterpret_cast<const T*>(fb + L::OFF_ROWHI)
+                                             : box + (cy0 + R + RY) * L::W;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      lo[k] = to_c(lsrc[k * L::W + L::CW + cx]);
+      hi[k] = to_c(hsrc[k * L::W + L::CW + cx]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      lo[k] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 - R + k, cx, ny, true);
+      hi[k] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 + RY + k, cx, ny, true);
+    }
+  }
+}
+
+template <int TY>
+__device__ __forceinline__ bool simple_y(const TileInfo& t, int ny) {
+  return t.nvy == TY && (!t.yh || t.y0 + TY == ny);
+}
+
+// One staged 2D tile: wrapped x halo patched by the warps that read it,
+// column registers (wrapped halo rows from the row slots when YW), then rows.
+template <bool YW, bool SIMPLE, bool WRAP, class Op, class T, int TX, int TY, int RY>
+__device__ __forceinline__ void tile2d(const Op& op, unsigned char* st, T* const* out, int nx,
+                                       int ny, const TileInfo& t, int cx, int cy0, double& red) {
+  using C = C_t<T>;
+  constexpr int R = Op::R, NF = Op::NF, NC = RY + 2 * R;
+  using L = Layout<T, TX, TY, R, NF>;
+  if (WRAP && (t.xl || t.xr)) fix_x_warp<T, TX, TY, R, NF, RY>(st, t, cx, cy0);
+  constexpr bool simple = !YW || SIMPLE;
+  C col[NF][NC];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    edge_rows<T, TX, TY, R, NF, RY, YW>(st, f, t, cx, cy0, ny, simple, &col[f][0], &col[f][R + RY]);
+    const T* box = reinterpret_cast<const T*>(st + f * L::FIELD_B);
+    if (simple) {
+#pragma unroll
+      for (int r = 0; r < RY; ++r) col[f][R + r] = to_c(box[(R + cy0 + r) * L::W + L::CW + cx]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < RY; ++r)
+        col[f][R + r] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 + r, cx, ny, true);
+    }
+  }
+  column_rows<Op, T, TX, TY, RY, 1, NC>(op, st, out, 0, nx, t, cx, cy0, col, nullptr, red);
+}
+
+// ------------------------------------------------------------------ column pairs
+// Paired consumers (FP32/BF16 storage): each thread computes two adjacent
+// columns cx2, cx2+1 with the packed f32x2 instructions.  Pair loads and
+// stores are 8 bytes (FP32) or 4 bytes (BF16) and aligned, since cx2, CW and
+// the box width are even.  x taps of radius <= 2 come from the aligned pairs
+// left (cx2-2, cx2-1) and right (cx2+2, cx2+3) of the centre pair.
+__device__ __forceinline__ F2 ld_pair(const float* p) {
+  F2 r;
+  r.v = *reinterpret_cast<const uint64_t*>(p);
+  return r;
+}
+__device__ __forceinline__ F2 ld_pair(const __nv_bfloat16* p) {
+  const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  return F2::make(f.x, f.y);
+}
+__device__ __forceinline__ void st_pair(float* p, F2 v) { *reinterpret_cast<uint64_t*>(p) = v.v; }
+__device__ __forceinline__ void st_pair(__nv_bfloat16* p, F2 v) {
+  __nv_bfloat162 b;
+  b.x = __float2bfloat16_rn(v.lo());
+  b.y = __float2bfloat16_rn(v.hi());
+  *reinterpret_cast<__nv_bfloat162*>(p) = b;
+}
+
+template <class T, int TX, int TY, int R, int NF, int NC>
+struct PairAcc {
+  static_assert(R <= 2, "paired taps reach two columns");
+  const T* b[NF];      // centre pair of this row in the wide box
+  const F2 (*col)[NC];
+  int r;
+  int64_t g;
+  __device__ __forceinline__ F2 operator()(int f, int dx, int dy, int) const {
+    if (dx == 0) return col[f][r + R + dy];
+    const T* rb = b[f] + dy * Layout<T, TX, TY, R, NF>::W;  // row r + dy (corner taps of box stencils)
+    if (dx == -2) return ld_pair(rb - 2);
+    if (dx == 2) return ld_pair(rb + 2);
+    const F2 c = col[f][r + R + dy];
+    if (dx == -1) return F2::make(ld_pair(rb - 2).hi(), c.lo());
+    return F2::make(c.hi(), ld_pair(rb + 2).lo());
+  }
+  __device__ __forceinline__ int64_t gidx() const { return g; }
+};
+
+// 3D variant: z taps come from the register queue of packed pairs.
+template <class T, int TX, int TY, int R, int NF, int NC, int NQ>
+struct PairAcc3 {
+  const T* b[NF];
+  const F2 (*col)[NC];
+  int r;
+  int64_t g;
+  const F2 (*q)[NQ];
+  __device__ __forceinline__ F2 operator()(int f, int dx, int dy, int dz) const {
+    if (dz != 0) return q[f][R + dz];
+    if (dx == 0) return col[f][r + R + dy];
+    if (dx == -2) return ld_pair(b[f] - 2);
+    if (dx == 2) return ld_pair(b[f] + 2);
+    const F2 c = col[f][r + R];
+    if (dx == -1) return F2::make(ld_pair(b[f] - 2).hi(), c.lo());
+    return F2::make(c.hi(), ld_pair(b[f] + 2).lo());
+  }
+  __device__ __forceinline__ int64_t gidx() const { return g; }
+};
+
+// Pair value of tile row tr for the column registers: from the wide box or,
+// where the periodic y halo wraps, from the row slots (as column_value).
+template <class T, int TX, int TY, int R, int NF>
+__device__ __forceinline__ F2 column_pair(const unsigned char* st, int f, const TileInfo& t, int tr,
+                                          int cx2, int ny) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const unsigned char* fb = st + f * L::FIELD_B;
+  if (t.yl && tr < 0)
+    return ld_pair(reinterpret_cast<const T*>(fb + L::OFF_ROWLO) + (tr + R) * L::W + L::CW + cx2);
+  const int gy = t.y0 + tr;
+  if (t.yh && gy >= ny)
+    return ld_pair(reinterpret_cast<const T*>(fb + L::OFF_ROWHI) + min(gy - ny, R - 1) * L::W +
+                   L::CW + cx2);
+  return ld_pair(reinterpret_cast<const T*>(fb) + (R + tr) * L::W + L::CW + cx2);
+}
+
+// Copy the wrapped halo columns of rows cy0 .. cy0+RY-1 from the column slots
+// into the wide box (as fix_x_warp); `left`/`right` say which sides this warp
+// reads.
+template <class T, int TX, int TY, int R, int NF, int RY>
+__device__ __forceinline__ void fix_x_rows(unsigned char* st, const TileInfo& t, int cy0, bool left,
+                                           bool right) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const int lane = threadIdx.x % 32;
+  if (lane < R * RY) {
+    const int d = lane / RY, r = lane % RY;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T* w = reinterpret_cast<T*>(st + f * L::FIELD_B);
+      const T* sl = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_COLL);
+      const T* sr = reinterpret_cast<const T*>(st + f * L::FIELD_B + L::OFF_COLR);
+      if (left) w[(R + cy0 + r) * L::W + L::CW - 1 - d] = sl[(cy0 + r) * L::CW + L::CW - 1 - d];
+      if (right) w[(R + cy0 + r) * L::W + L::CW + t.nvx + d] = sr[(cy0 + r) * L::CW + d];
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+}
+
+// One staged 2D tile on paired consumers: a warp covers a whole row group of
+// TX = 64 columns, so it owns both wrapped halo column blocks of its rows.
+// YW: the tile's periodic y halo wraps; all such tiles take the general
+// column_pair path (2D edge tiles are a few percent of the tiles).
+template <bool YW, bool WRAP, class Op, class T, int TX, int TY, int RY>
+__device__ __forceinline__ void tile2d_pair(const Op& op, unsigned char* st, T* const* out, int nx,
+                                            int ny, const TileInfo& t, int cx2, int cy0) {
+  constexpr int R = Op::R, NF = Op::NF, NC = RY + 2 * R;
+  using L = Layout<T, TX, TY, R, NF>;
+  static_assert(TX == 64, "a warp of pairs spans the tile");
+  if (WRAP && (t.xl || t.xr)) fix_x_rows<T, TX, TY, R, NF, RY>(st, t, cy0, t.xl, t.xr);
+  F2 col[NF][NC];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const T* box = reinterpret_cast<const T*>(st + f * L::FIELD_B);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      if (YW) col[f][k] = column_pair<T, TX, TY, R, NF>(st, f, t, cy0 - R + k, cx2, ny);
+      else col[f][k] = ld_pair(box + (cy0 + k) * L::W + L::CW + cx2);
+    }
+  }
+  const bool xvalid = cx2 < t.nvx;  // nvx is even: a pair is all valid or all invalid
+  const int64_t base = int64_t(t.y0 + cy0) * nx + t.x0 + cx2;
+  const int64_t gclamp = int64_t(t.y0) * nx + t.x0;  // a valid pair for clamped reads
+#pragma unroll
+  for (int r = 0; r < RY; ++r) {
+    PairAcc<T, TX, TY, R, NF, NC> acc;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      acc.b[f] = reinterpret_cast<const T*>(st + f * L::FIELD_B) + (R + cy0 + r) * L::W + L::CW + cx2;
+    acc.col = col;
+    acc.r = r;
+    acc.g = (xvalid && cy0 + r < t.nvy) ? base + int64_t(r) * nx : gclamp;
+    F2 o[NF];
+    F2 unused(0.f);
+    op(acc, o, unused);
+    if (xvalid && cy0 + r < t.nvy) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) st_pair(out[f] + base + int64_t(r) * nx, o[f]);
+    }
+  }
+}
+
+// Box stencils on a tile whose halo wraps: each consumer warp (which spans
+// the whole tile width, RY rows from cy0) rewrites the halo-ring cells of the
+// wide box that its own rows read -- tile rows cy0-R .. min(cy0+RY, nvy)+R-1,
+// columns -R .. nvx+R-1, outside the tile's valid cells -- from the wrapped
+// global coordinates, or 0 where a Dirichlet side is crossed (the TMA zero
+// fill already holds that value).  Adjacent warps may write the same cell
+// with the same value.  The proxy fence orders these shared-memory writes
+// before the stage's next TMA refill; no block-wide barrier is needed.
+template <class T, int TX, int TY, int R, int NF, int RY>
+__device__ __forceinline__ void fill_ring_warp(unsigned char* st, const TileInfo& t,
+                                               const T* const* in, int nx, int ny, int per_x,
+                                               int per_y, int cy0) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const int lane = threadIdx.x % 32;
+  if (cy0 < t.nvy) {
+    const int r0 = cy0 - R, r1 = min(cy0 + RY, t.nvy) + R;  // rows [r0, r1)
+    const int wr = t.nvx + 2 * R;
+    for (int c = lane; c < (r1 - r0) * wr; c += 32) {
+      const int tr = r0 + c / wr, tc = c % wr - R;
+      if (tr >= 0 && tr < t.nvy && tc >= 0 && tc < t.nvx) continue;  // valid cell: from TMA
+      int gy = t.y0 + tr, gx = t.x0 + tc;
+      bool zero = false;
+      if (gy < 0 || gy >= ny) {
+        if (per_y) gy = wrap(gy, ny);
+        else zero = true;
+      }
+      if (gx < 0 || gx >= nx) {
+        if (per_x) gx = wrap(gx, nx);
+        else zero = true;
+      }
+      const int64_t gi = int64_t(gy) * nx + gx;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        T* box = reinterpret_cast<T*>(st + f * L::FIELD_B);
+        box[(R + tr) * L::W + L::CW + tc] = zero ? from_c<T>(C_t<T>(0)) : in[f][gi];
+      }
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------ 2D tiles
+template <class Op, class T, int TX, int TY, int RY, int S, bool WRAP, bool PAIR>
+__global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32)
+    tma2d_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
+  constexpr int R = Op::R, NF = Op::NF;
+  using L = Layout<T, TX, TY, R, NF>;
+  constexpr int NCONS = (PAIR ? TX / 2 : TX) * (TY / RY);
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = align128(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * L::STAGE_B);
+  uint64_t* empty = full + S;
+  __shared__ volatile int abort_flag;
+  __shared__ double red_scratch[NCONS / 32];
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCONS / 32);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (tid >= NCONS) {  // producer warp
+    if (tid == NCONS) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) tma_prefetch_desc(&maps.wide[f]);
+      int i = 0;
+      for (int u = blockIdx.x; u < p.nunits; u += gridDim.x, ++i) {
+        const int s = i % S;
+        const uint32_t ph = (i / S) & 1;
+        if (i >= S && !mbar_wait_bounded(&empty[s], ph ^ 1, p.err)) {
+          abort_flag = 1;
+          break;
+        }
+        if (abort_flag) break;
+        const TileInfo t = classify<T, TX, TY, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx,
+                                              p.ny, WRAP && p.per_x, WRAP && p.per_y);
+        issue_plane<T, TX, TY, R, NF, 2, !Op::STAR>(maps, smem + s * L::STAGE_B, &full[s], t, 0,
+                                                    p.nx, p.ny);
+      }
+      if (abort_flag) {  // let copies already issued land before the block exits
+        for (int k = max(0, i - S); k < i; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
+      }
+    }
+    return;
+  }
+
+  constexpr int CPR = PAIR ? TX / 2 : TX;  // consumer threads per row group
+  const int cx = (tid % CPR) * (PAIR ? 2 : 1), cy0 = (tid / CPR) * RY, lane = tid % 32;
+  double red = 0.0;
+  int i = 0;
+  for (int u = blockIdx.x; u < p.nunits; u += gridDim.x, ++i) {
+    const int s = i % S;
+    if (!mbar_wait_bounded(&full[s], (i / S) & 1, p.err) || abort_flag) {
+      abort_flag = 1;
+      break;
+    }
+    const TileInfo t = classify<T, TX, TY, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx,
+                                              p.ny, WRAP && p.per_x, WRAP && p.per_y);
+    unsigned char* st = smem + s * L::STAGE_B;
+    if constexpr (!Op::STAR) {
+      // Box stencil: complete the halo ring of wrapped tiles in the box, then
+      // every tap (corners included) reads the box.
+      static_assert(CPR == 32, "a warp spans the tile width");
+      if (WRAP && (t.xl || t.xr || t.yl || t.yh))
+        fill_ring_warp<T, TX, TY, R, NF, RY>(st, t, p.in, p.nx, p.ny, p.per_x, p.per_y, cy0);
+      if constexpr (PAIR)
+        tile2d_pair<false, false, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0);
+      else
+        tile2d<false, true, false, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
+    } else if constexpr (PAIR) {
+      // 2D edge tiles are a few percent of the tiles: one general instance for
+      // all of them keeps the persistent loop's code small.
+      if (!WRAP || !(t.yl || t.yh))
+        tile2d_pair<false, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0);
+      else
+        tile2d_pair<true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0);
+    } else {
+      if (!WRAP || !(t.yl || t.yh))
+        tile2d<false, true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
+      else
+        tile2d<true, false, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  if (Op::REDUCES) block_accumulate<NCONS>(red, p.partials, red_scratch);
+}
+
+// ------------------------------------------------------------------ 3D z-march
+// Consumer side of the z-march for one tile.  YW: the tile's periodic y halo
+// wraps, so those rows come from the row slots.  XF: x-edge tiles patch their
+// wrapped halo columns per warp.
+template <bool YW, bool XF, bool SIMPLE, class Op, class T, int TX, int TY, int RY, int S>
+__device__ __forceinline__ void march3d(const TmaParams<Op, T>& p, unsigned char* smem,
+                                        uint64_t* full, uint64_t* empty, volatile int* abort_flag,
+                                        const TileInfo& t, int z0, int z1, int np, double& red) {
+  using C = C_t<T>;
+  constexpr int R = Op::R, NF = Op::NF, NQ = 2 * R + 1, NC = RY + 2 * R;
+  using L = Layout<T, TX, TY, R, NF>;
+  const int tid = threadIdx.x;
+  const int cx = tid % TX, cy0 = (tid / TX) * RY, lane = tid % 32;
+  const int64_t plane = int64_t(p.nx) * p.ny;
+  constexpr bool simple = !YW || SIMPLE;  // strip rows never wrap
+  C q[RY][NF][NQ];
+  bool ok = true;
+
+  auto release = [&](int j) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[j % S]);
+  };
+  // Wait for staged plane j and push its centre values onto each queue.
+  auto shift_in = [&](int j) -> bool {
+    const int s = j % S;
+    if (!mbar_wait_bounded(&full[s], (j / S) & 1, p.err) || *abort_flag) {
+      *abort_flag = 1;
+      return false;
+    }
+    unsigned char* st = smem + s * L::STAGE_B;
+    if (XF) fix_x_warp<T, TX, TY, R, NF, RY>(st, t, cx, cy0);
+#pragma unroll
+    for (int r = 0; r < RY; ++r)
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int k = 0; k < NQ - 1; ++k) q[r][f][k] = q[r][f][k + 1];
+    if (simple) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T* box = reinterpret_cast<const T*>(st + f * L::FIELD_B);
+#pragma unroll
+        for (int r = 0; r < RY; ++r) q[r][f][NQ - 1] = to_c(box[(R + cy0 + r) * L::W + L::CW + cx]);
+      }
+    } else {  // ragged periodic tile: strip rows past the grid edge wrap
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+          q[r][f][NQ - 1] = column_value<T, TX, TY, R, NF>(st, f, t, cy0 + r, cx, p.ny, true);
+    }
+    return true;
+  };
+
+  for (int j = 0; j < 2 * R && ok; ++j) {
+    ok = shift_in(j);
+    if (ok && (j < R || j >= np - R)) release(j);  // outside [z0, z1): centres only
+  }
+  for (int m = 0; ok && m < z1 - z0; ++m) {
+    const int jn = m + 2 * R;
+    ok = shift_in(jn);
+    if (!ok) break;
+    const int jc = m + R;  // plane of the outputs
+    const unsigned char* st = smem + (jc % S) * L::STAGE_B;
+    // column registers of the output plane: strip rows from the queue, the
+    // R rows on either side from the stage
+    C col[NF][NC];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      edge_rows<T, TX, TY, R, NF, RY, YW>(st, f, t, cx, cy0, p.ny, simple, &col[f][0],
+                                          &col[f][R + RY]);
+#pragma unroll
+      for (int r = 0; r < RY; ++r) col[f][R + r] = q[r][f][R];
+    }
+    column_rows<Op, T, TX, TY, RY, NQ, NC>(p.op, st, p.out, int64_t(z0 + m) * plane, p.nx, t, cx,
+                                           cy0, col, q, red);
+    release(jc);
+    if (jn >= np - R) release(jn);  // above z1-1: centres only
+  }
+}
+
+// Paired consumer side of the z-march (FP32/BF16 storage): each thread owns
+// two adjacent columns and RY rows; the z queue and the column registers
+// hold packed pairs.  A warp spans the tile width (TX = 64), so it patches
+// both wrapped halo column blocks of its own rows.
+template <bool YW, bool XF, bool SIMPLE, class Op, class T, int TX, int TY, int RY, int S>
+__device__ __forceinline__ void march3d_pair(const TmaParams<Op, T>& p, unsigned char* smem,
+                                             uint64_t* full, uint64_t* empty,
+                                             volatile int* abort_flag, const TileInfo& t, int z0,
+                                             int z1, int np) {
+  constexpr int R = Op::R, NF = Op::NF, NQ = 2 * R + 1, NC = RY + 2 * R;
+  using L = Layout<T, TX, TY, R, NF>;
+  static_assert(TX == 64, "a warp of pairs spans the tile");
+  const int tid = threadIdx.x;
+  const int cx2 = (tid % 32) * 2, cy0 = (tid / 32) * RY, lane = tid % 32;
+  const int64_t plane = int64_t(p.nx) * p.ny;
+  constexpr bool simple = !YW || SIMPLE;  // strip rows never wrap
+  F2 q[RY][NF][NQ];
+  bool ok = true;
+
+  auto release = [&](int j) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[j % S]);
+  };
+  auto shift_in = [&](int j) -> bool {
+    const int s = j % S;
+    if (!mbar_wait_bounded(&full[s], (j / S) & 1, p.err) || *abort_flag) {
+      *abort_flag = 1;
+      return false;
+    }
+    unsigned char* st = smem + s * L::STAGE_B;
+    if (XF) fix_x_rows<T, TX, TY, R, NF, RY>(st, t, cy0, t.xl, t.xr);
+#pragma unroll
+    for (int r = 0; r < RY; ++r)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+#pragma unroll
+        for (int k = 0; k < NQ - 1; ++k) q[r][f][k] = q[r][f][k + 1];
+        if (simple)
+          q[r][f][NQ - 1] = ld_pair(reinterpret_cast<const T*>(st + f * L::FIELD_B) +
+                                    (R + cy0 + r) * L::W + L::CW + cx2);
+        else
+          q[r][f][NQ - 1] = column_pair<T, TX, TY, R, NF>(st, f, t, cy0 + r, cx2, p.ny);
+      }
+    return true;
+  };
+
+  for (int j = 0; j < 2 * R && ok; ++j) {
+    ok = shift_in(j);
+    if (ok && (j < R || j >= np - R)) release(j);  // outside [z0, z1): centres only
+  }
+  const bool xvalid = cx2 < t.nvx;
+  for (int m = 0; ok && m < z1 - z0; ++m) {
+    const int jn = m + 2 * R;
+    ok = shift_in(jn);
+    if (!ok) break;
+    const int jc = m + R;  // plane of the outputs
+    const unsigned char* st = smem + (jc % S) * L::STAGE_B;
+    F2 col[NF][NC];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const T* box = reinterpret_cast<const T*>(st + f * L::FIELD_B);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        if (YW) {
+          col[f][k] = column_pair<T, TX, TY, R, NF>(st, f, t, cy0 - R + k, cx2, p.ny);
+          col[f][R + RY + k] = column_pair<T, TX, TY, R, NF>(st, f, t, cy0 + RY + k, cx2, p.ny);
+        } else {
+          col[f][k] = ld_pair(box + (cy0 + k) * L::W + L::CW + cx2);
+          col[f][R + RY + k] = ld_pair(box + (cy0 + R + RY + k) * L::W + L::CW + cx2);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RY; ++r) col[f][R + r] = q[r][f][R];
+    }
+    const int64_t base = int64_t(z0 + m) * plane + int64_t(t.y0 + cy0) * p.nx + t.x0 + cx2;
+    const int64_t gclamp = int64_t(z0 + m) * plane + int64_t(t.y0) * p.nx + t.x0;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      PairAcc3<T, TX, TY, R, NF, NC, NQ> acc;
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        acc.b[f] = reinterpret_cast<const T*>(st + f * L::FIELD_B) + (R + cy0 + r) * L::W + L::CW + cx2;
+      acc.col = col;
+      acc.r = r;
+      acc.g = (xvalid && cy0 + r < t.nvy) ? base + int64_t(r) * p.nx : gclamp;
+      acc.q = q[r];
+      F2 o[NF];
+      F2 unused(0.f);
+      p.op(acc, o, unused);
+      if (xvalid && cy0 + r < t.nvy) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) st_pair(p.out[f] + base + int64_t(r) * p.nx, o[f]);
+      }
+    }
+    release(jc);
+    if (jn >= np - R) release(jn);  // above z1-1: centres only
+  }
+}
+
+// WRAP: compile the periodic-halo handling (x or y axis periodic).  Grids
+// without a periodic x/y axis use the instance without it, whose consumer
+// code fits the register budget of two blocks per SM.
+template <class Op, class T, int TX, int TY, int RY, int S, bool WRAP, bool PAIR>
+__global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32, 2)
+    tma3d_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
+  constexpr int R = Op::R, NF = Op::NF;
+  using L = Layout<T, TX, TY, R, NF>;
+  constexpr int NCONS = (PAIR ? TX / 2 : TX) * (TY / RY);
+  static_assert(S >= R + 2, "ring too short for the z window");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = align128(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * L::STAGE_B);
+  uint64_t* empty = full + S;
+  __shared__ volatile int abort_flag;
+  __shared__ double red_scratch[NCONS / 32];
+
+  const int tid = threadIdx.x;
+  const int ntiles = p.tiles_x * p.tiles_y;
+  const int tile = blockIdx.x % ntiles, zc = blockIdx.x / ntiles;
+  const TileInfo t = classify<T, TX, TY, R>((tile % p.tiles_x) * TX, (tile / p.tiles_x) * TY, p.nx,
+                                            p.ny, WRAP && p.per_x, WRAP && p.per_y);
+  const int z0 = zc * p.zchunk, z1 = min(p.nz, z0 + p.zchunk);
+  const int np = (z1 - z0) + 2 * R;  // planes staged by this block
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCONS / 32);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (z0 >= z1) return;
+
+  if (tid >= NCONS) {  // producer warp
+    if (tid == NCONS) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) tma_prefetch_desc(&maps.wide[f]);
+      int j = 0;
+      for (; j < np; ++j) {
+        const int s = j % S;
+        const uint32_t ph = (j / S) & 1;
+        if (j >= S && !mbar_wait_bounded(&empty[s], ph ^ 1, p.err)) {
+          abort_flag = 1;
+          break;
+        }
+        if (abort_flag) break;
+        int z = z0 - R + j;
+        if (p.per_z) z = wrap(z, p.nz);
+        issue_plane<T, TX, TY, R, NF, 3>(maps, smem + s * L::STAGE_B, &full[s], t, z, p.nx, p.ny);
+      }
+      if (abort_flag) {  // let copies already issued land before the block exits
+        for (int k = max(0, j - S); k < j; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
+      }
+    }
+    return;
+  }
+
+  double red = 0.0;
+#define LOPE_MARCH(YW, XF, SIMPLE)                                                               \
+  do {                                                                                           \
+    if constexpr (PAIR)                                                                          \
+      march3d_pair<YW, XF, SIMPLE, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t,   \
+                                                         z0, z1, np);                            \
+    else                                                                                         \
+      march3d<YW, XF, SIMPLE, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0,    \
+                                                    z1, np, red);                                \
+  } while (0)
+  if constexpr (WRAP) {
+    const bool yw = t.yl || t.yh, xf = t.xl || t.xr;
+    const bool simple = simple_y<TY>(t, p.ny);
+    if (!yw) {
+      if (xf) LOPE_MARCH(false, true, true);
+      else LOPE_MARCH(false, false, true);
+    } else if (simple) {
+      if (xf) LOPE_MARCH(true, true, true);
+      else LOPE_MARCH(true, false, true);
+    } else {
+      if (xf) LOPE_MARCH(true, true, false);
+      else LOPE_MARCH(true, false, false);
+    }
+  } else {
+    LOPE_MARCH(false, false, true);
+  }
+#undef LOPE_MARCH
+  if (Op::REDUCES) block_accumulate<NCONS>(red, p.partials, red_scratch);
+}
+
+}  // namespace
+}  // namespace lope

@@ -1,0 +1,163 @@
+"""GPU parity of user-written local functions compiled at run time (NVRTC).
+
+Bodies that spell the builtins with the same operations must give bitwise the
+builtins' results on every kernel path (TMA tiles / z-march, trapezoid, direct,
+and the Runge-Kutta forms): the same kernel templates run the same arithmetic.
+A function with no builtin counterpart (Gray-Scott, two coupled nonlinear
+fields) is compared with the oracle, which compiles the same text for the host
+in FP64 (FP64: normwise 1e-12; FP32: the bound of gpu_helpers), and across
+paths bitwise.
+"""
+import numpy as np
+import pytest
+import torch
+
+import lope_inputs as LI
+from gpu_helpers import bound_f32, normwise, to_device, to_host
+from user_bodies import DIFF7, GRAY_SCOTT, GRAY_SCOTT_PRM, JACOBI5, SWE_FLUX
+
+pytestmark = pytest.mark.gpu
+
+TMA, TRAP, DIRECT = 1, 2, 3
+FLUX = [0.02, 1.0, 0.5, 1.0]
+
+
+def _launch(L, path, tx=0, ty=0, k=0, graph=-1):
+    return L.Launch(path, tx, ty, k, graph)
+
+
+def _grid(L, shape, dtype, halo, bc, bval=None, nf=1):
+    g = L.Grid(shape, dtype, halo=halo, nfields=nf)
+    g.set_boundaries(bc, bval)
+    return g
+
+
+def _run(L, g, st, fields, nsteps, launch=None):
+    out = L.apply(g, st, fields, nsteps=nsteps, launch=launch)
+    torch.cuda.synchronize()
+    L.sync_status()
+    return out if isinstance(out, list) else [out]
+
+
+def _gs_fields(seed, shape):
+    u = 1.0 - 0.3 * LI.uniform_field(seed, shape)
+    v = 0.25 * LI.uniform_field(seed, shape, offset=int(np.prod(shape)))
+    return [u, v]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f64"])
+@pytest.mark.parametrize("bc", [[0, 0], [1, 0]])
+def test_user_jacobi5_bitwise_equals_builtin(lope, dtype, bc):
+    shape, T = (83, 264), 7
+    u0 = to_device(LI.uniform_field(1200, shape), dtype)[0]
+    g = _grid(lope, shape, dtype, 1, bc)
+    user = lope.Stencil.source(JACOBI5, ndim=2, radius=1, params=[0.2])
+    builtin = lope.Stencil.builtin("jacobi5", 0.2)
+    for launch in (_launch(lope, TMA), _launch(lope, TRAP, 64, 32, 1), _launch(lope, TRAP, 32, 8, 3),
+                   _launch(lope, DIRECT), _launch(lope, TMA, graph=1), None):
+        a = _run(lope, g, user, u0, T, launch)[0]
+        b = _run(lope, g, builtin, u0, T, launch)[0]
+        assert torch.equal(a, b), launch
+    for scheme in ("rk2", "rk3"):
+        user.set_scheme(scheme)
+        builtin.set_scheme(scheme)
+        for launch in (_launch(lope, TMA), _launch(lope, TRAP, 64, 16, 1), _launch(lope, DIRECT)):
+            a = _run(lope, g, user, u0, 3, launch)[0]
+            b = _run(lope, g, builtin, u0, 3, launch)[0]
+            assert torch.equal(a, b), (scheme, launch)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_user_diff7_bitwise_equals_builtin(lope, dtype):
+    shape, T = (37, 50, 72), 6
+    u0 = to_device(LI.uniform_field(1201, shape), dtype)[0]
+    g = _grid(lope, shape, dtype, 1, [1, 0, 1])
+    user = lope.Stencil.source(DIFF7, ndim=3, radius=1, params=[0.1])
+    builtin = lope.Stencil.builtin("diff7", 0.1)
+    for launch in (_launch(lope, TMA), _launch(lope, DIRECT)):
+        assert torch.equal(_run(lope, g, user, u0, T, launch)[0],
+                           _run(lope, g, builtin, u0, T, launch)[0]), launch
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f64"])
+def test_user_swe_flux_bitwise_equals_builtin(lope, dtype):
+    shape, T = (83, 264), 5
+    h, u, v = LI.swe_fields(1202, shape)
+    dev = [to_device(x, dtype)[0] for x in (h - 1.0, u, v)]
+    g = _grid(lope, shape, dtype, 1, [0, 0], nf=3)
+    user = lope.Stencil.source(SWE_FLUX, ndim=2, radius=1, nfields=3, params=FLUX, box=True)
+    builtin = lope.Stencil.builtin("swe_flux", *FLUX)
+    for launch in (_launch(lope, TMA), _launch(lope, TRAP, 64, 32, 1), _launch(lope, DIRECT)):
+        a = _run(lope, g, user, dev, T, launch)
+        b = _run(lope, g, builtin, dev, T, launch)
+        for k in range(3):
+            assert torch.equal(a[k], b[k]), (launch, k)
+
+
+@pytest.mark.parametrize("scheme", ["euler", "rk3"])
+@pytest.mark.parametrize("bc,bval", [([0, 0], None), ([1, 1], [(1.0, 1.0), (0.0, 0.0)])])
+def test_gray_scott_fp64_vs_oracle_every_path(lope, orc, scheme, bc, bval):
+    shape, T = (70, 136), 12
+    fl = _gs_fields(1203, shape)
+    dev, stored = zip(*(to_device(f, "f64") for f in fl))
+    g = _grid(lope, shape, "f64", 1, bc, bval, nf=2)
+    st = lope.Stencil.source(GRAY_SCOTT, ndim=2, radius=1, nfields=2, params=GRAY_SCOTT_PRM)
+    st.set_scheme(scheme)
+    want = orc.apply_source(list(stored), GRAY_SCOTT, GRAY_SCOTT_PRM, T, bc=bc, bval=bval,
+                            scheme=scheme)
+    paths = [None, _launch(lope, TRAP, 64, 16, 1), _launch(lope, DIRECT)]
+    if bval is None:
+        paths.append(_launch(lope, TMA))
+    for launch in paths:
+        outs = _run(lope, g, st, list(dev), T, launch)
+        for k in range(2):
+            assert normwise(to_host(outs[k]), want[k]) <= 1e-12, (launch, k)
+
+
+def test_gray_scott_f32_bound_and_paths_bitwise(lope, orc):
+    shape, T = (100, 200), 20
+    fl = _gs_fields(1204, shape)
+    dev, stored = zip(*(to_device(f, "f32") for f in fl))
+    g = _grid(lope, shape, "f32", 1, [0, 0], nf=2)
+    st = lope.Stencil.source(GRAY_SCOTT, ndim=2, radius=1, nfields=2, params=GRAY_SCOTT_PRM)
+    want = orc.apply_source(list(stored), GRAY_SCOTT, GRAY_SCOTT_PRM, T)
+    # one step's Jacobian, infinity norm, for 0 <= u, v <= 1: diffusion part
+    # |1 - 4 D dt| + 4 D dt = 1 and reaction derivatives bounded by dt (F + 3)
+    G = 1 + GRAY_SCOTT_PRM[0] * (GRAY_SCOTT_PRM[3] + GRAY_SCOTT_PRM[4] + 3)
+    ref = _run(lope, g, st, list(dev), T, _launch(lope, TMA))
+    for k in range(2):
+        assert np.max(np.abs(to_host(ref[k]) - want[k])) <= bound_f32(T, 1.0, 12, G), k
+    for launch in (_launch(lope, TRAP, 64, 32, 2), _launch(lope, DIRECT)):
+        outs = _run(lope, g, st, list(dev), T, launch)
+        for k in range(2):
+            assert torch.equal(outs[k], ref[k]), (launch, k)
+
+
+def test_source_error_surfaces_at_launch(lope):
+    g = _grid(lope, (32, 32), "f32", 1, [0, 0])
+    st = lope.Stencil.source("out[0] = U(0, 0, 0) * no_such_thing;", params=[1.0])
+    u0 = torch.zeros(32, 32, device="cuda")
+    with pytest.raises(lope.LopeError, match="no_such_thing"):
+        lope.apply(g, st, u0, nsteps=1)
+
+
+def test_full_size_gray_scott_2048_sampled(lope, orc):
+    """Gray-Scott at 2048^2 x 2 fields, FP32, periodic, 100 steps on the TMA
+    tiles: sampled points against the oracle on their domain of dependence.
+    Stated bound 1e-4 (100 steps of about 12 roundings of 2^-24 on values
+    <= 1, with the per-step growth G of the test above bounded by 1.1)."""
+    from gpu_helpers import sub_box
+
+    shape, T = (2048, 2048), 100
+    fl = _gs_fields(1205, shape)
+    dev, stored = zip(*(to_device(f, "f32") for f in fl))
+    g = _grid(lope, shape, "f32", 1, [0, 0], nf=2)
+    st = lope.Stencil.source(GRAY_SCOTT, ndim=2, radius=1, nfields=2, params=GRAY_SCOTT_PRM)
+    outs = _run(lope, g, st, list(dev), T)
+    for p in [(0, 0), (2047, 2047), (1024, 5), (3, 1500)]:
+        idx, pos = sub_box(shape, p, T + 1, [True, True])
+        sub = [s[np.ix_(*idx)] for s in stored]
+        want = orc.apply_source(sub, GRAY_SCOTT, GRAY_SCOTT_PRM, T, bc=[1, 1],
+                                bval=[(1.0, 1.0), (0.0, 0.0)], nthreads=orc.max_threads())
+        for k in range(2):
+            assert abs(float(outs[k][p].item()) - want[k][pos]) <= 1e-4, (p, k)

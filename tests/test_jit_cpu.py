@@ -1,0 +1,62 @@
+"""Local functions written as source, compiled at run time (no GPU needed).
+
+lope_stencil_create_source wraps the body in a functor with the builtins'
+interface and NVRTC compiles it into the library's kernel templates (TMA
+tiles / z-march, trapezoid tiles, direct kernel and their Runge-Kutta stage
+forms) for sm_103a.  Compilation needs no device, so these tests run on the
+CPU: they check that every kernel instance compiles for every storage type and
+that a body with an error reports the compiler's message.
+"""
+import pytest
+
+JACOBI5 = """
+const C u = U(0, 0, 0);
+out[0] = fma_(P[0], fma_(C(-4), u, add(add(U(0, -1, 0), U(0, 1, 0)),
+                                        add(U(0, 0, -1), U(0, 0, 1)))), u);
+"""
+
+DIFF7 = """
+const C u = U(0, 0, 0, 0);
+const C nb = add(add(add(U(0, -1, 0, 0), U(0, 1, 0, 0)), add(U(0, 0, -1, 0), U(0, 0, 1, 0))),
+                 add(U(0, 0, 0, -1), U(0, 0, 0, 1)));
+out[0] = fma_(P[0], fma_(C(-6), u, nb), u);
+"""
+
+BOX_TWO_FIELDS = """
+// a coupled pair with corner taps, written with operators
+out[0] = U(0, 0, 0) + P[0] * (U(1, 1, 1) - U(1, -1, -1));
+out[1] = U(1, 0, 0) - P[1] * (U(0, 1, -1) - U(0, -1, 1));
+"""
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "bf16"])
+def test_source_stencils_compile_for_every_storage_type(lope, dtype):
+    lope.Stencil.source(JACOBI5, ndim=2, radius=1, params=[0.2]).compile(dtype)
+    lope.Stencil.source(DIFF7, ndim=3, radius=1, params=[0.1]).compile(dtype)
+    lope.Stencil.source(BOX_TWO_FIELDS, ndim=2, radius=1, nfields=2, params=[0.1, 0.05],
+                        box=True).compile(dtype)
+
+
+def test_radius_two_and_three_fields_compile(lope):
+    body = """
+for (int f = 0; f < 3; ++f)
+  out[f] = fma_(P[f], sub(add(U(f, -2, 0), U(f, 0, 2)), add(U(f, 2, 0), U(f, 0, -2))), U(f, 0, 0));
+"""
+    lope.Stencil.source(body, ndim=2, radius=2, nfields=3, params=[0.1, 0.2, 0.3]).compile("f32")
+
+
+def test_compile_error_reports_the_compiler_log(lope):
+    st = lope.Stencil.source("out[0] = U(0, 0, 0) + undefined_name;", params=[1.0])
+    with pytest.raises(lope.LopeError, match="undefined_name"):
+        st.compile("f32")
+
+
+def test_bad_arguments_are_rejected(lope):
+    with pytest.raises(lope.LopeError, match="radius"):
+        lope.Stencil.source(JACOBI5, ndim=2, radius=3)
+    with pytest.raises(lope.LopeError, match="nfields"):
+        lope.Stencil.source(JACOBI5, ndim=2, radius=1, nfields=4)
+    with pytest.raises(lope.LopeError, match="8 parameters"):
+        lope.Stencil.source(JACOBI5, params=[0.0] * 9)
+    with pytest.raises(lope.LopeError, match="non-finite"):
+        lope.Stencil.source(JACOBI5, params=[float("nan")])
