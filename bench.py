@@ -191,7 +191,8 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-KERNEL_SOURCES = ("k_tma.cu", "tma_kernels.cuh", "device_common.cuh", "lope_internal.h")
+KERNEL_SOURCES = ("k_tma.cu", "tma_kernels.cuh", "tma_device.cuh", "device_common.cuh",
+                  "lope_internal.h")
 
 
 def kernel_source_hash():
