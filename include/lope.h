@@ -167,6 +167,20 @@ lope_status lope_work_states(const lope_stencil* stencil, int* states);
 lope_status lope_apply(const lope_grid* grid, const lope_stencil* stencil, const void* const* in,
                        void* const* out, void* const* work, int64_t nsteps, void* cuda_stream);
 
+/* The end-to-end form of lope_apply for a state held in host memory: copies
+ * host_in[nfields] to the device buffers dev_in, runs lope_apply(dev_in ->
+ * dev_out, dev_work as the work buffers), and copies dev_out back to
+ * host_out[nfields], all in order on the stream (asynchronous).  dev_in is
+ * overwritten with the input; the other conventions are lope_apply's.  Host
+ * buffers should be page-locked (cudaHostAlloc / pinned) for asynchronous,
+ * full-bandwidth copies; pageable host memory works but the copies then
+ * synchronise.  Several calls on different streams with their own device
+ * buffers overlap one call's copies with another's sweeps. */
+lope_status lope_apply_host(const lope_grid* grid, const lope_stencil* stencil,
+                            const void* const* host_in, void* const* host_out,
+                            void* const* dev_in, void* const* dev_out, void* const* dev_work,
+                            int64_t nsteps, void* cuda_stream);
+
 /* Launch choices, for tests and tuning.  Zero fields mean "planner decides".
  *   path:    0 auto, 1 TMA tiles (2D tiles, any stencil / 3D z-march, star
  *            stencils; 16-byte row pitch), 2 shared-memory trapezoid tiles with temporal blocking

@@ -21,6 +21,7 @@ from ._lib import (  # noqa: F401
     Stencil,
     apply,
     apply_batch,
+    apply_host,
     adjoint,
     autotune,
     batch_workspace_size,
@@ -38,6 +39,7 @@ from ._lib import (  # noqa: F401
 from ._lib import (  # noqa: F401  (C ABI names)
     lope_adjoint,
     lope_apply,
+    lope_apply_host,
     lope_apply_batch,
     lope_apply_with,
     lope_autotune,

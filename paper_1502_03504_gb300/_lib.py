@@ -67,6 +67,7 @@ _SIGS = {
     "lope_work_states": (_INT, [_P, ctypes.POINTER(_INT)]),
     "lope_apply": (_INT, [_P, _P, _PP, _PP, _PP, _I64, _P]),
     "lope_apply_with": (_INT, [_P, _P, _PP, _PP, _PP, _I64, ctypes.POINTER(Launch), _P]),
+    "lope_apply_host": (_INT, [_P, _P, _PP, _PP, _PP, _PP, _PP, _I64, _P]),
     "lope_autotune": (_INT, [_P, _P, _PP, _PP, _PP, _I64, ctypes.POINTER(Launch), _DP, _P]),
     "lope_batch_workspace_size": (_INT, [_INT, _PP, _P, ctypes.POINTER(Launch), ctypes.POINTER(_SZ)]),
     "lope_apply_batch": (_INT, [_INT, _PP, _P, _PP, _PP, _PP, _I64, ctypes.POINTER(Launch), _P, _SZ, _P]),
@@ -416,6 +417,24 @@ def apply(grid: Grid, stencil: Stencil, inputs, out=None, work=None, nsteps=1, l
                         [_dptr(t) for t in outs],
                         [_dptr(t) for t in works] if works is not None else None, nsteps, launch, s)
     return outs if isinstance(inputs, (list, tuple)) else outs[0]
+
+
+def lope_apply_host(grid, stencil, host_in, host_out, dev_in, dev_out, dev_work, nsteps, stream):
+    _check(load().lope_apply_host(grid, stencil, _ptrs(host_in), _ptrs(host_out), _ptrs(dev_in),
+                                  _ptrs(dev_out), _ptrs(dev_work) if dev_work is not None else None,
+                                  int(nsteps), stream))
+
+
+def apply_host(grid: Grid, stencil: Stencil, host_in, host_out, dev_in, dev_out, dev_work=None,
+               nsteps=1, stream=None):
+    """lope_apply_host on tensors: host_in/host_out are (pinned) CPU tensors,
+    dev_in/dev_out/dev_work device tensors (lists for multi-field grids)."""
+    hi, ho, di, do = (_as_list(x) for x in (host_in, host_out, dev_in, dev_out))
+    dw = _as_list(dev_work) if dev_work is not None else None
+    lope_apply_host(grid.handle, stencil.handle, [t.data_ptr() for t in hi],
+                    [t.data_ptr() for t in ho], [_dptr(t) for t in di], [_dptr(t) for t in do],
+                    [_dptr(t) for t in dw] if dw is not None else None, nsteps, _stream(stream))
+    return host_out
 
 
 def autotune(grid, stencil, inputs, out, work, nsteps, stream=None):

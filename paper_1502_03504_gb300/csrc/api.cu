@@ -797,6 +797,30 @@ lope_status lope_apply_with(const lope_grid* grid, const lope_stencil* stencil,
                     static_cast<cudaStream_t>(cuda_stream));
 }
 
+lope_status lope_apply_host(const lope_grid* grid, const lope_stencil* stencil,
+                            const void* const* host_in, void* const* host_out,
+                            void* const* dev_in, void* const* dev_out, void* const* dev_work,
+                            int64_t nsteps, void* cuda_stream) {
+  lope_status rs = check_pair(grid, stencil);
+  if (rs != LOPE_OK) return rs;
+  if (!host_in || !host_out || !dev_in) return fail(LOPE_ERR_INVALID, "NULL field array");
+  const Geom& g = grid->g;
+  const size_t bytes = size_t(npts(g)) * esize(g.dtype);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  for (int f = 0; f < g.nf; ++f) {
+    if (!host_in[f] || !host_out[f] || !dev_in[f]) return fail(LOPE_ERR_INVALID, "NULL field pointer");
+    cudaError_t e = cudaMemcpyAsync(dev_in[f], host_in[f], bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (host to device)");
+  }
+  if ((rs = apply_impl(grid, stencil, dev_in, dev_out, dev_work, nsteps, nullptr, st)) != LOPE_OK)
+    return rs;
+  for (int f = 0; f < g.nf; ++f) {
+    cudaError_t e = cudaMemcpyAsync(host_out[f], dev_out[f], bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (device to host)");
+  }
+  return LOPE_OK;
+}
+
 lope_status lope_autotune(const lope_grid* grid, const lope_stencil* stencil,
                           const void* const* in, void* const* out, void* const* work,
                           int64_t nsteps, lope_launch* best, double* best_ms, void* cuda_stream) {
