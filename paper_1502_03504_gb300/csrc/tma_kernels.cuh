@@ -70,11 +70,13 @@ constexpr int kMinChunk = 48;
 // paired consumers (FP32/BF16 without reductions, radius <= 2).
 template <class T, int RANK, int R, int NF, bool PAIR>
 struct TmaShape {
-  using Cfg = TmaCfg<T, RANK, NF, PAIR>;
+  using Cfg = TmaCfg<T, RANK, R, NF, PAIR>;
   static constexpr int TX = Cfg::TX, TY = Cfg::TY, RY = Cfg::RY, S = Cfg::S;
   using L = Layout<T, TX, TY, R, NF>;
   static constexpr int THREADS = (PAIR ? TX / 2 : TX) * (TY / RY) + 32;
   static constexpr size_t SMEM = size_t(S) * L::STAGE_B + 2 * S * sizeof(uint64_t) + 128;
+  static_assert(SMEM <= 227 * 1024, "stage ring exceeds the shared memory of a block");
+  static_assert(THREADS <= 1024 && TY + 2 * R <= 256, "block or TMA box too large");
 
   // Fill the geometry fields of the kernel parameters and the block count;
   // occ(wrap) gives the resident blocks per SM of the kernel instance.
