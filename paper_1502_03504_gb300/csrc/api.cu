@@ -180,6 +180,18 @@ Choice default_choice(const Geom& g, const StencilDesc& s, int* err) {
     a.tile_y = 16;
     if (trap2d_supported(a)) return {kPathTrap, 64, 16, 1};
   }
+  if (g.ndim == 2 && s.stages == 1 &&
+      size_t(npts(g)) * esize(g.dtype) * size_t(g.nf) <= (size_t(8) << 20)) {
+    // A state that stays in L2 makes each sweep a short, launch-bound kernel:
+    // fuse 4 sweeps per launch in trapezoid tiles (measured on GB300 for a
+    // 256^2 FP64 grid, 100 steps: 0.44 ms against 0.56 ms for one TMA sweep
+    // per launch).
+    a.tile_x = 64;
+    a.tile_y = 16;
+    a.ksteps = 4;
+    if (trap2d_supported(a)) return {kPathTrap, 64, 16, 4};
+    a.ksteps = 1;
+  }
   if (tma_supported(a)) return {kPathTma, 0, 0, 1};
   if (g.ndim == 2) return {kPathTrap, 64, 32, 1};
   return {kPathDirect, 0, 0, 1};

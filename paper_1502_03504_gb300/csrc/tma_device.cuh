@@ -47,13 +47,17 @@ template <> struct TmaTx<double> { static constexpr int TX = 32; };
 // ring of 17-warp blocks holds one block per SM) and 64 rows in 3D; measured
 // on GB300 against shorter tiles and other depths (2D 9-point 8192^2: 0.74 ->
 // 0.91 of the copy peak; 3D 7-point 512^3: 0.905 -> 0.926; radius-1 only in
-// 3D, where a radius-2 register queue of 8 rows would spill).  Three-field 3D
-// rings take 6 stages to stay within 227 KB of shared memory.
+// 3D, where a radius-2 register queue of 8 rows would spill).  FP32
+// multi-field 2D tiles are 64 rows with 4 rows per thread (17-warp blocks:
+// nonlinear shallow water 0.44 -> 0.53, Gray-Scott 0.75 -> 0.86; the linear
+// shallow water unchanged).  Three-field 3D rings take 6 stages to stay
+// within 227 KB of shared memory.
 template <class T, int RANK, int R, int NF, bool PAIR> struct TmaCfg {
   static constexpr int TX = TmaTx<T>::TX;
   static constexpr bool TALL2 = RANK == 2 && NF == 1 && PAIR;
   static constexpr bool TALL3 = RANK == 3 && NF == 1 && PAIR && R == 1;
-  static constexpr int TY = TALL2 ? 128 : (RANK == 2 && NF == 1) ? 64 : TALL3 ? 64 : 32;
+  static constexpr bool MULTI32 = RANK == 2 && NF > 1 && PAIR && sizeof(T) == 4;
+  static constexpr int TY = TALL2 ? 128 : (RANK == 2 && NF == 1) ? 64 : (TALL3 || MULTI32) ? 64 : 32;
   static constexpr int RY = PAIR ? ((TALL2 || TALL3) ? 8 : 4) : (RANK == 2 ? 16 : 8);
   static constexpr int S = RANK == 3 ? (NF == 3 ? 6 : 8) : 3;
 };

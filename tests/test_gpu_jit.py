@@ -161,3 +161,64 @@ def test_full_size_gray_scott_2048_sampled(lope, orc):
                                 bval=[(1.0, 1.0), (0.0, 0.0)], nthreads=orc.max_threads())
         for k in range(2):
             assert abs(float(outs[k][p].item()) - want[k][pos]) <= 1e-4, (p, k)
+
+
+GRAY_SCOTT_3D = """
+const C u = U(0, 0, 0, 0), v = U(1, 0, 0, 0);
+const C nu = add(add(add(U(0, -1, 0, 0), U(0, 1, 0, 0)), add(U(0, 0, -1, 0), U(0, 0, 1, 0))),
+                 add(U(0, 0, 0, -1), U(0, 0, 0, 1)));
+const C nv = add(add(add(U(1, -1, 0, 0), U(1, 1, 0, 0)), add(U(1, 0, -1, 0), U(1, 0, 1, 0))),
+                 add(U(1, 0, 0, -1), U(1, 0, 0, 1)));
+const C uvv = mul(u, mul(v, v));
+out[0] = fma_(P[0], fma_(P[1], fma_(C(-6), u, nu), fma_(P[3], sub(C(1), u), -uvv)), u);
+out[1] = fma_(P[0], fma_(P[2], fma_(C(-6), v, nv), fma_(-add(P[3], P[4]), v, uvv)), v);
+"""
+
+THREE_FIELD_3D = """
+// three coupled fields, radius 2 along z (a 3D ring with three fields per stage)
+for (int f = 0; f < 3; ++f) {
+  const int g = (f + 1) % 3;
+  out[f] = fma_(P[0], sub(add(U(g, 0, 0, -2), U(g, 0, 0, 2)), add(U(f, 1, 0, 0), U(f, 0, -1, 0))),
+                U(f, 0, 0, 0));
+}
+"""
+
+BOX_3D = """
+out[0] = fma_(P[0], sub(add(U(0, 1, 1, 1), U(0, -1, -1, -1)), mul(C(2), U(0, 0, 0, 0))), U(0, 0, 0, 0));
+"""
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "bf16"])
+def test_user_3d_two_and_three_fields_vs_oracle(lope, orc, dtype):
+    shape, T = (21, 37, 72), 6
+    for body, nf, prm, radius in ((GRAY_SCOTT_3D, 2, [0.5, 0.08, 0.04, 0.035, 0.065], 1),
+                                  (THREE_FIELD_3D, 3, [0.05], 2)):
+        fl = [LI.uniform_field(1400 + k, shape) for k in range(nf)]
+        dev, stored = zip(*(to_device(f, dtype) for f in fl))
+        g = _grid(lope, shape, dtype, radius, [0, 1, 0], nf=nf)
+        st = lope.Stencil.source(body, ndim=3, radius=radius, nfields=nf, params=prm)
+        want = orc.apply_source(list(stored), body, prm, T, bc=[0, 1, 0])
+        ref = _run(lope, g, st, list(dev), T, _launch(lope, TMA))
+        for launch in (_launch(lope, DIRECT), None):
+            outs = _run(lope, g, st, list(dev), T, launch)
+            for k in range(nf):
+                assert torch.equal(outs[k], ref[k]), (nf, launch, k)
+        for k in range(nf):
+            got = to_host(ref[k])
+            if dtype == "f64":
+                assert normwise(got, want[k]) <= 1e-12, (nf, k)
+            else:
+                tol = 0.05 if dtype == "bf16" else 2e-5
+                assert np.max(np.abs(got - want[k])) <= tol, (nf, k)
+
+
+def test_user_3d_box_takes_direct_path(lope, orc):
+    shape, T = (12, 20, 36), 4
+    u0, u0s = to_device(LI.uniform_field(1410, shape), "f64")
+    g = _grid(lope, shape, "f64", 1, [0, 0, 1])
+    st = lope.Stencil.source(BOX_3D, ndim=3, radius=1, params=[0.1], box=True)
+    with pytest.raises(lope.LopeError, match="does not support"):
+        lope.apply(g, st, u0, nsteps=1, launch=_launch(lope, TMA))
+    got = to_host(_run(lope, g, st, u0, T)[0])
+    want = orc.apply_source(u0s, BOX_3D, [0.1], T, bc=[0, 0, 1])
+    assert normwise(got, want) <= 1e-12

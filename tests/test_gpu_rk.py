@@ -174,3 +174,20 @@ def test_full_size_rk3_swe_flux_4096_sampled(lope, orc):
                          nthreads=orc.max_threads())
         for k in range(3):
             assert abs(float(outs[k][p].item()) - want[k][pos]) <= 1e-4, (p, k)
+
+
+@pytest.mark.parametrize("scheme", ["rk2", "rk3"])
+def test_rk_bf16_vs_oracle_and_single_step(lope, orc, scheme):
+    shape = (64, 200)
+    u0, u0s = to_device(LI.uniform_field(1106, shape), "bf16")
+    g = _grid(lope, shape, "bf16", 1, [1, 0])
+    st = lope.Stencil.builtin("jacobi5", 0.2).set_scheme(scheme)
+    for T in (1, 7):
+        want = orc.apply(u0s, "jacobi5", [0.2], T, bc=[1, 0], scheme=scheme)
+        stages = 2 if scheme == "rk2" else 3
+        # every stage rounds to BF16 (2^-9 relative), the step is non-expansive
+        bound = T * stages * (2.0 ** -9 + 11 * 2.0 ** -24) * 1.0001
+        for launch in (None, _launch(lope, TMA), _launch(lope, DIRECT)):
+            got = to_host(_run(lope, g, st, u0, T, launch))
+            assert got.shape == want.shape
+            assert np.max(np.abs(got - want)) <= bound, (T, launch)
