@@ -187,7 +187,8 @@ lope_status lope_apply_host(const lope_grid* grid, const lope_stencil* stencil,
  *            (2D, any stencil, any shape), 3 direct (any stencil, one thread per
  *            point).
  *   tile_x, tile_y: tile shape for path 2 (tile_x in {32,64,128}, tile_y in
- *            {8,16,32}).
+ *            {8,16,32}); for path 1, tile_y = 1 or 2 forces the short or the
+ *            tall tiles (0: tall from 2^22 points in 2D, 2^26 in 3D).
  *   tsteps:  temporal depth k (sweeps fused per launch; path 2 only, 1..8).
  *   graph:   0 auto, 1 capture the launch sequence in a CUDA graph, -1 never. */
 typedef struct {

@@ -255,6 +255,8 @@ cudaError_t issue_stages(const Geom& g, const StencilDesc& s, const Choice& c,
     }
     for (int stage = 1; stage <= S; ++stage) {
       StepArgs a = base_args(g, s, err, st);
+      a.tile_x = c.tile_x;
+      a.tile_y = c.tile_y;
       a.stage = stage;
       if (stage >= 2) rk_coeffs(S, stage, &a.rk_a, &a.rk_b);
       for (int f = 0; f < g.nf; ++f) {

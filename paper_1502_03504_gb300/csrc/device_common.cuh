@@ -127,6 +127,21 @@ __device__ __forceinline__ F2 operator-(F2 a) {
   return d;
 }
 
+// Load a stored value (or an aligned pair of adjacent values) of global memory
+// in compute precision.
+__device__ __forceinline__ float ldc(const float* p, float) { return __ldg(p); }
+__device__ __forceinline__ float ldc(const __nv_bfloat16* p, float) { return __bfloat162float(p[0]); }
+__device__ __forceinline__ double ldc(const double* p, double) { return __ldg(p); }
+__device__ __forceinline__ F2 ldc(const float* p, F2) {
+  F2 r;
+  r.v = __ldg(reinterpret_cast<const unsigned long long*>(p));
+  return r;
+}
+__device__ __forceinline__ F2 ldc(const __nv_bfloat16* p, F2) {
+  const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  return F2::make(f.x, f.y);
+}
+
 // ---------------------------------------------------------------- timers / waits
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
@@ -441,24 +456,9 @@ struct OpAdjDiffusion {
       lt = fma_(C(4.0 / 3.0), s1, fma_(C(-1.0 / 12.0), s2, mul(C(-5), l)));
     }
     o[0] = fma_(c.get(C()), lt, l);
-    red = fma_(lt, to_c(__ldg(ut + U.gidx())), red);
+    red = fma_(lt, ldc(ut + U.gidx(), C()), red);
   }
 };
-
-// Load a stored value (or an aligned pair of adjacent values) of global memory
-// in compute precision.
-__device__ __forceinline__ float ldc(const float* p, float) { return __ldg(p); }
-__device__ __forceinline__ float ldc(const __nv_bfloat16* p, float) { return __bfloat162float(p[0]); }
-__device__ __forceinline__ double ldc(const double* p, double) { return __ldg(p); }
-__device__ __forceinline__ F2 ldc(const float* p, F2) {
-  F2 r;
-  r.v = __ldg(reinterpret_cast<const unsigned long long*>(p));
-  return r;
-}
-__device__ __forceinline__ F2 ldc(const __nv_bfloat16* p, F2) {
-  const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
-  return F2::make(f.x, f.y);
-}
 
 // One later stage of a multi-stage (Runge-Kutta) step: out = a * base + b *
 // E(in), where E is the wrapped local function (one forward-Euler step), `in`

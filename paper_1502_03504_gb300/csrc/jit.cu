@@ -150,15 +150,14 @@ struct UserOpHost {
   Coef p[kUserParams];
 };
 
-enum : int { kTmaPlain = 0, kTmaStage = 1, kDirectPlain = 2, kDirectStage = 3, kTrapPlain = 4,
-             kTrapRk = 5, kNumKernels = 6 };
+enum : int { kDirectPlain = 0, kDirectStage = 1, kTrapPlain = 2, kTrapRk = 3, kNumKernels = 4 };
 
 // Name expression of kernel `which` for the compiled functor, with the tile
 // constants of the host-side shape (TmaShape) so that both sides agree.
-template <class T, int RANK, int R, int NF>
+template <class T, int RANK, int R, int NF, bool TALL>
 std::string tma_name(bool stage, bool wrap) {
   constexpr bool PAIR = tma_pair<T, R>(false);
-  using Sh = TmaShape<T, RANK, R, NF, PAIR>;
+  using Sh = TmaShape<T, RANK, R, NF, PAIR, TALL>;
   const std::string t = std::is_same<T, float>::value ? "float"
                         : std::is_same<T, double>::value ? "double" : "__nv_bfloat16";
   const std::string op = stage ? "lope::OpStage<lope::UserOp, " + t + ">" : "lope::UserOp";
@@ -229,10 +228,7 @@ void kernel_names(const JitProgram& jp, std::vector<std::string>* names) {
   names->assign(kNumKernels, std::string());
   const std::string t = type_name(std::is_same<T, float>::value ? kF32
                                   : std::is_same<T, double>::value ? kF64 : kBF16);
-  if (jp.tma_ok()) {
-    (*names)[kTmaPlain] = tma_name<T, RANK, R, NF>(false, false);
-    (*names)[kTmaStage] = tma_name<T, RANK, R, NF>(true, false);
-  }
+  (void)jp;  // the TMA instances are appended by all_names
   (*names)[kDirectPlain] = "&lope::direct_kernel<lope::UserOp, " + t + ">";
   (*names)[kDirectStage] = "&lope::direct_kernel<lope::OpStage<lope::UserOp, " + t + ">, " + t + ">";
   if (RANK == 2) {
@@ -241,21 +237,24 @@ void kernel_names(const JitProgram& jp, std::vector<std::string>* names) {
   }
 }
 
-// The TMA kernels come in two instances (halo wrap code or not); their names
-// differ only in the WRAP argument, so the "wrap" variants are appended after
-// the fixed list.
+// The TMA kernels come in eight instances: plain or combining stage, with or
+// without the halo-wrap code, tall or short tiles; they follow the fixed list
+// at kNumKernels + tma_index(stage, wrap, tall).
+constexpr int tma_index(bool stage, bool wrap, bool tall) {
+  return kNumKernels + (stage ? 4 : 0) + (wrap ? 2 : 0) + (tall ? 1 : 0);
+}
+
 template <class T, int RANK, int R, int NF>
 void all_names(const JitProgram& jp, std::vector<std::string>* names) {
   kernel_names<T, RANK, R, NF>(jp, names);
-  if (jp.tma_ok()) {
-    names->push_back(tma_name<T, RANK, R, NF>(false, true));
-    names->push_back(tma_name<T, RANK, R, NF>(true, true));
-  } else {
-    names->push_back(std::string());
-    names->push_back(std::string());
-  }
+  names->resize(kNumKernels + 8);
+  if (!jp.tma_ok()) return;
+  for (int stage = 0; stage < 2; ++stage)
+    for (int wrap = 0; wrap < 2; ++wrap) {
+      (*names)[tma_index(stage, wrap, true)] = tma_name<T, RANK, R, NF, true>(stage, wrap);
+      (*names)[tma_index(stage, wrap, false)] = tma_name<T, RANK, R, NF, false>(stage, wrap);
+    }
 }
-constexpr int kTmaPlainWrap = kNumKernels, kTmaStageWrap = kNumKernels + 1, kAllKernels = kNumKernels + 2;
 
 // Dispatch a functor template over the run-time shape (storage type, rank,
 // radius, fields) to the compile-time instance.
@@ -396,10 +395,10 @@ void fill_stage(OpStage<Op, T>& st, const StepArgs& a) {
   for (int f = 0; f < kMaxFields; ++f) st.base[f] = static_cast<const T*>(a.base[f]);
 }
 
-template <class T, int RANK, int R, int NF>
-cudaError_t run_tma(JitProgram& jp, const StepArgs& a, int dtype) {
+template <class T, int RANK, int R, int NF, bool TALL>
+cudaError_t run_tma_t(JitProgram& jp, const StepArgs& a, int dtype) {
   constexpr bool PAIR = tma_pair<T, R>(false);
-  using Sh = TmaShape<T, RANK, R, NF, PAIR>;
+  using Sh = TmaShape<T, RANK, R, NF, PAIR, TALL>;
   using Host = UserOpHost<RANK, R, NF, true>;
   const bool stage = a.stage >= 2;
   Host op;
@@ -407,8 +406,9 @@ cudaError_t run_tma(JitProgram& jp, const StepArgs& a, int dtype) {
   auto occ = [&](bool wrap) {
     CUfunction f = nullptr;
     int o = 1;
-    const int which = stage ? (wrap ? kTmaStageWrap : kTmaStage) : (wrap ? kTmaPlainWrap : kTmaPlain);
-    if (get_kernel(jp, dtype, which, Sh::SMEM, Sh::THREADS, &f, &o) != cudaSuccess) o = 1;
+    if (get_kernel(jp, dtype, tma_index(stage, wrap, TALL), Sh::SMEM, Sh::THREADS, &f, &o) !=
+        cudaSuccess)
+      o = 1;
     return o;
   };
   auto go = [&](auto& p) -> cudaError_t {
@@ -418,7 +418,7 @@ cudaError_t run_tma(JitProgram& jp, const StepArgs& a, int dtype) {
     cudaError_t e = Sh::prepare(a, p, maps);
     if (e != cudaSuccess) return e;
     const bool wrap = p.per_x || p.per_y;
-    const int which = stage ? (wrap ? kTmaStageWrap : kTmaStage) : (wrap ? kTmaPlainWrap : kTmaPlain);
+    const int which = tma_index(stage, wrap, TALL);
     CUfunction f = nullptr;
     if ((e = get_kernel(jp, dtype, which, Sh::SMEM, Sh::THREADS, &f, nullptr)) != cudaSuccess) return e;
     void* args[] = {&maps, &p};
@@ -433,6 +433,12 @@ cudaError_t run_tma(JitProgram& jp, const StepArgs& a, int dtype) {
   TmaParams<Host, T> p;
   p.op = op;
   return go(p);
+}
+
+template <class T, int RANK, int R, int NF>
+cudaError_t run_tma(JitProgram& jp, const StepArgs& a, int dtype) {
+  return tma_tall(a) ? run_tma_t<T, RANK, R, NF, true>(jp, a, dtype)
+                     : run_tma_t<T, RANK, R, NF, false>(jp, a, dtype);
 }
 
 template <class T, int RANK, int R, int NF>

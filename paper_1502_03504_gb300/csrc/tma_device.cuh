@@ -52,13 +52,15 @@ template <> struct TmaTx<double> { static constexpr int TX = 32; };
 // nonlinear shallow water 0.44 -> 0.53, Gray-Scott 0.75 -> 0.86; the linear
 // shallow water unchanged).  Three-field 3D rings take 6 stages to stay
 // within 227 KB of shared memory.
-template <class T, int RANK, int R, int NF, bool PAIR> struct TmaCfg {
+// TALL = false gives the shorter tiles (2D single-field 64 rows, others 32),
+// which keep more blocks in flight on small grids; the runner picks per grid.
+template <class T, int RANK, int R, int NF, bool PAIR, bool TALL = true> struct TmaCfg {
   static constexpr int TX = TmaTx<T>::TX;
-  static constexpr bool TALL2 = RANK == 2 && NF == 1 && PAIR;
-  static constexpr bool TALL3 = RANK == 3 && NF == 1 && PAIR && R == 1;
-  static constexpr bool MULTI32 = RANK == 2 && NF > 1 && PAIR && sizeof(T) == 4;
+  static constexpr bool TALL2 = TALL && RANK == 2 && NF == 1 && PAIR;
+  static constexpr bool TALL3 = TALL && RANK == 3 && NF == 1 && PAIR && R == 1;
+  static constexpr bool MULTI32 = TALL && RANK == 2 && NF > 1 && PAIR && sizeof(T) == 4;
   static constexpr int TY = TALL2 ? 128 : (RANK == 2 && NF == 1) ? 64 : (TALL3 || MULTI32) ? 64 : 32;
-  static constexpr int RY = PAIR ? ((TALL2 || TALL3) ? 8 : 4) : (RANK == 2 ? 16 : 8);
+  static constexpr int RY = PAIR ? (((RANK == 2 && NF == 1) || TALL3) ? 8 : 4) : (RANK == 2 ? 16 : 8);
   static constexpr int S = RANK == 3 ? (NF == 3 ? 6 : 8) : 3;
 };
 
@@ -354,7 +356,8 @@ __device__ __forceinline__ void tile2d(const Op& op, unsigned char* st, T* const
 
 // ------------------------------------------------------------------ column pairs
 // Paired consumers (FP32/BF16 storage): each thread computes two adjacent
-// columns cx2, cx2+1 with the packed f32x2 instructions.  Pair loads and
+// columns cx2, cx2+1 with the packed f32x2 instructions (adjoint functors'
+// per-point terms are summed per lane and added to the FP64 block sum).  Pair loads and
 // stores are 8 bytes (FP32) or 4 bytes (BF16) and aligned, since cx2, CW and
 // the box width are even.  x taps of radius <= 2 come from the aligned pairs
 // left (cx2-2, cx2-1) and right (cx2+2, cx2+3) of the centre pair.
@@ -459,7 +462,8 @@ __device__ __forceinline__ void fix_x_rows(unsigned char* st, const TileInfo& t,
 // column_pair path (2D edge tiles are a few percent of the tiles).
 template <bool YW, bool WRAP, class Op, class T, int TX, int TY, int RY>
 __device__ __forceinline__ void tile2d_pair(const Op& op, unsigned char* st, T* const* out, int nx,
-                                            int ny, const TileInfo& t, int cx2, int cy0) {
+                                            int ny, const TileInfo& t, int cx2, int cy0,
+                                            double& red) {
   constexpr int R = Op::R, NF = Op::NF, NC = RY + 2 * R;
   using L = Layout<T, TX, TY, R, NF>;
   static_assert(TX == 64, "a warp of pairs spans the tile");
@@ -477,6 +481,7 @@ __device__ __forceinline__ void tile2d_pair(const Op& op, unsigned char* st, T* 
   const bool xvalid = cx2 < t.nvx;  // nvx is even: a pair is all valid or all invalid
   const int64_t base = int64_t(t.y0 + cy0) * nx + t.x0 + cx2;
   const int64_t gclamp = int64_t(t.y0) * nx + t.x0;  // a valid pair for clamped reads
+  F2 rsum(0.f);  // adjoint terms of this pair of columns, summed in FP32 per lane
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
     PairAcc<T, TX, TY, R, NF, NC> acc;
@@ -487,13 +492,15 @@ __device__ __forceinline__ void tile2d_pair(const Op& op, unsigned char* st, T* 
     acc.r = r;
     acc.g = (xvalid && cy0 + r < t.nvy) ? base + int64_t(r) * nx : gclamp;
     F2 o[NF];
-    F2 unused(0.f);
-    op(acc, o, unused);
+    F2 r1(0.f);
+    op(acc, o, r1);
     if (xvalid && cy0 + r < t.nvy) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) st_pair(out[f] + base + int64_t(r) * nx, o[f]);
+      if (Op::REDUCES) rsum = add(rsum, r1);
     }
   }
+  if (Op::REDUCES) red += double(rsum.lo()) + double(rsum.hi());
 }
 
 // Box stencils on a tile whose halo wraps: each consumer warp (which spans
@@ -608,16 +615,16 @@ __global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32)
       if (WRAP && (t.xl || t.xr || t.yl || t.yh))
         fill_ring_warp<T, TX, TY, R, NF, RY>(st, t, p.in, p.nx, p.ny, p.per_x, p.per_y, cy0);
       if constexpr (PAIR)
-        tile2d_pair<false, false, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0);
+        tile2d_pair<false, false, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
       else
         tile2d<false, true, false, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
     } else if constexpr (PAIR) {
       // 2D edge tiles are a few percent of the tiles: one general instance for
       // all of them keeps the persistent loop's code small.
       if (!WRAP || !(t.yl || t.yh))
-        tile2d_pair<false, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0);
+        tile2d_pair<false, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
       else
-        tile2d_pair<true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0);
+        tile2d_pair<true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
     } else {
       if (!WRAP || !(t.yl || t.yh))
         tile2d<false, true, WRAP, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
@@ -719,7 +726,7 @@ template <bool YW, bool XF, bool SIMPLE, class Op, class T, int TX, int TY, int 
 __device__ __forceinline__ void march3d_pair(const TmaParams<Op, T>& p, unsigned char* smem,
                                              uint64_t* full, uint64_t* empty,
                                              volatile int* abort_flag, const TileInfo& t, int z0,
-                                             int z1, int np) {
+                                             int z1, int np, double& red) {
   constexpr int R = Op::R, NF = Op::NF, NQ = 2 * R + 1, NC = RY + 2 * R;
   using L = Layout<T, TX, TY, R, NF>;
   static_assert(TX == 64, "a warp of pairs spans the tile");
@@ -787,6 +794,7 @@ __device__ __forceinline__ void march3d_pair(const TmaParams<Op, T>& p, unsigned
     }
     const int64_t base = int64_t(z0 + m) * plane + int64_t(t.y0 + cy0) * p.nx + t.x0 + cx2;
     const int64_t gclamp = int64_t(z0 + m) * plane + int64_t(t.y0) * p.nx + t.x0;
+    F2 rsum(0.f);  // adjoint terms of this plane, summed in FP32 per lane
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
       PairAcc3<T, TX, TY, R, NF, NC, NQ> acc;
@@ -798,13 +806,15 @@ __device__ __forceinline__ void march3d_pair(const TmaParams<Op, T>& p, unsigned
       acc.g = (xvalid && cy0 + r < t.nvy) ? base + int64_t(r) * p.nx : gclamp;
       acc.q = q[r];
       F2 o[NF];
-      F2 unused(0.f);
-      p.op(acc, o, unused);
+      F2 r1(0.f);
+      p.op(acc, o, r1);
       if (xvalid && cy0 + r < t.nvy) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) st_pair(p.out[f] + base + int64_t(r) * p.nx, o[f]);
+        if (Op::REDUCES) rsum = add(rsum, r1);
       }
     }
+    if (Op::REDUCES) red += double(rsum.lo()) + double(rsum.hi());
     release(jc);
     if (jn >= np - R) release(jn);  // above z1-1: centres only
   }
@@ -875,7 +885,7 @@ __global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32, 2)
   do {                                                                                           \
     if constexpr (PAIR)                                                                          \
       march3d_pair<YW, XF, SIMPLE, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t,   \
-                                                         z0, z1, np);                            \
+                                                         z0, z1, np, red);                       \
     else                                                                                         \
       march3d<YW, XF, SIMPLE, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0,    \
                                                     z1, np, red);                                \

@@ -68,9 +68,19 @@ constexpr int kMinChunk = 48;
 // type T, rank RANK, halo radius R and NF fields; shared by the builtin
 // runner below and by run-time compiled local functions (jit.cu).  PAIR:
 // paired consumers (FP32/BF16 without reductions, radius <= 2).
-template <class T, int RANK, int R, int NF, bool PAIR>
+// Tall or short tiles for this launch: lope_launch.tile_y 1 / 2 forces short /
+// tall tiles on the TMA path; otherwise tall tiles from 2^22 points in 2D and
+// 2^26 in 3D (a 512^3 grid), where enough tiles remain to fill every SM.
+inline bool tma_tall(const StepArgs& a) {
+  if (a.tile_y == 1) return false;
+  if (a.tile_y == 2) return true;
+  const int64_t n = a.g.n[0] * a.g.n[1] * a.g.n[2];
+  return n >= (a.g.ndim == 3 ? (int64_t(1) << 26) : (int64_t(1) << 22));
+}
+
+template <class T, int RANK, int R, int NF, bool PAIR, bool TALL = true>
 struct TmaShape {
-  using Cfg = TmaCfg<T, RANK, R, NF, PAIR>;
+  using Cfg = TmaCfg<T, RANK, R, NF, PAIR, TALL>;
   static constexpr int TX = Cfg::TX, TY = Cfg::TY, RY = Cfg::RY, S = Cfg::S;
   using L = Layout<T, TX, TY, R, NF>;
   static constexpr int THREADS = (PAIR ? TX / 2 : TX) * (TY / RY) + 32;
@@ -135,6 +145,9 @@ struct TmaShape {
   }
 };
 
+// Paired consumers for FP32/BF16 storage (radius <= 2).  Adjoint functors
+// (reductions) stay on single-column consumers: measured faster for them (the
+// paired form would carry the reduction, see tile2d_pair / march3d_pair).
 template <class T, int R>
 constexpr bool tma_pair(bool reduces) {
   return !std::is_same<T, double>::value && !reduces && R <= 2 && TmaTx<T>::TX == 64;
@@ -143,49 +156,59 @@ constexpr bool tma_pair(bool reduces) {
 template <class Op, class T, int RANK>
 struct TmaRunner {
   static constexpr bool PAIR = tma_pair<T, Op::R>(Op::REDUCES);
-  using Sh = TmaShape<T, RANK, Op::R, Op::NF, PAIR>;
-  static constexpr int TX = Sh::TX, TY = Sh::TY, RY = Sh::RY, S = Sh::S;
-  static constexpr int THREADS = Sh::THREADS;
-  static constexpr size_t SMEM = Sh::SMEM;
+  template <bool TALL> using Sh = TmaShape<T, RANK, Op::R, Op::NF, PAIR, TALL>;
 
-  template <bool WRAP> static auto kernel_w() {
-    if constexpr (RANK == 2) return &tma2d_kernel<Op, T, TX, TY, RY, S, WRAP, PAIR>;
-    else return &tma3d_kernel<Op, T, TX, TY, RY, S, WRAP, PAIR>;
+  template <bool TALL, bool WRAP> static auto kernel_w() {
+    using S_ = Sh<TALL>;
+    if constexpr (RANK == 2) return &tma2d_kernel<Op, T, S_::TX, S_::TY, S_::RY, S_::S, WRAP, PAIR>;
+    else return &tma3d_kernel<Op, T, S_::TX, S_::TY, S_::RY, S_::S, WRAP, PAIR>;
   }
 
-  template <bool WRAP> static int occupancy_w() {
+  template <bool TALL, bool WRAP> static int occupancy_w() {
     static int occ = -1;
     if (occ < 0) {
-      cudaFuncSetAttribute(kernel_w<WRAP>(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM));
+      cudaFuncSetAttribute(kernel_w<TALL, WRAP>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(Sh<TALL>::SMEM));
       int o = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel_w<WRAP>(), THREADS, SMEM) !=
-          cudaSuccess)
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel_w<TALL, WRAP>(), Sh<TALL>::THREADS,
+                                                        Sh<TALL>::SMEM) != cudaSuccess)
         o = 1;
       occ = o > 0 ? o : 1;
     }
     return occ;
   }
-  static int occupancy(bool wrap) { return wrap ? occupancy_w<true>() : occupancy_w<false>(); }
+  template <bool TALL> static int occupancy(bool wrap) {
+    return wrap ? occupancy_w<TALL, true>() : occupancy_w<TALL, false>();
+  }
 
   template <class P>
   static void geometry(const StepArgs& a, P& p, int* blocks) {
-    Sh::geometry(a, p, blocks, [](bool wrap) { return occupancy(wrap); });
+    if (tma_tall(a)) Sh<true>::geometry(a, p, blocks, [](bool w) { return occupancy<true>(w); });
+    else Sh<false>::geometry(a, p, blocks, [](bool w) { return occupancy<false>(w); });
   }
 
-  static cudaError_t run(const StepArgs& a, const Op& op, int* blocks_out) {
+  template <bool TALL>
+  static cudaError_t run_t(const StepArgs& a, const Op& op, int* blocks_out) {
+    using S_ = Sh<TALL>;
     TmaParams<Op, T> p;
     p.op = op;
     int blocks = 0;
-    geometry(a, p, &blocks);
+    S_::geometry(a, p, &blocks, [](bool w) { return occupancy<TALL>(w); });
     if (blocks_out) *blocks_out = blocks;
     if (Op::REDUCES && (!a.partials || blocks > a.partial_count)) return cudaErrorInvalidValue;
     TmaMaps<Op::NF> maps;
-    cudaError_t e = Sh::prepare(a, p, maps);
+    cudaError_t e = S_::prepare(a, p, maps);
     if (e != cudaSuccess) return e;
-    if (p.per_x || p.per_y) kernel_w<true>()<<<blocks, THREADS, SMEM, a.stream>>>(maps, p);
-    else kernel_w<false>()<<<blocks, THREADS, SMEM, a.stream>>>(maps, p);
+    if (p.per_x || p.per_y)
+      kernel_w<TALL, true>()<<<blocks, S_::THREADS, S_::SMEM, a.stream>>>(maps, p);
+    else
+      kernel_w<TALL, false>()<<<blocks, S_::THREADS, S_::SMEM, a.stream>>>(maps, p);
     count_launches(1);
     return cudaGetLastError();
+  }
+
+  static cudaError_t run(const StepArgs& a, const Op& op, int* blocks_out) {
+    return tma_tall(a) ? run_t<true>(a, op, blocks_out) : run_t<false>(a, op, blocks_out);
   }
 };
 
