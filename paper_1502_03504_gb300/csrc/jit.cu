@@ -188,6 +188,7 @@ struct JitProgram {
     CUmodule mod = nullptr;
     std::vector<CUfunction> fn;
     std::vector<int> occ;
+    std::vector<size_t> smem;  // dynamic shared memory the function is opted in to
   };
   std::map<std::pair<int, int>, Loaded> loaded;  // (device, dtype)
 
@@ -357,15 +358,22 @@ cudaError_t get_kernel(JitProgram& jp, int dtype, int which, size_t smem, int th
     if (d.load(&ld.mod, c.cubin.data()) != CUDA_SUCCESS) return cudaErrorInvalidKernelImage;
     ld.fn.assign(c.lowered.size(), nullptr);
     ld.occ.assign(c.lowered.size(), -1);
+    ld.smem.assign(c.lowered.size(), 48 * 1024);
   }
   if (which >= int(c.lowered.size()) || c.lowered[which].empty()) return cudaErrorNotSupported;
   if (!ld.fn[which]) {
     CUfunction f = nullptr;
     if (d.get_fn(&f, ld.mod, c.lowered[which].c_str()) != CUDA_SUCCESS) return cudaErrorSymbolNotFound;
-    if (smem > 48 * 1024 &&
-        d.set_attr(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(smem)) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
     ld.fn[which] = f;
+  }
+  // Opt in to the launch's dynamic shared memory when it exceeds what the
+  // function is set for (the trapezoid's window grows with tile and depth).
+  if (smem > ld.smem[which]) {
+    if (d.set_attr(ld.fn[which], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(smem)) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+    ld.smem[which] = smem;
+    ld.occ[which] = -1;
   }
   *fn = ld.fn[which];
   if (occ) {
@@ -383,7 +391,8 @@ cudaError_t launch(CUfunction fn, int blocks, int threads, size_t smem, cudaStre
                    void** args) {
   const CUresult r = driver().launch(fn, unsigned(blocks), 1, 1, unsigned(threads), 1, 1,
                                      unsigned(smem), reinterpret_cast<CUstream>(st), args, nullptr);
-  if (r != CUDA_SUCCESS) return cudaErrorLaunchFailure;
+  if (r == CUDA_ERROR_INVALID_VALUE) return cudaErrorInvalidValue;
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidConfiguration;  // the launch was rejected
   count_launches(1);
   return cudaSuccess;
 }

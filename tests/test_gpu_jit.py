@@ -222,3 +222,19 @@ def test_user_3d_box_takes_direct_path(lope, orc):
     got = to_host(_run(lope, g, st, u0, T)[0])
     want = orc.apply_source(u0s, BOX_3D, [0.1], T, bc=[0, 0, 1])
     assert normwise(got, want) <= 1e-12
+
+
+def test_user_trapezoid_with_large_shared_memory(lope, orc):
+    """Trapezoid tiles whose window needs more than 48 KB of shared memory
+    (two fields, RK3, depth 2) after a smaller launch of the same function."""
+    shape, T = (96, 200), 4
+    fl = _gs_fields(1420, shape)
+    dev, stored = zip(*(to_device(f, "f32") for f in fl))
+    g = _grid(lope, shape, "f32", 1, [0, 0], nf=2)
+    st = lope.Stencil.source(GRAY_SCOTT, ndim=2, radius=1, nfields=2, params=GRAY_SCOTT_PRM)
+    st.set_scheme("rk3")
+    small = _run(lope, g, st, list(dev), T, _launch(lope, TRAP, 64, 16, 1))
+    for launch in (_launch(lope, TRAP, 64, 32, 2), _launch(lope, TRAP, 128, 32, 2)):
+        outs = _run(lope, g, st, list(dev), T, launch)
+        for k in range(2):
+            assert torch.equal(outs[k], small[k]), (launch, k)
