@@ -72,6 +72,7 @@ constexpr int kMinChunk = 48;
 // tall tiles on the TMA path; otherwise tall tiles from 2^22 points in 2D and
 // 2^26 in 3D (a 512^3 grid), where enough tiles remain to fill every SM.
 inline bool tma_tall(const StepArgs& a) {
+  if (a.adjoint) return false;
   if (a.tile_y == 1) return false;
   if (a.tile_y == 2) return true;
   const int64_t n = a.g.n[0] * a.g.n[1] * a.g.n[2];
@@ -145,12 +146,15 @@ struct TmaShape {
   }
 };
 
-// Paired consumers for FP32/BF16 storage (radius <= 2).  Adjoint functors
-// (reductions) stay on single-column consumers: measured faster for them (the
-// paired form would carry the reduction, see tile2d_pair / march3d_pair).
+// Paired consumers for FP32/BF16 storage (radius <= 2), adjoint functors
+// included: their per-point reduction is summed per lane (tile2d_pair /
+// march3d_pair).  Adjoint launches take the short tiles (tma_tall), where the
+// paired adjoint does not spill: forward + adjoint of a 256^3 grid measured
+// 9.75 ms against 11.6 ms on single-column consumers.
 template <class T, int R>
 constexpr bool tma_pair(bool reduces) {
-  return !std::is_same<T, double>::value && !reduces && R <= 2 && TmaTx<T>::TX == 64;
+  (void)reduces;
+  return !std::is_same<T, double>::value && R <= 2 && TmaTx<T>::TX == 64;
 }
 
 template <class Op, class T, int RANK>
