@@ -450,6 +450,8 @@ def run_profile(args):
         st = L.Stencil.builtin("swe_cgrid", 0.02, 1.0, 1.0)
         kind, nf = "periodic", 3
         dtype, bpp = ("f32", 24) if name == "swe" else ("bf16", 12)
+    elif name == "batch":
+        return run_profile_batch(args, n)
     elif name in ("sweflux", "swefluxbf16"):
         shape, halo, pts = (n, n), 1, n * n
         st = L.Stencil.builtin("swe_flux", 0.02, 1.0, 0.5, 1.0)
@@ -479,6 +481,44 @@ def run_profile(args):
     us = a.elapsed_time(b) / args.steps * 1e3
     print(json.dumps({"profile": args.profile, "us_per_launch": us,
                       "alg_GBps": bpp * pts / (us * 1e-6) / 1e9}), flush=True)
+
+
+def run_profile_batch(args, ngrids):
+    """The first `ngrids` grids of the batched workload: one batched launch per
+    step (tile 128 x 32, 4 sweeps per pass, 4 sweeps = one pass)."""
+    import torch
+
+    import lope_inputs as LI
+    import paper_1502_03504_gb300 as L
+
+    dev = torch.device("cuda", 0)
+    shapes, kinds = LI.batch_shapes(1003, 512)
+    shapes, kinds = shapes[:ngrids], kinds[:ngrids]
+    grids, ins = [], []
+    for (ny, nx), k in zip(shapes, kinds):
+        g = L.Grid((ny, nx), "f32", halo=1)
+        g.set_boundaries([k, k])
+        grids.append(g)
+        ins.append(torch.from_numpy(LI.uniform_field(1003, (ny, nx)).astype(np.float32)).to(dev))
+    outs = [torch.empty_like(x) for x in ins]
+    works = [torch.empty_like(x) for x in ins]
+    s = L.Stencil.builtin("jacobi5", 0.2)
+    cfg = L.Launch(2, 128, 32, 4, -1)
+    wsb = torch.empty(L.batch_workspace_size(grids, s), dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        L.apply_batch(grids, s, ins, outs, works, 4, cfg, wsb)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        L.apply_batch(grids, s, ins, outs, works, 4, cfg, wsb)
+    b.record()
+    torch.cuda.synchronize()
+    L.sync_status()
+    pts = sum(y * x for y, x in shapes)
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"profile": f"batch:{ngrids}", "points": pts, "ms_per_launch": ms,
+                      "updates_per_s": 4 * pts / (ms / 1e3)}), flush=True)
 
 
 # ---------------------------------------------------------------- extra forms

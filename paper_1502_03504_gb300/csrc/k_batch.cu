@@ -10,6 +10,7 @@
 // through L2 (ld.global.cg), so no block reads a stale L1 line of data another
 // block wrote in the previous pass.
 #include <algorithm>
+#include <type_traits>
 
 #include "trap.cuh"
 
@@ -54,7 +55,27 @@ __device__ __forceinline__ int find_grid(const BatchGrid* grids, int ngrids, int
   return lo;
 }
 
-template <class Op, class T>
+// Tile policies: the variable-shape trapezoid (any tile and depth), or the
+// shape fixed at compile time (TrapFixed: every tap at an immediate offset).
+struct TileAny {
+  template <class Op, class T>
+  static __device__ __forceinline__ void run(const Op& op, const T* const* src, T* const* dst,
+                                             const TrapGrid& g, int x0, int y0, int tx, int ty,
+                                             int kp, C_t<T>* smem) {
+    trap_tile<Op, T>(op, src, dst, g, x0, y0, tx, ty, kp, smem);
+  }
+};
+template <int TX, int TY, int K>
+struct TileFixed {
+  template <class Op, class T>
+  static __device__ __forceinline__ void run(const Op& op, const T* const* src, T* const* dst,
+                                             const TrapGrid& g, int x0, int y0, int, int, int kp,
+                                             C_t<T>* smem) {
+    TrapFixed<Op, T, TX, TY, K>::tile(op, src, dst, g, x0, y0, kp, smem);
+  }
+};
+
+template <class Op, class T, class Tile>
 __global__ void __launch_bounds__(kBatchThreads) batch_kernel(Op op, BatchPlanDev p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ volatile int s_abort;
@@ -84,8 +105,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(Op op, BatchPlanDe
         }
       const T* srcs[1] = {src};
       T* dsts[1] = {dst};
-      trap_tile<Op, T>(op, srcs, dsts, tg, x0, y0, p.tile_x, p.tile_y, kp,
-                       reinterpret_cast<C_t<T>*>(smem_raw));
+      Tile::template run<Op, T>(op, srcs, dsts, tg, x0, y0, p.tile_x, p.tile_y, kp,
+                                reinterpret_cast<C_t<T>*>(smem_raw));
     }
     const bool arrive = !(pass == 0 && int(blockIdx.x) == p.skip_block);
     if (pass + 1 < passes &&
@@ -94,9 +115,9 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(Op op, BatchPlanDe
   }
 }
 
-template <class Op, class T> struct BatchRunner {
+template <class Op, class T, class Tile> struct BatchRunner {
   static cudaError_t prepare(size_t smem) {
-    return cudaFuncSetAttribute(&batch_kernel<Op, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(&batch_kernel<Op, T, Tile>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(smem));
   }
   static int max_blocks(size_t smem) {
@@ -104,7 +125,7 @@ template <class Op, class T> struct BatchRunner {
     int occ = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, &batch_kernel<Op, T>, kBatchThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, &batch_kernel<Op, T, Tile>, kBatchThreads,
                                                       smem) != cudaSuccess)
       return 0;
     return occ * sms;
@@ -123,7 +144,7 @@ template <class Op, class T> struct BatchRunner {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, &batch_kernel<Op, T>, op, p);
+    e = cudaLaunchKernelEx(&cfg, &batch_kernel<Op, T, Tile>, op, p);
     count_launches(1);
     return e;
   }
@@ -137,18 +158,38 @@ template <class T, class F> auto with_op(const StencilDesc& s, F&& f) {
   return f(op);
 }
 
+// Run F with the tile policy for (tile_x, tile_y, k): the fixed shapes the
+// batch autotuner tries for FP32 storage, else the variable-shape tile.
+template <class T, class F>
+auto with_tile(int tx, int ty, int k, F&& f) {
+  if constexpr (std::is_same<T, float>::value) {
+#define LOPE_FIXED(X, Y, KK) \
+    if (tx == X && ty == Y && k == KK) return f(TileFixed<X, Y, KK>());
+    LOPE_FIXED(128, 32, 4) LOPE_FIXED(128, 32, 2) LOPE_FIXED(64, 32, 4) LOPE_FIXED(64, 32, 2)
+    LOPE_FIXED(128, 16, 4) LOPE_FIXED(128, 16, 2) LOPE_FIXED(64, 16, 4) LOPE_FIXED(64, 16, 2)
+#undef LOPE_FIXED
+  }
+  return f(TileAny());
+}
+
 template <class T>
 cudaError_t launch_t(const BatchPlanDev& p, const StencilDesc& s, int blocks, cudaStream_t st) {
   const size_t smem = trap_smem_bytes(sizeof(T) == 8 ? kF64 : kF32, 1, p.tile_x, p.tile_y,
                                       s.radius * p.ksteps);
   return with_op<T>(s, [&](auto op) {
-    return BatchRunner<decltype(op), T>::launch(op, p, blocks, smem, st);
+    return with_tile<T>(p.tile_x, p.tile_y, p.ksteps, [&](auto tile) {
+      return BatchRunner<decltype(op), T, decltype(tile)>::launch(op, p, blocks, smem, st);
+    });
   });
 }
 
 template <class T> int max_blocks_t(const StencilDesc& s, int tx, int ty, int k) {
   const size_t smem = trap_smem_bytes(sizeof(T) == 8 ? kF64 : kF32, 1, tx, ty, s.radius * k);
-  return with_op<T>(s, [&](auto op) { return BatchRunner<decltype(op), T>::max_blocks(smem); });
+  return with_op<T>(s, [&](auto op) {
+    return with_tile<T>(tx, ty, k, [&](auto tile) {
+      return BatchRunner<decltype(op), T, decltype(tile)>::max_blocks(smem);
+    });
+  });
 }
 
 }  // namespace

@@ -123,6 +123,115 @@ __device__ __forceinline__ void trap_tile(const Op& op, const T* const* src, T* 
   __syncthreads();
 }
 
+// ------------------------------------------------------------------ fixed shape
+// The trapezoid tile with its shape (TX x TY, up to K sweeps) fixed at compile
+// time, for 256-thread blocks: thread (tx, ty) = (lane, warp) owns the window
+// cells (tx + 32c, ty + 8r), so every tap of the local function is a shared
+// load at a compile-time offset from the cell's address.  Each sweep updates
+// every cell of [R, W-R) x [R, H-R), a superset of the shrinking trapezoid
+// region: a cell outside the region after sweep s is computed from values
+// that are no longer exact, but it only feeds cells outside the region of
+// sweep s+1, so the central TX x TY tile is exact after the last sweep (the
+// same values the variable-shape trap_tile computes, operation for
+// operation).  Windows that cross a Dirichlet side mask those cells to the
+// halo value in every sweep; periodic windows need no mask (the window holds
+// the periodic extension).
+template <class C, int NF, int W, int HW>
+struct FixedAcc {
+  const C* p;  // the cell in field 0 of the current buffer
+  __device__ __forceinline__ C operator()(int f, int dx, int dy, int) const {
+    return p[f * HW + dy * W + dx];
+  }
+  __device__ __forceinline__ int64_t gidx() const { return 0; }
+};
+
+template <class Op, class T, int TX, int TY, int K>
+struct TrapFixed {
+  using C = C_t<T>;
+  static constexpr int R = Op::R, NF = Op::NF;
+  static constexpr int h = R * K, W = TX + 2 * h, H = TY + 2 * h, HW = W * H;
+  static constexpr int NXC = (W + 31) / 32, NYC = (H + 7) / 8;
+  static constexpr size_t SMEM = 2 * size_t(NF) * HW * sizeof(C);
+
+  // kp <= K sweeps from src to dst for the tile at (x0, y0); blockDim.x = 256.
+  static __device__ __forceinline__ void tile(const Op& op, const T* const* src, T* const* dst,
+                                              const TrapGrid& g, int x0, int y0, int kp, C* smem) {
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+    C* b0 = smem;
+    C* b1 = smem + NF * HW;
+    const bool inside = x0 - h >= 0 && y0 - h >= 0 && x0 + TX + h <= g.nx && y0 + TY + h <= g.ny;
+    const bool dirichlet = g.bc[0][0] == kDirichlet || g.bc[0][1] == kDirichlet ||
+                           g.bc[1][0] == kDirichlet || g.bc[1][1] == kDirichlet;
+    const bool masked = !inside && dirichlet;
+#pragma unroll
+    for (int r = 0; r < NYC; ++r) {
+      const int j = ty + 8 * r;
+      if (j >= H) break;
+      const int gy = y0 - h + j;
+#pragma unroll
+      for (int c = 0; c < NXC; ++c) {
+        const int i = tx + 32 * c;
+        if (i < W) {
+          const int gx = x0 - h + i;
+#pragma unroll
+          for (int f = 0; f < NF; ++f)
+            b0[f * HW + j * W + i] = inside ? to_c(__ldcg(src[f] + int64_t(gy) * g.nx + gx))
+                                            : halo_read<T>(src[f], g, gy, gx);
+        }
+      }
+    }
+    __syncthreads();
+    for (int s = 1; s <= kp; ++s) {
+      const C* cur = (s & 1) ? b0 : b1;
+      C* nxt = (s & 1) ? b1 : b0;
+#pragma unroll
+      for (int r = 0; r < NYC; ++r) {
+        const int j = ty + 8 * r;
+        if (j < R || j >= H - R) continue;
+#pragma unroll
+        for (int c = 0; c < NXC; ++c) {
+          const int i = tx + 32 * c;
+          if (i < R || i >= W - R) continue;
+          const int o = j * W + i;
+          double v;
+          if (masked && outside_dirichlet(g, y0 - h + j, x0 - h + i, &v)) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) nxt[f * HW + o] = C(v);
+            continue;
+          }
+          FixedAcc<C, NF, W, HW> acc{cur + o};
+          C out[NF];
+          C unused = C(0);
+          op(acc, out, unused);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) nxt[f * HW + o] = to_storage_precision<T>(out[f]);
+        }
+      }
+      __syncthreads();
+    }
+    const C* fin = (kp & 1) ? b1 : b0;
+#pragma unroll
+    for (int r = 0; r < NYC; ++r) {
+      const int j = ty + 8 * r;
+      if (j < h || j >= h + TY) continue;
+      const int gy = y0 + j - h;
+      if (gy >= g.ny) continue;
+#pragma unroll
+      for (int c = 0; c < NXC; ++c) {
+        const int i = tx + 32 * c;
+        if (i < h || i >= h + TX) continue;
+        const int gx = x0 + i - h;
+        if (gx < g.nx) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f)
+            dst[f][int64_t(gy) * g.nx + gx] = from_c<T>(fin[f * HW + j * W + i]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+};
+
 // One sweep of the window region [lo, W-lo) x [lo, H-lo) for the multi-stage
 // tile: nxt = E(cur), or, when `comb`, nxt = a * base + b * E(cur) (base read
 // at the local element only).  Cells outside a Dirichlet side keep their halo
