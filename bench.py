@@ -697,15 +697,10 @@ def form_batch(L, LI, torch, dev, peak):
     T = 20
     pts = sum(a * b for a, b in shapes)
     wsb = torch.empty(L.batch_workspace_size(grids, s), dtype=torch.uint8, device=dev)
-    best = None
-    for k in (1, 2, 4, 5):
-        for tx, ty in ((64, 32), (128, 16), (64, 16), (128, 32)):
-            cfg = L.Launch(2, tx, ty, k, -1)
-            ms = _time(torch, lambda: L.apply_batch(grids, s, ins, outs, works, T, cfg, wsb), reps=2)
-            if best is None or ms < best[0]:
-                best = (ms, k, tx, ty)
-    ms, k, tx, ty = best
-    ms = _time(torch, lambda: L.apply_batch(grids, s, ins, outs, works, T, L.Launch(2, tx, ty, k, -1), wsb), reps=5)
+    best, _ = L.autotune_batch(grids, s, ins, outs, works, T, workspace=wsb)  # library autotuner
+    tx, ty, k = best.tile_x, best.tile_y, best.tsteps
+    # cfg None: lope_apply_batch takes the tuned choice from the autotuner cache
+    ms = _time(torch, lambda: L.apply_batch(grids, s, ins, outs, works, T, None, wsb), reps=5)
     per1 = L.Launch(2, 64, 32, 1, -1)
 
     def per_grid():

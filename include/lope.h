@@ -216,9 +216,10 @@ lope_status lope_autotune(const lope_grid* grid, const lope_stencil* stencil,
  * hold n*nfields pointers, grid-major.  workspace is caller device memory of at
  * least lope_batch_workspace_size bytes; it holds the work list and the
  * inter-block barrier and must stay untouched between calls that reuse it.
- * cfg may be NULL (tile and temporal depth from the batch autotuner cache or
- * defaults).  Errors as lope_apply; LOPE_ERR_TIMEOUT is reported by
- * lope_sync_status if a bounded barrier wait gave up. */
+ * cfg may be NULL (tile and temporal depth from the batch autotuner cache,
+ * see lope_autotune_batch, else 64 x 32 tiles and depth 4).  Errors as
+ * lope_apply; LOPE_ERR_TIMEOUT is reported by lope_sync_status if a bounded
+ * barrier wait gave up. */
 lope_status lope_batch_workspace_size(int n, const lope_grid* const* grids,
                                       const lope_stencil* stencil, const lope_launch* cfg,
                                       size_t* bytes);
@@ -226,6 +227,17 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
                              const void* const* in, void* const* out, void* const* work,
                              int64_t nsteps, const lope_launch* cfg, void* workspace,
                              size_t workspace_bytes, void* cuda_stream);
+
+/* Batch autotuner: times the batched launch over tile shapes {128, 64} x {32,
+ * 16} and temporal depths {1, 2, 4, 5} on the caller's buffers (out and work
+ * are overwritten), stores the fastest for this batch (grid extents and
+ * boundaries, dtype, stencil) and returns it in *best (*best_ms its time for
+ * nsteps).  Later lope_apply_batch calls with cfg NULL (or zero tile/depth) on
+ * a batch with the same signature use it.  Synchronises the stream. */
+lope_status lope_autotune_batch(int n, const lope_grid* const* grids, const lope_stencil* stencil,
+                                const void* const* in, void* const* out, void* const* work,
+                                int64_t nsteps, void* workspace, size_t workspace_bytes,
+                                lope_launch* best, double* best_ms, void* cuda_stream);
 
 /* Differentiation of u_T = A^T u_0 for linear stencils, by the discrete adjoint
  * (transposed stencil, run backward in time) with recomputation from

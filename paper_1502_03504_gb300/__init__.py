@@ -24,6 +24,7 @@ from ._lib import (  # noqa: F401
     apply_host,
     adjoint,
     autotune,
+    autotune_batch,
     batch_workspace_size,
     forward_ckpt,
     launch_count,
@@ -43,6 +44,7 @@ from ._lib import (  # noqa: F401  (C ABI names)
     lope_apply_batch,
     lope_apply_with,
     lope_autotune,
+    lope_autotune_batch,
     lope_batch_workspace_size,
     lope_forward_ckpt,
     lope_grid_create,

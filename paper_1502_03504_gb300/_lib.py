@@ -71,6 +71,8 @@ _SIGS = {
     "lope_autotune": (_INT, [_P, _P, _PP, _PP, _PP, _I64, ctypes.POINTER(Launch), _DP, _P]),
     "lope_batch_workspace_size": (_INT, [_INT, _PP, _P, ctypes.POINTER(Launch), ctypes.POINTER(_SZ)]),
     "lope_apply_batch": (_INT, [_INT, _PP, _P, _PP, _PP, _PP, _I64, ctypes.POINTER(Launch), _P, _SZ, _P]),
+    "lope_autotune_batch": (_INT, [_INT, _PP, _P, _PP, _PP, _PP, _I64, _P, _SZ,
+                                   ctypes.POINTER(Launch), _DP, _P]),
     "lope_workspace_size": (_INT, [_P, _P, _I64, _I64, ctypes.POINTER(_SZ)]),
     "lope_forward_ckpt": (_INT, [_P, _P, _P, _P, _I64, _I64, _P, _SZ, _P]),
     "lope_vjp": (_INT, [_P, _P, _P, _P, _I64, _I64, _INT, _P, _P, _P, _SZ, _P]),
@@ -461,6 +463,29 @@ def apply_batch(grids, stencil, inputs, outs=None, works=None, nsteps=1, launch=
                      [_dptr(t) for t in outs], [_dptr(t) for t in works], nsteps, launch,
                      _dptr(workspace), workspace.numel(), _stream(stream))
     return outs
+
+
+def lope_autotune_batch(grids, stencil, ins, outs, works, nsteps, ws, ws_bytes, stream):
+    best = Launch()
+    ms = ctypes.c_double(0.0)
+    _check(load().lope_autotune_batch(len(grids), _ptrs(grids), stencil, _ptrs(ins), _ptrs(outs),
+                                      _ptrs(works), int(nsteps), ws, int(ws_bytes),
+                                      ctypes.byref(best), ctypes.byref(ms), stream))
+    return best, ms.value
+
+
+def autotune_batch(grids, stencil, inputs, outs, works, nsteps, workspace=None, stream=None):
+    """Time the batched launch's tile shapes and depths on these buffers and
+    remember the fastest for this batch; returns (Launch, ms)."""
+    import torch
+
+    nb = batch_workspace_size(grids, stencil)
+    if workspace is None:
+        workspace = torch.empty(nb, dtype=torch.uint8, device=inputs[0].device)
+    return lope_autotune_batch([g.handle for g in grids], stencil.handle,
+                               [_dptr(t) for t in inputs], [_dptr(t) for t in outs],
+                               [_dptr(t) for t in works], nsteps, _dptr(workspace),
+                               workspace.numel(), _stream(stream))
 
 
 def workspace_size(grid, stencil, nsteps, ckpt):

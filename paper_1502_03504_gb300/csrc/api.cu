@@ -596,6 +596,35 @@ std::map<std::vector<int64_t>, std::shared_ptr<BatchPlan>> g_batch;
 
 size_t batch_ws_bytes(int n) { return 256 + (size_t(n) * sizeof(BatchGrid) + 255) / 256 * 256; }
 
+// Batch autotuner cache: the fastest (tile, depth) per batch signature (grid
+// shapes and boundaries, dtype, stencil), filled by lope_autotune_batch.
+using BatchSig = std::vector<int64_t>;
+std::mutex g_btune_mu;
+std::map<BatchSig, Choice> g_btune;
+
+BatchSig batch_sig(int n, const lope_grid* const* grids, const StencilDesc& s) {
+  BatchSig k = {int64_t(n), int64_t(grids[0]->g.dtype), s.kind, s.radius, s.stages,
+                int64_t(reinterpret_cast<uintptr_t>(s.jit))};
+  for (int i = 0; i < 4; ++i) {
+    int64_t b;
+    std::memcpy(&b, &s.prm[i], 8);
+    k.push_back(b);
+  }
+  for (int i = 0; i < n; ++i) {
+    const Geom& g = grids[i]->g;
+    k.push_back(g.n[1]);
+    k.push_back(g.n[2]);
+    for (int ax = 1; ax < 3; ++ax)
+      for (int sd = 0; sd < 2; ++sd) {
+        k.push_back(g.bc[ax][sd]);
+        int64_t b;
+        std::memcpy(&b, &g.bval[ax][sd], 8);
+        k.push_back(b);
+      }
+  }
+  return k;
+}
+
 }  // namespace
 
 void count_launches(int64_t n) {
@@ -916,9 +945,15 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
     void* work1[1] = {work ? work[i] : nullptr};
     if ((rs = check_fields(grids[i]->g, in1, out1, work1, true)) != LOPE_OK) return rs;
   }
-  const int tx = cfg && cfg->tile_x > 0 ? cfg->tile_x : 64;
-  const int ty = cfg && cfg->tile_y > 0 ? cfg->tile_y : 32;
-  const int k = cfg && cfg->tsteps > 0 ? cfg->tsteps : 4;
+  Choice tuned = {kPathTrap, 64, 32, 4};  // defaults, or the autotuner's choice for this batch
+  if (!cfg || cfg->tile_x <= 0 || cfg->tile_y <= 0 || cfg->tsteps <= 0) {
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    auto it = g_btune.find(batch_sig(n, grids, s));
+    if (it != g_btune.end()) tuned = it->second;
+  }
+  const int tx = cfg && cfg->tile_x > 0 ? cfg->tile_x : tuned.tile_x;
+  const int ty = cfg && cfg->tile_y > 0 ? cfg->tile_y : tuned.tile_y;
+  const int k = cfg && cfg->tsteps > 0 ? cfg->tsteps : tuned.k;
   if (tx < 8 || tx > 256 || ty < 1 || ty > 256 || k < 1 || k > 8)
     return fail(LOPE_ERR_INVALID, "bad batch tile or depth");
   DevState* d = nullptr;
@@ -1015,6 +1050,52 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
   cudaError_t e = cudaGraphLaunch(plan->exec, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch(batch)");
   count_launches(1);
+  return LOPE_OK;
+}
+
+lope_status lope_autotune_batch(int n, const lope_grid* const* grids, const lope_stencil* stencil,
+                                const void* const* in, void* const* out, void* const* work,
+                                int64_t nsteps, void* workspace, size_t workspace_bytes,
+                                lope_launch* best, double* best_ms, void* cuda_stream) {
+  if (n < 1 || !grids || !stencil) return fail(LOPE_ERR_INVALID, "NULL argument");
+  if (nsteps < 1) return fail(LOPE_ERR_INVALID, "autotune needs nsteps >= 1");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int tiles[][2] = {{128, 32}, {64, 32}, {128, 16}, {64, 16}};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double bms = 1e300;
+  lope_launch bl = {0, 0, 0, 0, 0};
+  lope_status last = LOPE_OK;
+  for (const auto& t : tiles)
+    for (int k : {1, 2, 4, 5}) {
+      const lope_launch c = {kPathTrap, t[0], t[1], k, -1};
+      // first call builds and caches the plan's graph; the second is timed
+      if ((last = lope_apply_batch(n, grids, stencil, in, out, work, nsteps, &c, workspace,
+                                   workspace_bytes, cuda_stream)) != LOPE_OK)
+        continue;
+      cudaEventRecord(e0, st);
+      last = lope_apply_batch(n, grids, stencil, in, out, work, nsteps, &c, workspace,
+                              workspace_bytes, cuda_stream);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess || last != LOPE_OK) continue;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < bms) {
+        bms = ms;
+        bl = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (bl.path == 0) return last != LOPE_OK ? last : fail(LOPE_ERR_UNSUPPORTED, "no batched plan ran");
+  g_last_error = "no error";
+  {
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    g_btune[batch_sig(n, grids, stencil->s)] = {kPathTrap, bl.tile_x, bl.tile_y, bl.tsteps};
+  }
+  if (best) *best = bl;
+  if (best_ms) *best_ms = bms;
   return LOPE_OK;
 }
 

@@ -229,3 +229,28 @@ def test_adjoint_full_size_256_dot_product(lope):
     rhs = float(torch.sum(x.double() * ATy.double()))
     assert abs(lhs - rhs) <= 1e-5 * (abs(lhs) + float(torch.sum(torch.abs(Ax.double() * y.double()))) * 1e-2)
     assert np.isfinite(float(gc.item()))
+
+
+def test_batch_autotuner_choice_is_used_and_bitwise_equal(lope):
+    """lope_autotune_batch stores its choice; a later lope_apply_batch with no
+    launch configuration uses it, and gives bitwise what the explicit choice
+    (and each grid advanced alone with that tile and depth) gives."""
+    shapes = [(70, 130), (33, 257), (128, 64), (200, 201), (5, 300)]
+    kinds = [0, 1, 1, 0, 1]
+    grids, ins, _ = _batch_setup(lope, shapes, kinds, "f32", 1600)
+    st = lope.Stencil.builtin("jacobi5", 0.2)
+    outs = [torch.empty_like(x) for x in ins]
+    works = [torch.empty_like(x) for x in ins]
+    best, ms = lope.autotune_batch(grids, st, ins, outs, works, 9)
+    assert best.path == 2 and best.tile_x in (64, 128) and best.tsteps in (1, 2, 4, 5) and ms > 0
+    auto = [o.clone() for o in lope.apply_batch(grids, st, ins, nsteps=9)]
+    explicit = lope.apply_batch(grids, st, ins, nsteps=9,
+                                launch=lope.Launch(2, best.tile_x, best.tile_y, best.tsteps, -1))
+    torch.cuda.synchronize()
+    lope.sync_status()
+    for a, b, g, i in zip(auto, explicit, grids, ins):
+        assert torch.equal(a, b)
+        alone = lope.apply(g, st, i, nsteps=9,
+                           launch=lope.Launch(2, best.tile_x, best.tile_y, best.tsteps, -1))
+        torch.cuda.synchronize()
+        assert torch.equal(alone, a)
