@@ -288,6 +288,12 @@ lope_status lope_reduce(int op, lope_dtype dtype, const void* x, const void* y, 
  *                        run out and lope_sync_status reports LOPE_ERR_TIMEOUT
  *                        (-1, the default, disables it).  No fault is raised on
  *                        the GPU: every wait ends by itself.
+ *   "log"                1: print each distinct plan that lope_apply and
+ *                        lope_apply_with resolve, once, as one line on stderr
+ *                        (grid, boundaries, local function, scheme, path, tile,
+ *                        depth, launch count, graph); 0: silent.  The initial
+ *                        value is that of the LOPE_LOG environment variable
+ *                        (unset: 0).
  * Errors: LOPE_ERR_INVALID for an unknown name or out-of-range value. */
 lope_status lope_set_option(const char* name, int64_t value);
 

@@ -10,11 +10,13 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <initializer_list>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -234,6 +236,58 @@ lope_status resolve(const Geom& g, const StencilDesc& s, const void* const* in,
   return LOPE_OK;
 }
 
+// Plan log: with option "log" = 1 (initially the value of the LOPE_LOG
+// environment variable), every distinct plan an apply call resolves is printed
+// once on stderr: the grid, the local function and the launch sequence.
+std::atomic<int> g_log{-1};
+std::mutex g_log_mu;
+std::set<std::vector<int64_t>> g_logged;
+
+bool log_enabled() {
+  int v = g_log.load();
+  if (v < 0) {
+    const char* e = std::getenv("LOPE_LOG");
+    v = (e && std::atoi(e) > 0) ? 1 : 0;
+    int expect = -1;
+    g_log.compare_exchange_strong(expect, v);
+    v = g_log.load();
+  }
+  return v > 0;
+}
+
+void log_plan(const Geom& g, const StencilDesc& s, const Choice& c, int64_t nsteps,
+              int64_t launches, bool graph) {
+  static const char* kinds[] = {"linear", "jacobi5", "diff7", "star9r2", "swe_cgrid", "swe_flux",
+                                "source"};
+  static const char* dtypes[] = {"f64", "f32", "bf16"};
+  static const char* paths[] = {"auto", "tma", "trapezoid", "direct"};
+  static const char* bcs[] = {"periodic", "dirichlet"};
+  std::vector<int64_t> key{g.ndim, g.n[0], g.n[1], g.n[2], g.dtype, g.nf, s.kind, s.radius,
+                           s.stages, c.path, c.tile_x, c.tile_y, c.k, nsteps, graph};
+  for (int ax = 0; ax < 3; ++ax) key.insert(key.end(), {g.bc[ax][0], g.bc[ax][1]});
+  {
+    std::lock_guard<std::mutex> lk(g_log_mu);
+    if (!g_logged.insert(key).second) return;
+  }
+  // extents and boundaries slowest axis first, as the caller's shape
+  char ext[64];
+  if (g.ndim == 2) std::snprintf(ext, sizeof ext, "%lldx%lld", (long long)g.n[1], (long long)g.n[2]);
+  else std::snprintf(ext, sizeof ext, "%lldx%lldx%lld", (long long)g.n[0], (long long)g.n[1],
+                     (long long)g.n[2]);
+  std::string bc;
+  for (int ax = 3 - g.ndim; ax < 3; ++ax) {
+    if (ax > 3 - g.ndim) bc += ",";
+    bc += bcs[g.bc[ax][0] == kDirichlet];
+    if (g.bc[ax][1] != g.bc[ax][0]) bc += std::string("/") + bcs[g.bc[ax][1] == kDirichlet];
+  }
+  std::fprintf(stderr,
+               "lope: grid %s %s nf=%d bc=[%s] | %s r=%d %s | path=%s tile=%dx%d k=%d | "
+               "nsteps=%lld launches=%lld graph=%d\n",
+               ext, dtypes[g.dtype], g.nf, bc.c_str(), kinds[s.kind], s.radius,
+               s.stages == 1 ? "euler" : s.stages == 2 ? "rk2" : "rk3", paths[c.path], c.tile_x,
+               c.tile_y, c.k, (long long)nsteps, (long long)launches, int(graph));
+}
+
 // Multi-stage steps as one launch per stage (TMA or direct kernels).  Step j
 // starts from b = in (j = 0) or out; with work state W1 (and W2, the second
 // state of each work buffer, for RK3):
@@ -407,6 +461,7 @@ lope_status apply_impl(const lope_grid* grid, const lope_stencil* st, const void
   }
   const int gmode = cfg ? cfg->graph : 0;
   const bool use_graph = gmode == 1 || (gmode == 0 && L >= 8 && npts(g) <= (int64_t(1) << 22));
+  if (log_enabled()) log_plan(g, s, c, nsteps, L, use_graph);
   if (use_graph) {
     return run_graph(graph_key(g, s, c, in, out, work, nsteps), stream, [&](cudaStream_t cs) {
       cudaError_t e = issue(g, s, c, in, out, work, nsteps, d->err, cs);
@@ -1219,6 +1274,11 @@ lope_status lope_set_option(const char* name, int64_t value) {
   if (n == "wait_limit_ms") {
     if (value < 1 || value > 600000) return fail(LOPE_ERR_INVALID, "wait_limit_ms out of range");
     g_wait_limit_ms = value;
+    return LOPE_OK;
+  }
+  if (n == "log") {
+    if (value < 0 || value > 1) return fail(LOPE_ERR_INVALID, "log must be 0 or 1");
+    g_log = int(value);
     return LOPE_OK;
   }
   if (n == "batch_skip_arrive") {

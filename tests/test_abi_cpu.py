@@ -92,6 +92,9 @@ def test_set_option_validation(lope):
         lope.lope_set_option("wait_limit_ms", 0)
     lope.lope_set_option("wait_limit_ms", 1000)
     lope.lope_set_option("batch_skip_arrive", -1)
+    with pytest.raises(lope.LopeError):
+        lope.lope_set_option("log", 2)
+    lope.lope_set_option("log", 0)
 
 
 def test_noalloc_reduce_rejects_bad_arguments_without_gpu(lope):

@@ -49,3 +49,26 @@ def test_apply_host_multi_field_two_streams(lope):
     for ho, _ in outs:
         for k in range(3):
             assert torch.equal(ho[k], ref[k].cpu()), k
+
+
+def test_plan_log_one_line_per_distinct_plan(lope, capfd):
+    shape = (96, 200)
+    u = torch.rand(shape, device="cuda")
+    g = lope.Grid(shape, "f32", halo=1)
+    g.set_boundaries([1, 0])
+    st = lope.Stencil.builtin("jacobi5", 0.2)
+    lope.lope_set_option("log", 1)
+    try:
+        for _ in range(3):
+            lope.apply(g, st, u, nsteps=3, launch=lope.Launch(1, 0, 0, 0, -1))
+        lope.apply(g, st, u, nsteps=3, launch=lope.Launch(3, 0, 0, 0, -1))
+        torch.cuda.synchronize()
+    finally:
+        lope.lope_set_option("log", 0)
+    lope.apply(g, st, u, nsteps=4)  # silent again
+    torch.cuda.synchronize()
+    lines = [ln for ln in capfd.readouterr().err.splitlines() if ln.startswith("lope: ")]
+    assert len(lines) == 2, lines
+    assert "grid 96x200 f32 nf=1 bc=[dirichlet,periodic]" in lines[0]
+    assert "jacobi5 r=1 euler" in lines[0] and "path=tma" in lines[0]
+    assert "launches=3" in lines[0] and "path=direct" in lines[1]
