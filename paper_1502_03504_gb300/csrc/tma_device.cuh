@@ -505,40 +505,64 @@ __device__ __forceinline__ void tile2d_pair(const Op& op, unsigned char* st, T* 
 
 // Box stencils on a tile whose halo wraps: each consumer warp (which spans
 // the whole tile width, RY rows from cy0) rewrites the halo-ring cells of the
-// wide box that its own rows read -- tile rows cy0-R .. min(cy0+RY, nvy)+R-1,
-// columns -R .. nvx+R-1, outside the tile's valid cells -- from the wrapped
-// global coordinates, or 0 where a Dirichlet side is crossed (the TMA zero
-// fill already holds that value).  Adjacent warps may write the same cell
-// with the same value.  The proxy fence orders these shared-memory writes
-// before the stage's next TMA refill; no block-wide barrier is needed.
+// wide box that its own rows read (tile rows cy0-R .. min(cy0+RY, nvy)+R-1,
+// columns -R .. nvx+R-1, outside the tile's valid cells) whose global
+// position lies outside the grid on periodic axes only: those take the value
+// at the wrapped position.  Every other ring cell already holds the right
+// value from the TMA box (in-range data, or the zero fill past a Dirichlet
+// side).  The cells are enumerated as the 2R halo columns of the warp's body
+// rows, then its halo rows over the full box width; each lane takes K cells
+// per pass and issues all their loads before any store, so a warp has up to
+// K * NF loads in flight.  Adjacent warps may write the same cell with the
+// same value.  The proxy fence orders these shared-memory writes before the
+// stage's next TMA refill; no block-wide barrier is needed.
 template <class T, int TX, int TY, int R, int NF, int RY>
 __device__ __forceinline__ void fill_ring_warp(unsigned char* st, const TileInfo& t,
                                                const T* const* in, int nx, int ny, int per_x,
                                                int per_y, int cy0) {
   using L = Layout<T, TX, TY, R, NF>;
+  constexpr int K = 4;
   const int lane = threadIdx.x % 32;
   if (cy0 < t.nvy) {
     const int r0 = cy0 - R, r1 = min(cy0 + RY, t.nvy) + R;  // rows [r0, r1)
+    const int b0 = max(r0, 0), b1 = min(r1, t.nvy);          // body rows among them
+    const int na = (b1 - b0) * 2 * R;                        // halo-column cells of the body rows
+    const int nlo = max(0, -r0), nhi = max(0, r1 - t.nvy);   // halo rows above / below
     const int wr = t.nvx + 2 * R;
-    for (int c = lane; c < (r1 - r0) * wr; c += 32) {
-      const int tr = r0 + c / wr, tc = c % wr - R;
-      if (tr >= 0 && tr < t.nvy && tc >= 0 && tc < t.nvx) continue;  // valid cell: from TMA
-      int gy = t.y0 + tr, gx = t.x0 + tc;
-      bool zero = false;
-      if (gy < 0 || gy >= ny) {
-        if (per_y) gy = wrap(gy, ny);
-        else zero = true;
-      }
-      if (gx < 0 || gx >= nx) {
-        if (per_x) gx = wrap(gx, nx);
-        else zero = true;
-      }
-      const int64_t gi = int64_t(gy) * nx + gx;
+    const int n = na + (nlo + nhi) * wr;
+    for (int c0 = 0; c0 < n; c0 += 32 * K) {
+      int si[K];
+      int64_t gi[K];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        T* box = reinterpret_cast<T*>(st + f * L::FIELD_B);
-        box[(R + tr) * L::W + L::CW + tc] = zero ? from_c<T>(C_t<T>(0)) : in[f][gi];
+      for (int k = 0; k < K; ++k) {
+        const int c = c0 + k * 32 + lane;
+        int tr, tc;
+        if (c < na) {
+          const int j = c % (2 * R);
+          tr = b0 + c / (2 * R);
+          tc = j < R ? j - R : t.nvx + j - R;
+        } else {
+          const int d = c - na, hr = d / wr;
+          tr = hr < nlo ? r0 + hr : t.nvy + hr - nlo;
+          tc = d % wr - R;
+        }
+        const int gy = t.y0 + tr, gx = t.x0 + tc;
+        const bool oy = gy < 0 || gy >= ny, ox = gx < 0 || gx >= nx;
+        const bool need = c < n && (oy || ox) && (!oy || per_y) && (!ox || per_x);
+        si[k] = need ? (R + tr) * L::W + L::CW + tc : -1;
+        gi[k] = need ? int64_t(oy ? wrap(gy, ny) : gy) * nx + (ox ? wrap(gx, nx) : gx) : 0;
       }
+      T v[K][NF];
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          if (si[k] >= 0) v[k][f] = in[f][gi[k]];
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          if (si[k] >= 0) reinterpret_cast<T*>(st + f * L::FIELD_B)[si[k]] = v[k][f];
     }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
