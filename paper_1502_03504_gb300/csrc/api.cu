@@ -197,7 +197,19 @@ Choice default_choice(const Geom& g, const StencilDesc& s, int* err) {
     a.ksteps = 1;
   }
   if (tma_supported(a)) return {kPathTma, 0, 0, 1};
-  if (g.ndim == 2) return {kPathTrap, 64, 32, 1};
+  if (g.ndim == 2) {
+    // Rows whose pitch is not a multiple of 16 bytes cannot be TMA-staged.
+    // Trapezoid tiles fusing 4 sweeps measured 2.4x faster than one sweep per
+    // launch (FP32, 20 steps): jacobi5 7094^2 2.01 ms on 128 x 32 tiles
+    // against 4.85 ms on 64 x 32 tiles with k = 1; the three-field swe_flux
+    // 6.6 ms on 64 x 16 tiles against 14.8 ms (and 18.3 ms on 128 x 32 tiles,
+    // whose shared memory leaves one block per SM).
+    a.tile_x = g.nf == 1 ? 128 : 64;
+    a.tile_y = g.nf == 1 ? 32 : 16;
+    a.ksteps = 4;
+    if (s.stages == 1 && trap2d_supported(a)) return {kPathTrap, a.tile_x, a.tile_y, 4};
+    return {kPathTrap, 64, 32, 1};
+  }
   return {kPathDirect, 0, 0, 1};
 }
 

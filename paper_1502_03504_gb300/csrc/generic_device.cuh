@@ -45,47 +45,92 @@ __global__ void __launch_bounds__(256) trap2d_rk_kernel(Op op, TrapGrid g, const
 }
 
 // ------------------------------------------------------------------ direct
+// Taps of one output point.  A point whose whole halo box lies inside the
+// grid reads at constant offsets from its own index; any other point applies
+// the boundary rule per axis (a Dirichlet side gives its value; a periodic
+// side wraps by one period, since the radius never exceeds a periodic extent).
 template <class T, int NF>
 struct GlobalAcc {
   using C = C_t<T>;
   const T* const* f;
-  Geom g;
-  int64_t z, y, x;
+  const Geom* g;
+  int64_t p, plane;
+  int z, y, x, nx;
+  bool inside;
   __device__ __forceinline__ C operator()(int fi, int dx, int dy, int dz) const {
-    int64_t q[3] = {z + dz, y + dy, x + dx};
+    if (inside) return to_c(__ldg(f[fi] + p + dz * plane + int64_t(dy) * nx + dx));
+    int q[3] = {z + dz, y + dy, x + dx};
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-      if (q[ax] < 0 && g.bc[ax][0] == kDirichlet) return C(g.bval[ax][0]);
-      if (q[ax] >= g.n[ax] && g.bc[ax][1] == kDirichlet) return C(g.bval[ax][1]);
+      const int n = int(g->n[ax]);
+      if (q[ax] < 0) {
+        if (g->bc[ax][0] == kDirichlet) return C(g->bval[ax][0]);
+        q[ax] += n;
+      } else if (q[ax] >= n) {
+        if (g->bc[ax][1] == kDirichlet) return C(g->bval[ax][1]);
+        q[ax] -= n;
+      }
     }
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-      const int64_t m = g.n[ax];
-      q[ax] = q[ax] < 0 ? q[ax] + m * ((-q[ax] + m - 1) / m) : q[ax] % m;
-    }
-    return to_c(__ldg(f[fi] + (q[0] * g.n[1] + q[1]) * g.n[2] + q[2]));
+    return to_c(__ldg(f[fi] + (int64_t(q[0]) * g->n[1] + q[1]) * nx + q[2]));
   }
-  __device__ __forceinline__ int64_t gidx() const { return (z * g.n[1] + y) * g.n[2] + x; }
+  __device__ __forceinline__ int64_t gidx() const { return p; }
 };
 
+// The grid is cut into units of 256 consecutive points of one row (the last
+// unit of a row may be short); block b takes a contiguous range of units and
+// thread t the point t of each, so loads and stores are coalesced along x and
+// the row and plane of each unit follow by counting, without a division per
+// point.  (Evaluating four units per thread before storing, to keep more
+// loads in flight, measured slower: 5.5 ms against 4.3 ms for 20 sweeps of a
+// 7094^2 FP32 grid.)
 template <class Op, class T>
-__global__ void __launch_bounds__(256) direct_kernel(Op op, Geom g, const T* in0, const T* in1,
-                                                     const T* in2, T* out0, T* out1, T* out2,
-                                                     double* partials) {
+__global__ void __launch_bounds__(256) direct_kernel(Op op, const __grid_constant__ Geom g,
+                                                     const T* in0, const T* in1, const T* in2,
+                                                     T* out0, T* out1, T* out2, double* partials) {
   using C = C_t<T>;
+  constexpr int R = Op::R;
   const T* src[3] = {in0, in1, in2};
   T* dst[3] = {out0, out1, out2};
-  const int64_t n = g.n[0] * g.n[1] * g.n[2];
+  const int nz = int(g.n[0]), ny = int(g.n[1]), nx = int(g.n[2]);
+  const int chunks = (nx + 255) / 256;
+  const int64_t units = int64_t(nz) * ny * chunks;
+  const int64_t per = (units + gridDim.x - 1) / gridDim.x;
+  int64_t u = int64_t(blockIdx.x) * per;
+  const int64_t u1 = u + per < units ? u + per : units;
   double red = 0.0;
-  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n;
-       p += int64_t(gridDim.x) * blockDim.x) {
-    GlobalAcc<T, Op::NF> acc{src, g, p / (g.n[1] * g.n[2]), (p / g.n[2]) % g.n[1], p % g.n[2]};
-    C o[Op::NF];
-    C r1 = C(0);
-    op(acc, o, r1);
-    red += double(r1);
+  if (u < u1) {
+    const int64_t row = u / chunks;
+    int c = int(u - row * chunks);
+    int z = int(row / ny), y = int(row - int64_t(z) * ny);
+    GlobalAcc<T, Op::NF> acc;
+    acc.f = src;
+    acc.g = &g;
+    acc.plane = int64_t(nx) * ny;
+    acc.nx = nx;
+    for (; u < u1; ++u) {
+      const int x = c * 256 + int(threadIdx.x);
+      if (x < nx) {
+        acc.z = z;
+        acc.y = y;
+        acc.x = x;
+        acc.p = (int64_t(z) * ny + y) * nx + x;
+        acc.inside = x >= R && x + R < nx && y >= R && y + R < ny &&
+                     (g.ndim == 2 || (z >= R && z + R < nz));
+        C o[Op::NF];
+        C r1 = C(0);
+        op(acc, o, r1);
+        red += double(r1);
 #pragma unroll
-    for (int f = 0; f < Op::NF; ++f) dst[f][p] = from_c<T>(o[f]);
+        for (int f = 0; f < Op::NF; ++f) dst[f][acc.p] = from_c<T>(o[f]);
+      }
+      if (++c == chunks) {
+        c = 0;
+        if (++y == ny) {
+          y = 0;
+          ++z;
+        }
+      }
+    }
   }
   if (Op::REDUCES) {
     __shared__ double ws[8];

@@ -82,9 +82,11 @@ cudaError_t run_trap(const StepArgs& a, const Op& op) {
   return cudaGetLastError();
 }
 
+// Blocks of the direct kernel: one per unit of 256 points of a row, at most
+// eight per SM.
 int direct_grid(const Geom& g) {
-  const int64_t n = g.n[0] * g.n[1] * g.n[2];
-  return int(std::min<int64_t>((n + 255) / 256, 152 * 8));
+  const int64_t units = g.n[0] * g.n[1] * ((g.n[2] + 255) / 256);
+  return int(std::min<int64_t>(units, 152 * 8));
 }
 
 template <class Op, class T>
