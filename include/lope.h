@@ -182,10 +182,18 @@ lope_status lope_apply_host(const lope_grid* grid, const lope_stencil* stencil,
                             int64_t nsteps, void* cuda_stream);
 
 /* Launch choices, for tests and tuning.  Zero fields mean "planner decides".
- *   path:    0 auto, 1 TMA tiles (2D tiles, any stencil / 3D z-march, star
- *            stencils; 16-byte row pitch), 2 shared-memory trapezoid tiles with temporal blocking
- *            (2D, any stencil, any shape), 3 direct (any stencil, one thread per
- *            point).
+ *   path:    0 auto;
+ *            1 TMA tiles (2D tiles, any stencil / 3D z-march, star stencils;
+ *              16-byte row pitch);
+ *            2 shared-memory trapezoid tiles with temporal blocking (2D, any
+ *              stencil, any shape);
+ *            3 direct (any stencil, one thread per point);
+ *            4 column march (3D, any stencil and row pitch; not for the
+ *              adjoint or source stencils): each thread keeps its column in
+ *              registers along z.  The planner takes it for 3D grids whose
+ *              row pitch is not a multiple of 16 bytes.
+ *            Trapezoid tiles fusing 4 sweeps (128 x 32 for one field, 64 x 16
+ *            for several) are the planner's choice for such 2D grids.
  *   tile_x, tile_y: tile shape for path 2 (tile_x in {32,64,128}, tile_y in
  *            {8,16,32}); for path 1, tile_y = 1 or 2 forces the short or the
  *            tall tiles (0: tall from 2^22 points in 2D, 2^26 in 3D).

@@ -34,7 +34,8 @@ class LopeError(RuntimeError):
 
 
 class Launch(ctypes.Structure):
-    """lope_launch: path (0 auto, 1 TMA, 2 trapezoid, 3 direct), tile, depth, graph."""
+    """lope_launch: path (0 auto, 1 TMA, 2 trapezoid, 3 direct, 4 column march), tile,
+    depth, graph."""
 
     _fields_ = [("path", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("tsteps", ctypes.c_int), ("graph", ctypes.c_int)]

@@ -210,6 +210,10 @@ Choice default_choice(const Geom& g, const StencilDesc& s, int* err) {
     if (s.stages == 1 && trap2d_supported(a)) return {kPathTrap, a.tile_x, a.tile_y, 4};
     return {kPathTrap, 64, 32, 1};
   }
+  // 3D rows that cannot be TMA-staged: the column march, else the direct
+  // kernel (adjoint and run-time compiled functions).
+  a.ksteps = 1;
+  if (march_supported(a)) return {kPathMarch, 0, 0, 1};
   return {kPathDirect, 0, 0, 1};
 }
 
@@ -240,6 +244,7 @@ lope_status resolve(const Geom& g, const StencilDesc& s, const void* const* in,
     case kPathTma: ok = tma_supported(a); break;
     case kPathTrap: ok = trap2d_supported(a); break;
     case kPathDirect: ok = direct_supported(a); break;
+    case kPathMarch: ok = march_supported(a); break;
     default: ok = false;
   }
   if (ok && s.stages >= 2 && d.path != kPathTrap && a.ksteps != 1) ok = false;
@@ -272,7 +277,7 @@ void log_plan(const Geom& g, const StencilDesc& s, const Choice& c, int64_t nste
   static const char* kinds[] = {"linear", "jacobi5", "diff7", "star9r2", "swe_cgrid", "swe_flux",
                                 "source"};
   static const char* dtypes[] = {"f64", "f32", "bf16"};
-  static const char* paths[] = {"auto", "tma", "trapezoid", "direct"};
+  static const char* paths[] = {"auto", "tma", "trapezoid", "direct", "march"};
   static const char* bcs[] = {"periodic", "dirichlet"};
   std::vector<int64_t> key{g.ndim, g.n[0], g.n[1], g.n[2], g.dtype, g.nf, s.kind, s.radius,
                            s.stages, c.path, c.tile_x, c.tile_y, c.k, nsteps, graph};
@@ -334,6 +339,7 @@ cudaError_t issue_stages(const Geom& g, const StencilDesc& s, const Choice& c,
       }
       cudaError_t e;
       if (c.path == kPathTma) e = stage == 1 ? launch_tma(a, nullptr) : launch_tma_stage(a);
+      else if (c.path == kPathMarch) e = launch_march(a);
       else e = launch_direct(a, nullptr);
       if (e != cudaSuccess) return e;
     }
@@ -364,6 +370,7 @@ cudaError_t issue(const Geom& g, const StencilDesc& s, const Choice& c, const vo
     switch (c.path) {
       case kPathTma: e = launch_tma(a, nullptr); break;
       case kPathTrap: e = launch_trap2d(a); break;
+      case kPathMarch: e = launch_march(a); break;
       default: e = launch_direct(a, nullptr); break;
     }
     if (e != cudaSuccess) return e;
@@ -948,6 +955,7 @@ lope_status lope_autotune(const lope_grid* grid, const lope_stencil* stencil,
     for (auto& t : tiles)
       for (int k : {1, 2, 3, 4, 6, 8}) cands.push_back({kPathTrap, t[0], t[1], k, -1});
   }
+  if (g.ndim == 3) cands.push_back({kPathMarch, 0, 0, 1, -1});
   cands.push_back({kPathDirect, 0, 0, 1, -1});
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);

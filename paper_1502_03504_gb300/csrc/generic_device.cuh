@@ -6,7 +6,9 @@
 //  * direct_kernel — one thread per output point reading its halo straight
 //    from global memory through the boundary rule (2D and 3D).  This is the
 //    plainest GPU form of "call the local function for each interior index"
-//    (Sec. 2.2, Sec. 3.2) and serves shapes the TMA path cannot take.
+//    (Sec. 2.2, Sec. 3.2) and serves shapes the TMA path cannot take;
+//  * march3d_plain_kernel — 3D columns marched along z with the column in
+//    registers, for grids the TMA tiles cannot stage.
 #pragma once
 
 #include "trap.cuh"
@@ -141,6 +143,131 @@ __global__ void __launch_bounds__(256) direct_kernel(Op op, const __grid_constan
       double s = 0.0;
       for (int w = 0; w < int(blockDim.x / 32); ++w) s += ws[w];
       partials[blockIdx.x] += s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ column march
+// 3D sweeps for grids the TMA tiles cannot stage (a row pitch that is not a
+// multiple of 16 bytes).  A 256-thread block owns a kMarchX x kMarchY tile of
+// (x, y) columns and marches a chunk of planes [z0, z1).  Each thread keeps
+// its column's values of planes z-R .. z+R in registers and loads the planes
+// ahead of z PF steps early, so PF loads per field are in flight.  Taps off
+// the column read the state at plane z+dz through the cache (the block's own
+// columns, loaded one to R steps earlier, mostly hit L1); their addresses are
+// sums of per-thread row offsets and per-step plane offsets held in
+// registers.  The boundary rule is applied per axis from per-thread indexes:
+// a wrapped index on a periodic axis, or a Dirichlet side (z checked first,
+// then y, then x, as in the direct kernel), so every tap has the value the
+// direct kernel reads.
+constexpr int kMarchX = 32, kMarchY = 8;
+
+template <class T, int NF, int R>
+struct MarchAcc {
+  using C = C_t<T>;
+  const C (*q)[2 * R + 1];  // q[f][dz + R]: the column at plane z + dz
+  const T* const* f;
+  const Geom* g;
+  const int* xi;  // wrapped x index per dx + R, or -1 / -2 past the low / high Dirichlet side
+  const int* yi;
+  const int* zi;
+  const int64_t* yrow;  // yi * nx per dy + R
+  const int64_t* zpl;   // zi * plane per dz + R (this step)
+  int64_t p;
+  __device__ __forceinline__ C side(int ax, int code) const {
+    return C(g->bval[ax][code == -1 ? 0 : 1]);
+  }
+  __device__ __forceinline__ C operator()(int fi, int dx, int dy, int dz) const {
+    if (dx == 0 && dy == 0) return q[fi][dz + R];
+    const int zz = zi[dz + R], yy = yi[dy + R], xx = xi[dx + R];
+    if (zz < 0) return side(0, zz);
+    if (yy < 0) return side(1, yy);
+    if (xx < 0) return side(2, xx);
+    return to_c(__ldg(f[fi] + zpl[dz + R] + yrow[dy + R] + xx));
+  }
+  __device__ __forceinline__ int64_t gidx() const { return p; }
+};
+
+// Index of coordinate v on an axis of extent n: itself when inside, wrapped on
+// a periodic side, or -1 / -2 past a low / high Dirichlet side.
+__device__ __forceinline__ int axis_index(int v, int n, int bc_lo, int bc_hi) {
+  if (v < 0) return bc_lo == kDirichlet ? -1 : v + n;
+  if (v >= n) return bc_hi == kDirichlet ? -2 : v - n;
+  return v;
+}
+
+template <class Op, class T>
+__global__ void __launch_bounds__(256) march3d_plain_kernel(Op op, const __grid_constant__ Geom g,
+                                                            const T* in0, const T* in1,
+                                                            const T* in2, T* out0, T* out1,
+                                                            T* out2, int zchunk) {
+  using C = C_t<T>;
+  constexpr int R = Op::R, NF = Op::NF, NQ = 2 * R + 1, PF = 4;
+  const T* src[3] = {in0, in1, in2};
+  T* dst[3] = {out0, out1, out2};
+  const int nz = int(g.n[0]), ny = int(g.n[1]), nx = int(g.n[2]);
+  const int tiles_x = (nx + kMarchX - 1) / kMarchX, tiles_y = (ny + kMarchY - 1) / kMarchY;
+  const int tile = int(blockIdx.x % unsigned(tiles_x * tiles_y));
+  const int chunk = int(blockIdx.x / unsigned(tiles_x * tiles_y));
+  const int x = (tile % tiles_x) * kMarchX + int(threadIdx.x % kMarchX);
+  const int y = (tile / tiles_x) * kMarchY + int(threadIdx.x / kMarchX);
+  const int z0 = chunk * zchunk, z1 = min(nz, z0 + zchunk);
+  if (x >= nx || y >= ny || z0 >= z1) return;
+  const int64_t plane = int64_t(nx) * ny, col = int64_t(y) * nx + x;
+  int xi[NQ], yi[NQ], zi[NQ];
+  int64_t yrow[NQ], zpl[NQ];
+#pragma unroll
+  for (int d = 0; d < NQ; ++d) {
+    xi[d] = axis_index(x + d - R, nx, g.bc[2][0], g.bc[2][1]);
+    yi[d] = axis_index(y + d - R, ny, g.bc[1][0], g.bc[1][1]);
+    yrow[d] = int64_t(yi[d]) * nx;
+  }
+  // The column's value at plane v (any v within R + PF of the chunk).
+  auto column = [&](int f, int v) -> C {
+    const int zz = axis_index(v, nz, g.bc[0][0], g.bc[0][1]);
+    if (zz < 0) return C(g.bval[0][zz == -1 ? 0 : 1]);
+    return to_c(__ldg(src[f] + zz * plane + col));
+  };
+  C q[NF][NQ], pend[NF][PF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+#pragma unroll
+    for (int k = 0; k < NQ - 1; ++k) q[f][k] = column(f, z0 - R + k);
+#pragma unroll
+    for (int j = 0; j < PF; ++j) pend[f][j] = z0 + R + j < z1 + R ? column(f, z0 + R + j) : C(0);
+  }
+  MarchAcc<T, NF, R> acc;
+  acc.q = q;
+  acc.f = src;
+  acc.g = &g;
+  acc.xi = xi;
+  acc.yi = yi;
+  acc.zi = zi;
+  acc.yrow = yrow;
+  acc.zpl = zpl;
+  for (int z = z0; z < z1; ++z) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      q[f][NQ - 1] = pend[f][0];
+#pragma unroll
+      for (int j = 0; j < PF - 1; ++j) pend[f][j] = pend[f][j + 1];
+      const int v = z + R + PF;
+      pend[f][PF - 1] = v < z1 + R ? column(f, v) : C(0);
+    }
+#pragma unroll
+    for (int d = 0; d < NQ; ++d) {
+      zi[d] = axis_index(z + d - R, nz, g.bc[0][0], g.bc[0][1]);
+      zpl[d] = zi[d] * plane;
+    }
+    acc.p = z * plane + col;
+    C o[NF];
+    C r1 = C(0);
+    op(acc, o, r1);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      dst[f][acc.p] = from_c<T>(o[f]);
+#pragma unroll
+      for (int k = 0; k < NQ - 1; ++k) q[f][k] = q[f][k + 1];
     }
   }
 }

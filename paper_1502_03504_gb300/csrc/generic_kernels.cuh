@@ -106,12 +106,44 @@ cudaError_t run_direct(const StepArgs& a, const Op& op, int* blocks_out) {
   return cudaGetLastError();
 }
 
-// RK = false: plain sweeps (trapezoid with temporal blocking, direct).  RK =
-// true: the multi-stage forms (fused trapezoid steps; a combining stage on the
-// direct kernel, out = a * base + b * E(in)).
+// Column march geometry: 32 x 8 column tiles; z cut into chunks of at least
+// 16 planes so that about two waves of 256-thread blocks (eight per SM) are
+// in flight (each chunk stages 2R extra planes).
+inline bool march_geometry(const Geom& g, int* blocks, int* zchunk) {
+  const int64_t tiles = ((g.n[2] + kMarchX - 1) / kMarchX) * ((g.n[1] + kMarchY - 1) / kMarchY);
+  const int64_t slots = 2 * 8 * 152;
+  int64_t nzc = std::max<int64_t>(1, std::min<int64_t>(g.n[0] / 16, (slots + tiles - 1) / tiles));
+  const int64_t zc = (g.n[0] + nzc - 1) / nzc;
+  nzc = (g.n[0] + zc - 1) / zc;
+  if (tiles * nzc > int64_t(0x7fffffff)) return false;
+  *blocks = int(tiles * nzc);
+  *zchunk = int(zc);
+  return true;
+}
+
+template <class Op, class T>
+cudaError_t run_march(const StepArgs& a, const Op& op) {
+  int blocks = 0, zchunk = 0;
+  if (!march_geometry(a.g, &blocks, &zchunk)) return cudaErrorInvalidConfiguration;
+  const T* in[3] = {nullptr, nullptr, nullptr};
+  T* out[3] = {nullptr, nullptr, nullptr};
+  for (int f = 0; f < Op::NF; ++f) {
+    in[f] = static_cast<const T*>(a.in[f]);
+    out[f] = static_cast<T*>(a.out[f]);
+  }
+  march3d_plain_kernel<Op, T><<<blocks, 256, 0, a.stream>>>(op, a.g, in[0], in[1], in[2], out[0],
+                                                             out[1], out[2], zchunk);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// RK = false: plain sweeps (trapezoid with temporal blocking, direct, column
+// march).  RK = true: the multi-stage forms (fused trapezoid steps; a
+// combining stage, out = a * base + b * E(in), on the direct kernel or the
+// column march).
 template <bool RK, class Op, class T>
-cudaError_t run_any(const StepArgs& a, const Op& op, bool trap, int* blocks) {
-  if (trap) {
+cudaError_t run_any(const StepArgs& a, const Op& op, int kind, int* blocks) {
+  if (kind == kGenTrap) {
     if constexpr (Op::NDIM == 2 && !Op::REDUCES) {
       if constexpr (RK) return run_trap_rk<Op, T>(a, op);
       else return run_trap<Op, T>(a, op);
@@ -125,10 +157,18 @@ cudaError_t run_any(const StepArgs& a, const Op& op, bool trap, int* blocks) {
       st.a = a.rk_a;
       st.b = a.rk_b;
       for (int f = 0; f < kMaxFields; ++f) st.base[f] = static_cast<const T*>(a.base[f]);
+      if (kind == kGenMarch) {
+        if constexpr (Op::NDIM == 3) return run_march<OpStage<Op, T>, T>(a, st);
+        return cudaErrorNotSupported;
+      }
       return run_direct<OpStage<Op, T>, T>(a, st, blocks);
     }
     return cudaErrorNotSupported;
   } else {
+    if (kind == kGenMarch) {
+      if constexpr (Op::NDIM == 3 && !Op::REDUCES) return run_march<Op, T>(a, op);
+      return cudaErrorNotSupported;
+    }
     return run_direct<Op, T>(a, op, blocks);
   }
 }
@@ -145,44 +185,44 @@ template <int ND, int RR> OpBoxLinear<ND, RR> box_op(const StencilDesc& s) {
   return op;
 }
 
-template <bool RK, class T> cudaError_t dispatch_t(const StepArgs& a, bool trap, int* blocks) {
+template <bool RK, class T> cudaError_t dispatch_t(const StepArgs& a, int kind, int* blocks) {
   const StencilDesc& s = a.s;
   if (!RK && a.adjoint) {
     switch (s.kind) {
-      case kJacobi5: return run_any<RK, OpAdjDiffusion<kJacobi5, T>, T>(a, {s.prm[0], (const T*)a.ut}, trap, blocks);
-      case kStar9r2: return run_any<RK, OpAdjDiffusion<kStar9r2, T>, T>(a, {s.prm[0], (const T*)a.ut}, trap, blocks);
-      case kDiff7: return run_any<RK, OpAdjDiffusion<kDiff7, T>, T>(a, {s.prm[0], (const T*)a.ut}, trap, blocks);
+      case kJacobi5: return run_any<RK, OpAdjDiffusion<kJacobi5, T>, T>(a, {s.prm[0], (const T*)a.ut}, kind, blocks);
+      case kStar9r2: return run_any<RK, OpAdjDiffusion<kStar9r2, T>, T>(a, {s.prm[0], (const T*)a.ut}, kind, blocks);
+      case kDiff7: return run_any<RK, OpAdjDiffusion<kDiff7, T>, T>(a, {s.prm[0], (const T*)a.ut}, kind, blocks);
       default: break;
     }
   }
   switch (s.kind) {
-    case kJacobi5: return run_any<RK, OpJacobi5, T>(a, {s.prm[0]}, trap, blocks);
-    case kStar9r2: return run_any<RK, OpStar9r2, T>(a, {s.prm[0]}, trap, blocks);
-    case kDiff7: return run_any<RK, OpDiff7, T>(a, {s.prm[0]}, trap, blocks);
-    case kSwe: return run_any<RK, OpSwe, T>(a, {-s.prm[0] * s.prm[2], -s.prm[0] * s.prm[1]}, trap, blocks);
-    case kSweFlux: return run_any<RK, OpSweFlux, T>(a, OpSweFlux::make(s.prm), trap, blocks);
+    case kJacobi5: return run_any<RK, OpJacobi5, T>(a, {s.prm[0]}, kind, blocks);
+    case kStar9r2: return run_any<RK, OpStar9r2, T>(a, {s.prm[0]}, kind, blocks);
+    case kDiff7: return run_any<RK, OpDiff7, T>(a, {s.prm[0]}, kind, blocks);
+    case kSwe: return run_any<RK, OpSwe, T>(a, {-s.prm[0] * s.prm[2], -s.prm[0] * s.prm[1]}, kind, blocks);
+    case kSweFlux: return run_any<RK, OpSweFlux, T>(a, OpSweFlux::make(s.prm), kind, blocks);
     case kLinear:
       if (s.star) {
-        if (s.ndim == 2 && s.radius == 1) return run_any<RK, OpStarLinear<2, 1>, T>(a, star_op<2, 1>(s), trap, blocks);
-        if (s.ndim == 2 && s.radius == 2) return run_any<RK, OpStarLinear<2, 2>, T>(a, star_op<2, 2>(s), trap, blocks);
-        if (s.ndim == 3 && s.radius == 1) return run_any<RK, OpStarLinear<3, 1>, T>(a, star_op<3, 1>(s), trap, blocks);
-        if (s.ndim == 3 && s.radius == 2) return run_any<RK, OpStarLinear<3, 2>, T>(a, star_op<3, 2>(s), trap, blocks);
+        if (s.ndim == 2 && s.radius == 1) return run_any<RK, OpStarLinear<2, 1>, T>(a, star_op<2, 1>(s), kind, blocks);
+        if (s.ndim == 2 && s.radius == 2) return run_any<RK, OpStarLinear<2, 2>, T>(a, star_op<2, 2>(s), kind, blocks);
+        if (s.ndim == 3 && s.radius == 1) return run_any<RK, OpStarLinear<3, 1>, T>(a, star_op<3, 1>(s), kind, blocks);
+        if (s.ndim == 3 && s.radius == 2) return run_any<RK, OpStarLinear<3, 2>, T>(a, star_op<3, 2>(s), kind, blocks);
       } else {
-        if (s.ndim == 2 && s.radius == 1) return run_any<RK, OpBoxLinear<2, 1>, T>(a, box_op<2, 1>(s), trap, blocks);
-        if (s.ndim == 2 && s.radius == 2) return run_any<RK, OpBoxLinear<2, 2>, T>(a, box_op<2, 2>(s), trap, blocks);
-        if (s.ndim == 3 && s.radius == 1) return run_any<RK, OpBoxLinear<3, 1>, T>(a, box_op<3, 1>(s), trap, blocks);
-        if (s.ndim == 3 && s.radius == 2) return run_any<RK, OpBoxLinear<3, 2>, T>(a, box_op<3, 2>(s), trap, blocks);
+        if (s.ndim == 2 && s.radius == 1) return run_any<RK, OpBoxLinear<2, 1>, T>(a, box_op<2, 1>(s), kind, blocks);
+        if (s.ndim == 2 && s.radius == 2) return run_any<RK, OpBoxLinear<2, 2>, T>(a, box_op<2, 2>(s), kind, blocks);
+        if (s.ndim == 3 && s.radius == 1) return run_any<RK, OpBoxLinear<3, 1>, T>(a, box_op<3, 1>(s), kind, blocks);
+        if (s.ndim == 3 && s.radius == 2) return run_any<RK, OpBoxLinear<3, 2>, T>(a, box_op<3, 2>(s), kind, blocks);
       }
       return cudaErrorNotSupported;
     default: return cudaErrorNotSupported;
   }
 }
 
-template <bool RK> cudaError_t dispatch_generic(const StepArgs& a, bool trap, int* blocks) {
+template <bool RK> cudaError_t dispatch_generic(const StepArgs& a, int kind, int* blocks) {
   switch (a.g.dtype) {
-    case kF32: return dispatch_t<RK, float>(a, trap, blocks);
-    case kF64: return dispatch_t<RK, double>(a, trap, blocks);
-    case kBF16: return dispatch_t<RK, __nv_bfloat16>(a, trap, blocks);
+    case kF32: return dispatch_t<RK, float>(a, kind, blocks);
+    case kF64: return dispatch_t<RK, double>(a, kind, blocks);
+    case kBF16: return dispatch_t<RK, __nv_bfloat16>(a, kind, blocks);
     default: return cudaErrorNotSupported;
   }
 }

@@ -1,6 +1,6 @@
-// Plain sweeps on the generic kernels (trapezoid tiles, direct), their
-// support checks and shared-memory sizing; multi-stage forms are routed to
-// k_generic_rk.cu.
+// Plain sweeps on the generic kernels (trapezoid tiles, direct, column
+// march), their support checks and shared-memory sizing; multi-stage forms
+// are routed to k_generic_rk.cu.
 #include "generic_kernels.cuh"
 
 namespace lope {
@@ -22,18 +22,28 @@ bool trap2d_supported(const StepArgs& a) {
 
 bool direct_supported(const StepArgs& a) { return a.ksteps == 1; }
 
+bool march_supported(const StepArgs& a) {
+  int blocks = 0, zchunk = 0;
+  return a.g.ndim == 3 && !a.adjoint && a.s.kind != kUser && a.ksteps == 1 &&
+         march_geometry(a.g, &blocks, &zchunk);
+}
+
 cudaError_t launch_trap2d(const StepArgs& a) {
   if (a.s.kind == kUser) return jit_launch(a, kPathTrap);
-  if (a.s.stages >= 2) return launch_generic_rk(a, true, nullptr);
-  return dispatch_generic<false>(a, true, nullptr);
+  if (a.s.stages >= 2) return launch_generic_rk(a, kGenTrap, nullptr);
+  return dispatch_generic<false>(a, kGenTrap, nullptr);
 }
 cudaError_t launch_direct(const StepArgs& a, int* blocks) {
   if (a.s.kind == kUser) {
     if (blocks) *blocks = direct_grid(a.g);
     return jit_launch(a, kPathDirect);
   }
-  if (a.stage >= 2) return launch_generic_rk(a, false, blocks);
-  return dispatch_generic<false>(a, false, blocks);
+  if (a.stage >= 2) return launch_generic_rk(a, kGenDirect, blocks);
+  return dispatch_generic<false>(a, kGenDirect, blocks);
+}
+cudaError_t launch_march(const StepArgs& a) {
+  if (a.stage >= 2) return launch_generic_rk(a, kGenMarch, nullptr);
+  return dispatch_generic<false>(a, kGenMarch, nullptr);
 }
 int direct_blocks(const StepArgs& a) { return direct_grid(a.g); }
 

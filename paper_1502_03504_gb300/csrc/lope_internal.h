@@ -20,7 +20,7 @@ enum : int { kLinear = 0, kJacobi5 = 1, kDiff7 = 2, kStar9r2 = 3, kSwe = 4, kSwe
 constexpr int kUserParams = 8;  // parameters P[0..7] of a user-written local function
 enum : int { kF64 = 0, kF32 = 1, kBF16 = 2 };
 enum : int { kPeriodic = 0, kDirichlet = 1 };
-enum : int { kPathAuto = 0, kPathTma = 1, kPathTrap = 2, kPathDirect = 3 };
+enum : int { kPathAuto = 0, kPathTma = 1, kPathTrap = 2, kPathDirect = 3, kPathMarch = 4 };
 
 // Device error codes written to the error flag.
 constexpr int kErrTimeout = 1;
@@ -102,6 +102,10 @@ bool tma_supported(const StepArgs& a);
 cudaError_t launch_trap2d(const StepArgs& a);
 bool trap2d_supported(const StepArgs& a);
 cudaError_t launch_direct(const StepArgs& a, int* blocks);
+// 3D column march for grids the TMA tiles cannot stage (not for adjoint or
+// run-time compiled functions).
+cudaError_t launch_march(const StepArgs& a);
+bool march_supported(const StepArgs& a);
 // Run-time compiled local functions (jit.cu).
 struct JitProgram;
 lope_status jit_create(const char* body, int ndim, int radius, int nf, bool star,
@@ -115,8 +119,10 @@ bool jit_tma_ok(const JitProgram* jp);
 cudaError_t jit_launch(const StepArgs& a, int path);
 
 // Multi-stage forms on the generic kernels (k_generic_rk.cu): fused trapezoid
-// steps (trap) or a combining stage on the direct kernel.
-cudaError_t launch_generic_rk(const StepArgs& a, bool trap, int* blocks);
+// steps (kGenTrap), or a combining stage on the direct kernel (kGenDirect) or
+// the column march (kGenMarch).
+enum : int { kGenDirect = 0, kGenTrap = 1, kGenMarch = 2 };
+cudaError_t launch_generic_rk(const StepArgs& a, int kind, int* blocks);
 bool direct_supported(const StepArgs& a);
 int tma_blocks(const StepArgs& a);
 int direct_blocks(const StepArgs& a);

@@ -94,3 +94,41 @@ def test_direct_wide_and_narrow_rows(lope, orc):
         st = lope.Stencil.builtin(kind, 0.1)
         got = _run(lope, g, st, u, 4, lope.Launch(3, 0, 0, 0, -1))[0]
         assert normwise(to_host(got), orc.apply(us, kind, [0.1], 4, bc=[0] * len(shape))) <= 1e-12, shape
+
+
+MARCH, DIRECT = 4, 3
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f64"])
+@pytest.mark.parametrize("bc", [[0, 0, 0], [1, 1, 1], [0, 1, 0], [1, 0, 1]])
+def test_3d_march_equals_direct(lope, dtype, bc):
+    shape, T = (21, 19, 45), 5  # 45 points per row: no TMA staging for any storage type
+    u, _ = to_device(LI.uniform_field(1440, shape), dtype)
+    rng = np.random.default_rng(1441)
+    box = rng.uniform(-0.1, 0.1, (3, 3, 3))
+    star2 = np.zeros((5, 5, 5))
+    star2[2, 2, :] = star2[2, :, 2] = star2[:, 2, 2] = rng.uniform(-0.1, 0.1, 5)
+    for st, halo in ((lope.Stencil.builtin("diff7", 0.1), 1), (lope.Stencil.linear(box), 1),
+                     (lope.Stencil.linear(star2), 2), (lope.Stencil.builtin("diff7", 0.1).set_scheme("rk3"), 1)):
+        g = lope.Grid(shape, dtype, halo=halo)
+        bval = [0.0, 0.0, 0.0] if dtype == "bf16" else [(0.5, -0.3), -0.25, (1.0, 0.2)]
+        g.set_boundaries(bc, bval)
+        a = _run(lope, g, st, u, T, lope.Launch(MARCH, 0, 0, 0, -1))[0]
+        b = _run(lope, g, st, u, T, lope.Launch(DIRECT, 0, 0, 0, -1))[0]
+        assert torch.equal(a, b), (st.scheme, halo)
+
+
+def test_3d_march_is_the_default_for_odd_widths_and_matches_oracle(lope, orc, capfd):
+    shape, T = (33, 18, 27), 8
+    u, us = to_device(LI.uniform_field(1450, shape), "f64")
+    g = lope.Grid(shape, "f64", halo=1)
+    g.set_boundaries([1, 0, 1], [0.25, 0.0, -0.5])
+    st = lope.Stencil.builtin("diff7", 0.1)
+    lope.lope_set_option("log", 1)
+    try:
+        got = _run(lope, g, st, u, T)[0]
+    finally:
+        lope.lope_set_option("log", 0)
+    assert "path=march" in capfd.readouterr().err
+    want = orc.apply(us, "diff7", [0.1], T, bc=[1, 0, 1], bval=[0.25, 0.0, -0.5])
+    assert normwise(to_host(got), want) <= 1e-12
