@@ -188,12 +188,12 @@ lope_status lope_apply_host(const lope_grid* grid, const lope_stencil* stencil,
  *            2 shared-memory trapezoid tiles with temporal blocking (2D, any
  *              stencil, any shape);
  *            3 direct (any stencil, one thread per point);
- *            4 column march (3D, any stencil and row pitch; not for the
- *              adjoint or source stencils): each thread keeps its column in
- *              registers along z.
+ *            4 plane march (3D, any stencil and row pitch; not for the
+ *              adjoint or source stencils): 64 x 4 column tiles marched along
+ *              z through a shared-memory ring of planes.
  *            For grids whose row pitch is not a multiple of 16 bytes the
  *            planner takes trapezoid tiles fusing 4 sweeps in 2D (128 x 32
- *            for one field, 64 x 16 for several) and the direct kernel in 3D.
+ *            for one field, 64 x 16 for several) and the plane march in 3D.
  *   tile_x, tile_y: tile shape for path 2 (tile_x in {32,64,128}, tile_y in
  *            {8,16,32}); for path 1, tile_y = 1 or 2 forces the short or the
  *            tall tiles (0: tall from 2^22 points in 2D, 2^26 in 3D).

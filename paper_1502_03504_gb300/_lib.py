@@ -34,7 +34,7 @@ class LopeError(RuntimeError):
 
 
 class Launch(ctypes.Structure):
-    """lope_launch: path (0 auto, 1 TMA, 2 trapezoid, 3 direct, 4 column march), tile,
+    """lope_launch: path (0 auto, 1 TMA, 2 trapezoid, 3 direct, 4 plane march), tile,
     depth, graph."""
 
     _fields_ = [("path", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),

@@ -210,10 +210,11 @@ Choice default_choice(const Geom& g, const StencilDesc& s, int* err) {
     if (s.stages == 1 && trap2d_supported(a)) return {kPathTrap, a.tile_x, a.tile_y, 4};
     return {kPathTrap, 64, 32, 1};
   }
-  // 3D rows that cannot be TMA-staged: the direct kernel.  The column march
-  // (path 4) measured slower (diff7 FP32 130 x 500 x 510, 20 steps: 6.36 ms
-  // against 4.64 ms), limited by the texture pipe at five cached loads per
-  // point.
+  // 3D rows that cannot be TMA-staged: the plane march (diff7 FP32
+  // 130 x 500 x 510, 20 steps: 2.72 ms against 4.64 ms on the direct kernel),
+  // else the direct kernel (adjoint and run-time compiled functions).
+  a.ksteps = 1;
+  if (march_supported(a)) return {kPathMarch, 0, 0, 1};
   return {kPathDirect, 0, 0, 1};
 }
 

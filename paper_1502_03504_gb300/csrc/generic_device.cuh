@@ -7,8 +7,8 @@
 //    from global memory through the boundary rule (2D and 3D).  This is the
 //    plainest GPU form of "call the local function for each interior index"
 //    (Sec. 2.2, Sec. 3.2) and serves shapes the TMA path cannot take;
-//  * march3d_plain_kernel — 3D columns marched along z with the column in
-//    registers, for grids the TMA tiles cannot stage.
+//  * march3d_plain_kernel — 3D planes marched along z through a shared-memory
+//    ring, for grids the TMA tiles cannot stage.
 #pragma once
 
 #include "trap.cuh"
@@ -147,43 +147,31 @@ __global__ void __launch_bounds__(256) direct_kernel(Op op, const __grid_constan
   }
 }
 
-// ------------------------------------------------------------------ column march
+// ------------------------------------------------------------------ plane march
 // 3D sweeps for grids the TMA tiles cannot stage (a row pitch that is not a
 // multiple of 16 bytes).  A 256-thread block owns a kMarchX x kMarchY tile of
-// (x, y) columns and marches a chunk of planes [z0, z1).  Each thread keeps
-// its column's values of planes z-R .. z+R in registers and loads the planes
-// ahead of z PF steps early, so PF loads per field are in flight.  Taps off
-// the column read the state at plane z+dz through the cache (the block's own
-// columns, loaded one to R steps earlier, mostly hit L1); their addresses are
-// sums of per-thread row offsets and per-step plane offsets held in
-// registers.  The boundary rule is applied per axis from per-thread indexes:
-// a wrapped index on a periodic axis, or a Dirichlet side (z checked first,
-// then y, then x, as in the direct kernel), so every tap has the value the
-// direct kernel reads.
-constexpr int kMarchX = 32, kMarchY = 8;
+// (x, y) columns (one output per thread and plane) and marches a chunk of
+// planes [z0, z1).  Each plane's (kMarchX + 2R) x (kMarchY + 2R) window, halo
+// included, is staged in shared memory in compute precision, with the boundary
+// rule already applied: a wrapped position on a periodic side, or the side's
+// value past a Dirichlet side (z checked first, then y, then x, as in the
+// direct kernel), so every tap reads the value the direct kernel reads.  A
+// ring of 2R + 2 planes holds z-R .. z+R and the plane being written.  The
+// loads of planes z+R+1 .. z+R+PF are kept in registers, issued PF steps
+// before their plane enters the ring, so they are in flight while earlier
+// planes compute.
+constexpr int kMarchX = 64, kMarchY = 4;
 
-template <class T, int NF, int R>
-struct MarchAcc {
-  using C = C_t<T>;
-  const C (*q)[2 * R + 1];  // q[f][dz + R]: the column at plane z + dz
-  const T* const* f;
-  const Geom* g;
-  const int* xi;  // wrapped x index per dx + R, or -1 / -2 past the low / high Dirichlet side
-  const int* yi;
-  const int* zi;
-  const int64_t* yrow;  // yi * nx per dy + R
-  const int64_t* zpl;   // zi * plane per dz + R (this step)
+template <class C, int NF, int W, int H, int NS, int R>
+struct PlaneAcc {
+  const C* ring;  // NS planes x NF fields x H x W
+  int slot0;      // ring slot of plane z - R
+  int o;          // window offset of this thread's output cell
   int64_t p;
-  __device__ __forceinline__ C side(int ax, int code) const {
-    return C(g->bval[ax][code == -1 ? 0 : 1]);
-  }
-  __device__ __forceinline__ C operator()(int fi, int dx, int dy, int dz) const {
-    if (dx == 0 && dy == 0) return q[fi][dz + R];
-    const int zz = zi[dz + R], yy = yi[dy + R], xx = xi[dx + R];
-    if (zz < 0) return side(0, zz);
-    if (yy < 0) return side(1, yy);
-    if (xx < 0) return side(2, xx);
-    return to_c(__ldg(f[fi] + zpl[dz + R] + yrow[dy + R] + xx));
+  __device__ __forceinline__ C operator()(int f, int dx, int dy, int dz) const {
+    int sl = slot0 + dz + R;
+    sl = sl >= NS ? sl - NS : sl;
+    return ring[(sl * NF + f) * (W * H) + o + dy * W + dx];
   }
   __device__ __forceinline__ int64_t gidx() const { return p; }
 };
@@ -202,72 +190,101 @@ __global__ void __launch_bounds__(256) march3d_plain_kernel(Op op, const __grid_
                                                             const T* in2, T* out0, T* out1,
                                                             T* out2, int zchunk) {
   using C = C_t<T>;
-  constexpr int R = Op::R, NF = Op::NF, NQ = 2 * R + 1, PF = 4;
+  constexpr int R = Op::R, NF = Op::NF, W = kMarchX + 2 * R, H = kMarchY + 2 * R;
+  constexpr int NS = 2 * R + 2, CELLS = W * H, PER = (CELLS + 255) / 256, PF = 3;
+  static_assert(kMarchX * kMarchY == 256, "one output per thread and plane");
+  static_assert(sizeof(C) * NS * NF * CELLS <= 48 * 1024, "plane ring exceeds static shared memory");
+  __shared__ C ring[NS * NF * CELLS];
   const T* src[3] = {in0, in1, in2};
   T* dst[3] = {out0, out1, out2};
   const int nz = int(g.n[0]), ny = int(g.n[1]), nx = int(g.n[2]);
   const int tiles_x = (nx + kMarchX - 1) / kMarchX, tiles_y = (ny + kMarchY - 1) / kMarchY;
-  const int tile = int(blockIdx.x % unsigned(tiles_x * tiles_y));
-  const int chunk = int(blockIdx.x / unsigned(tiles_x * tiles_y));
-  const int x = (tile % tiles_x) * kMarchX + int(threadIdx.x % kMarchX);
-  const int y = (tile / tiles_x) * kMarchY + int(threadIdx.x / kMarchX);
+  const unsigned ntiles = unsigned(tiles_x) * unsigned(tiles_y);
+  const int tile = int(blockIdx.x % ntiles), chunk = int(blockIdx.x / ntiles);
+  const int x0 = (tile % tiles_x) * kMarchX, y0 = (tile / tiles_x) * kMarchY;
   const int z0 = chunk * zchunk, z1 = min(nz, z0 + zchunk);
-  if (x >= nx || y >= ny || z0 >= z1) return;
-  const int64_t plane = int64_t(nx) * ny, col = int64_t(y) * nx + x;
-  int xi[NQ], yi[NQ], zi[NQ];
-  int64_t yrow[NQ], zpl[NQ];
+  if (z0 >= z1) return;  // the whole block
+  const int64_t plane = int64_t(nx) * ny;
+  // This thread's window cells: the in-plane position of the source value, or
+  // which Dirichlet side gives it (1, 2: y low / high; 3, 4: x low / high),
+  // or -1 for a cell no output reads (past the tile's valid cells + R).
+  const int xend = min(x0 + kMarchX, nx) + R, yend = min(y0 + kMarchY, ny) + R;
+  int64_t cpos[PER];
+  int ccode[PER];
 #pragma unroll
-  for (int d = 0; d < NQ; ++d) {
-    xi[d] = axis_index(x + d - R, nx, g.bc[2][0], g.bc[2][1]);
-    yi[d] = axis_index(y + d - R, ny, g.bc[1][0], g.bc[1][1]);
-    yrow[d] = int64_t(yi[d]) * nx;
+  for (int j = 0; j < PER; ++j) {
+    const int e = int(threadIdx.x) + 256 * j;
+    const int gy = y0 - R + e / W, gx = x0 - R + e % W;
+    cpos[j] = 0;
+    if (e >= CELLS || gx >= xend || gy >= yend) {
+      ccode[j] = -1;
+      continue;
+    }
+    const int yy = axis_index(gy, ny, g.bc[1][0], g.bc[1][1]);
+    const int xx = axis_index(gx, nx, g.bc[2][0], g.bc[2][1]);
+    if (yy < 0) ccode[j] = yy == -1 ? 1 : 2;
+    else if (xx < 0) ccode[j] = xx == -1 ? 3 : 4;
+    else {
+      ccode[j] = 0;
+      cpos[j] = int64_t(yy) * nx + xx;
+    }
   }
-  // The column's value at plane v (any v within R + PF of the chunk).
-  auto column = [&](int f, int v) -> C {
+  auto load_plane = [&](int v, C (&val)[NF][PER]) {
     const int zz = axis_index(v, nz, g.bc[0][0], g.bc[0][1]);
-    if (zz < 0) return C(g.bval[0][zz == -1 ? 0 : 1]);
-    return to_c(__ldg(src[f] + zz * plane + col));
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        const int c = ccode[j];
+        if (zz < 0) val[f][j] = C(g.bval[0][zz == -1 ? 0 : 1]);
+        else if (c == 0) val[f][j] = to_c(__ldg(src[f] + zz * plane + cpos[j]));
+        else if (c > 0) val[f][j] = C(g.bval[(c + 1) / 2][(c + 1) % 2]);
+        else val[f][j] = C(0);
+      }
   };
-  C q[NF][NQ], pend[NF][PF];
+  auto slot = [&](int v) { return (v - z0 + R) % NS; };
+  auto store_plane = [&](int v, const C (&val)[NF][PER]) {
+    C* base = ring + slot(v) * NF * CELLS;
 #pragma unroll
-  for (int f = 0; f < NF; ++f) {
+    for (int f = 0; f < NF; ++f)
 #pragma unroll
-    for (int k = 0; k < NQ - 1; ++k) q[f][k] = column(f, z0 - R + k);
-#pragma unroll
-    for (int j = 0; j < PF; ++j) pend[f][j] = z0 + R + j < z1 + R ? column(f, z0 + R + j) : C(0);
+      for (int j = 0; j < PER; ++j) {
+        const int e = int(threadIdx.x) + 256 * j;
+        if (e < CELLS) base[f * CELLS + e] = val[f][j];
+      }
+  };
+  C pend[PF][NF][PER];
+  for (int v = z0 - R; v < z0 + R; ++v) {
+    load_plane(v, pend[0]);
+    store_plane(v, pend[0]);
   }
-  MarchAcc<T, NF, R> acc;
-  acc.q = q;
-  acc.f = src;
-  acc.g = &g;
-  acc.xi = xi;
-  acc.yi = yi;
-  acc.zi = zi;
-  acc.yrow = yrow;
-  acc.zpl = zpl;
+#pragma unroll
+  for (int k = 0; k < PF; ++k)
+    if (z0 + k < z1) load_plane(z0 + R + k, pend[k]);
+  const int tx = int(threadIdx.x) % kMarchX, ty = int(threadIdx.x) / kMarchX;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool valid = x < nx && y < ny;
+  PlaneAcc<C, NF, W, H, NS, R> acc;
+  acc.ring = ring;
+  acc.o = (ty + R) * W + tx + R;
   for (int z = z0; z < z1; ++z) {
+    store_plane(z + R, pend[0]);
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      q[f][NQ - 1] = pend[f][0];
+    for (int k = 0; k < PF - 1; ++k)
 #pragma unroll
-      for (int j = 0; j < PF - 1; ++j) pend[f][j] = pend[f][j + 1];
-      const int v = z + R + PF;
-      pend[f][PF - 1] = v < z1 + R ? column(f, v) : C(0);
-    }
+      for (int f = 0; f < NF; ++f)
 #pragma unroll
-    for (int d = 0; d < NQ; ++d) {
-      zi[d] = axis_index(z + d - R, nz, g.bc[0][0], g.bc[0][1]);
-      zpl[d] = zi[d] * plane;
-    }
-    acc.p = z * plane + col;
-    C o[NF];
-    C r1 = C(0);
-    op(acc, o, r1);
+        for (int j = 0; j < PER; ++j) pend[k][f][j] = pend[k + 1][f][j];
+    if (z + PF < z1) load_plane(z + R + PF, pend[PF - 1]);
+    __syncthreads();
+    if (valid) {
+      acc.slot0 = slot(z - R);
+      acc.p = (int64_t(z) * ny + y) * nx + x;
+      C o[NF];
+      C r1 = C(0);
+      op(acc, o, r1);
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      dst[f][acc.p] = from_c<T>(o[f]);
-#pragma unroll
-      for (int k = 0; k < NQ - 1; ++k) q[f][k] = q[f][k + 1];
+      for (int f = 0; f < NF; ++f) dst[f][acc.p] = from_c<T>(o[f]);
     }
   }
 }

@@ -106,9 +106,9 @@ cudaError_t run_direct(const StepArgs& a, const Op& op, int* blocks_out) {
   return cudaGetLastError();
 }
 
-// Column march geometry: 32 x 8 column tiles; z cut into chunks of at least
-// 16 planes so that about two waves of 256-thread blocks (eight per SM) are
-// in flight (each chunk stages 2R extra planes).
+// Plane march geometry: kMarchX x kMarchY column tiles; z cut into chunks of
+// at least 16 planes so that about two waves of 256-thread blocks (eight per
+// SM) are in flight (each chunk stages 2R extra planes).
 inline bool march_geometry(const Geom& g, int* blocks, int* zchunk) {
   const int64_t tiles = ((g.n[2] + kMarchX - 1) / kMarchX) * ((g.n[1] + kMarchY - 1) / kMarchY);
   const int64_t slots = 2 * 8 * 152;
@@ -140,7 +140,7 @@ cudaError_t run_march(const StepArgs& a, const Op& op) {
 // RK = false: plain sweeps (trapezoid with temporal blocking, direct, column
 // march).  RK = true: the multi-stage forms (fused trapezoid steps; a
 // combining stage, out = a * base + b * E(in), on the direct kernel or the
-// column march).
+// plane march).
 template <bool RK, class Op, class T>
 cudaError_t run_any(const StepArgs& a, const Op& op, int kind, int* blocks) {
   if (kind == kGenTrap) {

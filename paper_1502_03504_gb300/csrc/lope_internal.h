@@ -102,7 +102,7 @@ bool tma_supported(const StepArgs& a);
 cudaError_t launch_trap2d(const StepArgs& a);
 bool trap2d_supported(const StepArgs& a);
 cudaError_t launch_direct(const StepArgs& a, int* blocks);
-// 3D column march for grids the TMA tiles cannot stage (not for adjoint or
+// 3D plane march for grids the TMA tiles cannot stage (not for adjoint or
 // run-time compiled functions).
 cudaError_t launch_march(const StepArgs& a);
 bool march_supported(const StepArgs& a);
@@ -120,7 +120,7 @@ cudaError_t jit_launch(const StepArgs& a, int path);
 
 // Multi-stage forms on the generic kernels (k_generic_rk.cu): fused trapezoid
 // steps (kGenTrap), or a combining stage on the direct kernel (kGenDirect) or
-// the column march (kGenMarch).
+// the plane march (kGenMarch).
 enum : int { kGenDirect = 0, kGenTrap = 1, kGenMarch = 2 };
 cudaError_t launch_generic_rk(const StepArgs& a, int kind, int* blocks);
 bool direct_supported(const StepArgs& a);

@@ -1,8 +1,8 @@
 """Grids whose row pitch is not a multiple of 16 bytes (no TMA staging).
 
 The planner sends such 2D grids to trapezoid tiles fusing 4 sweeps (128 x 32
-for one field, 64 x 16 for several) and 3D grids to the direct kernel; the 3D
-column march (launch path 4) is checked against the direct kernel.  Every
+for one field, 64 x 16 for several) and 3D grids to the plane march (launch
+path 4), which is checked against the direct kernel.  Every
 path evaluates the same arithmetic, so the default plan, trapezoid tiles with
 one sweep and the direct kernel agree bitwise; FP64 runs match the oracle
 (normwise 1e-12).
@@ -119,7 +119,7 @@ def test_3d_march_equals_direct(lope, dtype, bc):
         assert torch.equal(a, b), (st.scheme, halo)
 
 
-def test_3d_odd_width_default_is_direct_and_march_matches_oracle(lope, orc, capfd):
+def test_3d_odd_width_default_is_march_and_matches_oracle(lope, orc, capfd):
     shape, T = (33, 18, 27), 8
     u, us = to_device(LI.uniform_field(1450, shape), "f64")
     g = lope.Grid(shape, "f64", halo=1)
@@ -130,8 +130,8 @@ def test_3d_odd_width_default_is_direct_and_march_matches_oracle(lope, orc, capf
         got = _run(lope, g, st, u, T)[0]
     finally:
         lope.lope_set_option("log", 0)
-    assert "path=direct" in capfd.readouterr().err
+    assert "path=march" in capfd.readouterr().err
     want = orc.apply(us, "diff7", [0.1], T, bc=[1, 0, 1], bval=[0.25, 0.0, -0.5])
     assert normwise(to_host(got), want) <= 1e-12
-    march = _run(lope, g, st, u, T, lope.Launch(MARCH, 0, 0, 0, -1))[0]
-    assert normwise(to_host(march), want) <= 1e-12
+    direct = _run(lope, g, st, u, T, lope.Launch(DIRECT, 0, 0, 0, -1))[0]
+    assert normwise(to_host(direct), want) <= 1e-12
