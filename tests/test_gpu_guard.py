@@ -118,3 +118,21 @@ def test_batched_and_source_and_host_paths_write_only_their_output(lope):
                     dbufs[2][1], nsteps=6)
     torch.cuda.synchronize()
     assert all(_guards_intact(b, 150 * 200) for b, _ in dbufs)
+
+
+@pytest.mark.parametrize("bc", [[0, 0, 0], [1, 0, 1]])
+def test_unaligned_paths_write_only_their_output(lope, bc):
+    # rows whose pitch is not a multiple of 16 bytes: 2D trapezoid tiles fusing
+    # 4 sweeps (the default) and the 3D plane march and direct kernel
+    u2 = torch.from_numpy(LI.uniform_field(1740, (83, 261)).astype(np.float32)).cuda()
+    g2 = lope.Grid((83, 261), "f32", halo=1)
+    g2.set_boundaries(bc[1:])
+    st2 = lope.Stencil.builtin("jacobi5", 0.2)
+    for launch in (lope.Launch(0, 0, 0, 0, -1), lope.Launch(2, 64, 16, 4, -1)):
+        _check(lope, g2, st2, [u2], 9, launch)
+    u3 = torch.from_numpy(LI.uniform_field(1741, (21, 19, 45)).astype(np.float32)).cuda()
+    g3 = lope.Grid((21, 19, 45), "f32", halo=1)
+    g3.set_boundaries(bc)
+    st3 = lope.Stencil.builtin("diff7", 0.1)
+    for launch in (lope.Launch(4, 0, 0, 0, -1), lope.Launch(3, 0, 0, 0, -1)):
+        _check(lope, g3, st3, [u3], 5, launch)
