@@ -462,15 +462,17 @@ lope_status apply_impl(const lope_grid* grid, const lope_stencil* st, const void
     std::string err;
     if ((rs = jit_compile(st->jit, g.dtype, &err)) != LOPE_OK) return fail(rs, err);
   }
-  DevState* d = nullptr;
-  if ((rs = dev_state(&d)) != LOPE_OK) return rs;
+  // Plan and argument checks are host-only: a bad call fails before any CUDA
+  // call is made.
   Choice c;
-  if ((rs = resolve(g, s, in, cfg, d->err, &c)) != LOPE_OK) return rs;
+  if ((rs = resolve(g, s, in, cfg, nullptr, &c)) != LOPE_OK) return rs;
   int64_t L = nsteps == 0 ? 0 : (nsteps + c.k - 1) / c.k;
   const bool staged = s.stages >= 2 && c.path != kPathTrap;  // one launch per stage
   if (staged) L = nsteps * s.stages;
   if ((rs = check_fields(g, in, out, work, staged ? nsteps >= 1 : L >= 2, work_states(s))) != LOPE_OK)
     return rs;
+  DevState* d = nullptr;
+  if ((rs = dev_state(&d)) != LOPE_OK) return rs;
   if (nsteps == 0) {
     for (int f = 0; f < g.nf; ++f) {
       cudaError_t e = cudaMemcpyAsync(out[f], in[f], size_t(npts(g)) * esize(g.dtype),

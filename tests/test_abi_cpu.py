@@ -102,3 +102,39 @@ def test_noalloc_reduce_rejects_bad_arguments_without_gpu(lope):
         lope.lope_reduce_noalloc(0, lope.DTYPES["f32"], 16, 0, (1 << 28) + 1, 32, None)
     with pytest.raises(lope.LopeError, match="bad reduction"):
         lope.lope_reduce_noalloc(7, lope.DTYPES["f32"], 16, 0, 10, 32, None)
+
+
+def test_apply_arguments_are_checked_before_any_cuda_call(lope):
+    """Misaligned, missing and aliasing buffers fail on the host (fake device
+    addresses, never dereferenced), before the library touches CUDA."""
+    g = lope.Grid((64, 64), halo=1)  # 16 KiB per FP32 field
+    s = lope.Stencil.builtin("jacobi5", 0.2)
+    base, field = 1 << 40, 64 * 64 * 4
+    with pytest.raises(lope.LopeError, match="16-byte aligned"):
+        lope.lope_apply(g.handle, s.handle, [base + 4], [base + 2 * field], None, 1, None)
+    with pytest.raises(lope.LopeError, match="aliases"):
+        lope.lope_apply(g.handle, s.handle, [base], [base + field // 2], None, 1, None)
+    direct = lope.Launch(3, 0, 0, 0, -1)  # one sweep per launch: 3 steps need a work buffer
+    with pytest.raises(lope.LopeError, match="work buffers"):
+        lope.lope_apply_with(g.handle, s.handle, [base], [base + field], None, 3, direct, None)
+    with pytest.raises(lope.LopeError, match="work aliases"):
+        lope.lope_apply_with(g.handle, s.handle, [base], [base + field], [base + field + 256], 3,
+                             direct, None)
+    with pytest.raises(lope.LopeError, match="NULL field"):
+        lope.lope_apply(g.handle, s.handle, [0], [base], None, 1, None)
+    with pytest.raises(lope.LopeError, match="nsteps"):
+        lope.lope_apply(g.handle, s.handle, [base], [base + field], None, -1, None)
+    # multi-stage: RK3 on the stage path needs two states per work buffer
+    s.set_scheme("rk3")
+    with pytest.raises(lope.LopeError, match="work aliases"):
+        lope.lope_apply_with(g.handle, s.handle, [base], [base + 2 * field], [base + field], 1,
+                             lope.Launch(3, 0, 0, 0, -1), None)
+    # a launch path that cannot take the grid is refused by the planner
+    g3 = lope.Grid((8, 8, 10), halo=1)  # 40-byte rows: no TMA staging
+    s3 = lope.Stencil.builtin("diff7", 0.1)
+    with pytest.raises(lope.LopeError, match="does not support"):
+        lope.lope_apply_with(g3.handle, s3.handle, [base], [base + 4096], None, 1,
+                             lope.Launch(1, 0, 0, 0, -1), None)
+    with pytest.raises(lope.LopeError, match="does not support"):
+        lope.lope_apply_with(g3.handle, s3.handle, [base], [base + 4096], None, 1,
+                             lope.Launch(2, 64, 32, 1, -1), None)
