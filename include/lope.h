@@ -218,6 +218,22 @@ lope_status lope_autotune(const lope_grid* grid, const lope_stencil* stencil,
                           const void* const* in, void* const* out, void* const* work,
                           int64_t nsteps, lope_launch* best, double* best_ms, void* cuda_stream);
 
+/* Autotune cache file.  lope_tune_cache_save writes every choice that
+ * lope_autotune and lope_autotune_batch made in this process (builtin and
+ * weight-table stencils; source stencils are left out) to the text file at
+ * path, one entry per line, tagged with a GPU name: gpu_name, or the current
+ * device's name when gpu_name is NULL.  lope_tune_cache_load installs the
+ * entries of such a file whose GPU name matches, so that later lope_apply and
+ * lope_apply_batch calls plan with them; lines that do not parse or name
+ * another GPU are skipped, and *loaded (may be NULL) receives the number
+ * installed.  A remembered choice that cannot run a grid (e.g. a TMA plan for
+ * a misaligned input) is ignored at planning time.  The paper has no
+ * counterpart; this is a property of the library only.
+ * Errors: LOPE_ERR_INVALID for a NULL path or a file that cannot be opened or
+ * written; LOPE_ERR_CUDA when gpu_name is NULL and no device can be queried. */
+lope_status lope_tune_cache_save(const char* path, const char* gpu_name);
+lope_status lope_tune_cache_load(const char* path, const char* gpu_name, int* loaded);
+
 /* Batched form: n independent grids of possibly different extents and
  * boundaries (same dtype, nfields and stencil) advanced nsteps each in one
  * persistent launch per call, replayed from a cached CUDA graph.  in/out/work

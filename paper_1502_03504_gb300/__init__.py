@@ -63,6 +63,8 @@ from ._lib import (  # noqa: F401  (C ABI names)
     lope_stencil_destroy,
     lope_stencil_set_scheme,
     lope_sync_status,
+    lope_tune_cache_load,
+    lope_tune_cache_save,
     lope_version,
     lope_vjp,
     lope_work_states,

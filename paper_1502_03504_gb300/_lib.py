@@ -57,6 +57,8 @@ _SIGS = {
     "lope_grid_create": (_INT, [ctypes.POINTER(_P), _INT, ctypes.POINTER(_I64),
                                 ctypes.POINTER(_INT), ctypes.POINTER(_INT), _INT, _INT]),
     "lope_grid_destroy": (None, [_P]),
+    "lope_tune_cache_save": (_INT, [ctypes.c_char_p, ctypes.c_char_p]),
+    "lope_tune_cache_load": (_INT, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(_INT)]),
     "lope_set_boundary": (_INT, [_P, _INT, _INT, _INT, _D]),
     "lope_stencil_create_builtin": (_INT, [ctypes.POINTER(_P), ctypes.c_char_p, _DP, _INT]),
     "lope_stencil_create_linear": (_INT, [ctypes.POINTER(_P), _INT, _INT, _DP]),
@@ -275,6 +277,19 @@ def lope_reduce_noalloc(op, dtype, x, y, n, result_dev, stream):
     """FP64 reduction whose partial sums live in the library's own static
     device array: no scratch buffer from the caller (see include/lope.h)."""
     _check(load().lope_reduce_noalloc(op, dtype, x, y, int(n), result_dev, stream))
+
+
+def lope_tune_cache_save(path: str, gpu_name=None):
+    _check(load().lope_tune_cache_save(str(path).encode(),
+                                       gpu_name.encode() if gpu_name is not None else None))
+
+
+def lope_tune_cache_load(path: str, gpu_name=None) -> int:
+    n = _INT(0)
+    _check(load().lope_tune_cache_load(str(path).encode(),
+                                       gpu_name.encode() if gpu_name is not None else None,
+                                       ctypes.byref(n)))
+    return n.value
 
 
 def lope_sync_status(stream):

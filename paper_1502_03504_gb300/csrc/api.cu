@@ -12,11 +12,13 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <initializer_list>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <set>
+#include <sstream>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -165,13 +167,32 @@ StepArgs base_args(const Geom& g, const StencilDesc& s, int* err, cudaStream_t s
   return a;
 }
 
+// Whether launch choice c can run this grid and stencil (a.in holds the
+// input pointers, whose alignment the TMA path checks).
+bool choice_supported(StepArgs a, const Choice& c) {
+  a.ksteps = c.k;
+  a.tile_x = c.tile_x;
+  a.tile_y = c.tile_y;
+  bool ok = false;
+  switch (c.path) {
+    case kPathTma: ok = tma_supported(a); break;
+    case kPathTrap: ok = trap2d_supported(a); break;
+    case kPathDirect: ok = direct_supported(a); break;
+    case kPathMarch: ok = march_supported(a); break;
+    default: ok = false;
+  }
+  return ok && !(a.s.stages >= 2 && c.path != kPathTrap && c.k != 1);
+}
+
 Choice default_choice(const Geom& g, const StencilDesc& s, int* err) {
   StepArgs a = base_args(g, s, err, nullptr);
   for (int f = 0; f < g.nf; ++f) a.in[f] = reinterpret_cast<const void*>(uintptr_t(256));
   {
+    // a remembered autotuner choice (possibly loaded from a cache file) is
+    // used when it can run this grid
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(tune_key(g, s));
-    if (it != g_tune.end()) return it->second;
+    if (it != g_tune.end() && choice_supported(a, it->second)) return it->second;
   }
   if (s.stages >= 2 && g.ndim == 2 && g.nf == 1 && g.dtype == kF32) {
     // Multi-stage steps of a single FP32 field: the fused trapezoid keeps the
@@ -237,19 +258,7 @@ lope_status resolve(const Geom& g, const StencilDesc& s, const void* const* in,
   }
   StepArgs a = base_args(g, s, err, nullptr);
   for (int f = 0; f < g.nf; ++f) a.in[f] = in ? in[f] : nullptr;
-  a.ksteps = d.k;
-  a.tile_x = d.tile_x;
-  a.tile_y = d.tile_y;
-  bool ok = false;
-  switch (d.path) {
-    case kPathTma: ok = tma_supported(a); break;
-    case kPathTrap: ok = trap2d_supported(a); break;
-    case kPathDirect: ok = direct_supported(a); break;
-    case kPathMarch: ok = march_supported(a); break;
-    default: ok = false;
-  }
-  if (ok && s.stages >= 2 && d.path != kPathTrap && a.ksteps != 1) ok = false;
-  if (!ok) return fail(LOPE_ERR_UNSUPPORTED, "requested launch path does not support this grid/stencil/depth");
+  if (!choice_supported(a, d)) return fail(LOPE_ERR_UNSUPPORTED, "requested launch path does not support this grid/stencil/depth");
   *c = d;
   return LOPE_OK;
 }
@@ -471,6 +480,9 @@ lope_status apply_impl(const lope_grid* grid, const lope_stencil* st, const void
   if (staged) L = nsteps * s.stages;
   if ((rs = check_fields(g, in, out, work, staged ? nsteps >= 1 : L >= 2, work_states(s))) != LOPE_OK)
     return rs;
+  const int gmode = cfg ? cfg->graph : 0;
+  const bool use_graph = gmode == 1 || (gmode == 0 && L >= 8 && npts(g) <= (int64_t(1) << 22));
+  if (nsteps > 0 && log_enabled()) log_plan(g, s, c, nsteps, L, use_graph);
   DevState* d = nullptr;
   if ((rs = dev_state(&d)) != LOPE_OK) return rs;
   if (nsteps == 0) {
@@ -481,9 +493,6 @@ lope_status apply_impl(const lope_grid* grid, const lope_stencil* st, const void
     }
     return LOPE_OK;
   }
-  const int gmode = cfg ? cfg->graph : 0;
-  const bool use_graph = gmode == 1 || (gmode == 0 && L >= 8 && npts(g) <= (int64_t(1) << 22));
-  if (log_enabled()) log_plan(g, s, c, nsteps, L, use_graph);
   if (use_graph) {
     return run_graph(graph_key(g, s, c, in, out, work, nsteps), stream, [&](cudaStream_t cs) {
       cudaError_t e = issue(g, s, c, in, out, work, nsteps, d->err, cs);
@@ -700,6 +709,76 @@ BatchSig batch_sig(int n, const lope_grid* const* grids, const StencilDesc& s) {
       }
   }
   return k;
+}
+
+// ------------------------------------------------------------------ tune cache file
+// The autotuners' choices as a text file, one entry per line:
+//   lope-tune 1 <gpu> grid <ndim> <n0> <n1> <n2> <dtype> <kind> <radius> <star> <bcs> <nf> <stages> : <path> <tile_x> <tile_y> <k>
+//   lope-tune 1 <gpu> batch <m> <m signature integers> : <path> <tile_x> <tile_y> <k>
+// <gpu> is the device name with blanks replaced by '_'.  Entries of source
+// stencils are not written (their keys hold a process-local pointer).
+std::string gpu_tag(const char* name) {
+  std::string t(name);
+  for (char& ch : t)
+    if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
+  return t;
+}
+
+lope_status gpu_tag_of(const char* gpu_name, std::string* out) {
+  if (gpu_name) {
+    *out = gpu_tag(gpu_name);
+  } else {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess)
+      return cuda_fail(e, "cudaGetDeviceProperties");
+    *out = gpu_tag(prop.name);
+  }
+  if (out->empty()) return fail(LOPE_ERR_INVALID, "empty GPU name");
+  return LOPE_OK;
+}
+
+bool choice_in_range(const Choice& c) {
+  return c.path >= kPathTma && c.path <= kPathMarch && c.tile_x >= 0 && c.tile_x <= 256 &&
+         c.tile_y >= 0 && c.tile_y <= 256 && c.k >= 1 && c.k <= 8;
+}
+
+// One line of a cache file; false if it is malformed or names another GPU.
+bool parse_tune_line(const std::string& line, const std::string& gpu, bool* batch, TuneKey* gk,
+                     BatchSig* bk, Choice* c) {
+  std::istringstream is(line);
+  std::string magic, tag, kind, colon;
+  int version = 0;
+  if (!(is >> magic >> version >> tag >> kind) || magic != "lope-tune" || version != 1 || tag != gpu)
+    return false;
+  if (kind == "grid") {
+    long long v[11];
+    for (auto& x : v)
+      if (!(is >> x)) return false;
+    if (v[0] < 2 || v[0] > 3 || v[1] < 1 || v[2] < 1 || v[3] < 1 || v[4] < 0 || v[4] > 2) return false;
+    *gk = TuneKey(int(v[0]), v[1], v[2], v[3], int(v[4]), int(v[5]), int(v[6]), int(v[7]), int(v[8]),
+                  int(v[9]), int(v[10]), 0);
+    *batch = false;
+  } else if (kind == "batch") {
+    long long m = 0;
+    if (!(is >> m) || m < 6 || m > (1 << 22)) return false;
+    bk->assign(size_t(m), 0);
+    for (auto& x : *bk) {
+      long long y;
+      if (!(is >> y)) return false;
+      x = y;
+    }
+    if ((*bk)[5] != 0) return false;
+    *batch = true;
+  } else {
+    return false;
+  }
+  if (!(is >> colon >> c->path >> c->tile_x >> c->tile_y >> c->k) || colon != ":") return false;
+  if (!choice_in_range(*c)) return false;
+  if (*batch && (c->path != kPathTrap || c->tile_x < 8 || c->tile_y < 1)) return false;
+  return true;
 }
 
 }  // namespace
@@ -1325,6 +1404,73 @@ lope_status lope_sync_status(void* cuda_stream) {
     cudaMemset(d->err, 0, sizeof(int));
     return fail(LOPE_ERR_TIMEOUT, "a bounded in-kernel wait gave up");
   }
+  return LOPE_OK;
+}
+
+
+lope_status lope_tune_cache_save(const char* path, const char* gpu_name) {
+  if (!path) return fail(LOPE_ERR_INVALID, "NULL cache file path");
+  std::string gpu;
+  lope_status rs = gpu_tag_of(gpu_name, &gpu);
+  if (rs != LOPE_OK) return rs;
+  std::ostringstream os;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& kv : g_tune) {
+      const TuneKey& k = kv.first;
+      const Choice& c = kv.second;
+      if (std::get<11>(k) != 0) continue;
+      os << "lope-tune 1 " << gpu << " grid " << std::get<0>(k) << ' ' << std::get<1>(k) << ' '
+         << std::get<2>(k) << ' ' << std::get<3>(k) << ' ' << std::get<4>(k) << ' ' << std::get<5>(k)
+         << ' ' << std::get<6>(k) << ' ' << std::get<7>(k) << ' ' << std::get<8>(k) << ' '
+         << std::get<9>(k) << ' ' << std::get<10>(k) << " : " << c.path << ' ' << c.tile_x << ' '
+         << c.tile_y << ' ' << c.k << '\n';
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    for (const auto& kv : g_btune) {
+      if (kv.first[5] != 0) continue;
+      os << "lope-tune 1 " << gpu << " batch " << kv.first.size();
+      for (int64_t v : kv.first) os << ' ' << v;
+      const Choice& c = kv.second;
+      os << " : " << c.path << ' ' << c.tile_x << ' ' << c.tile_y << ' ' << c.k << '\n';
+    }
+  }
+  FILE* fp = std::fopen(path, "w");
+  if (!fp) return fail(LOPE_ERR_INVALID, "cannot open the tune cache file for writing");
+  const std::string text = os.str();
+  const bool ok = std::fwrite(text.data(), 1, text.size(), fp) == text.size();
+  if (std::fclose(fp) != 0 || !ok) return fail(LOPE_ERR_INVALID, "error writing the tune cache file");
+  return LOPE_OK;
+}
+
+lope_status lope_tune_cache_load(const char* path, const char* gpu_name, int* loaded) {
+  if (loaded) *loaded = 0;
+  if (!path) return fail(LOPE_ERR_INVALID, "NULL cache file path");
+  std::string gpu;
+  lope_status rs = gpu_tag_of(gpu_name, &gpu);
+  if (rs != LOPE_OK) return rs;
+  std::ifstream in(path);
+  if (!in) return fail(LOPE_ERR_INVALID, "cannot open the tune cache file");
+  std::string line;
+  int count = 0;
+  while (std::getline(in, line)) {
+    bool batch = false;
+    TuneKey gk;
+    BatchSig bk;
+    Choice c;
+    if (!parse_tune_line(line, gpu, &batch, &gk, &bk, &c)) continue;
+    if (batch) {
+      std::lock_guard<std::mutex> lk(g_btune_mu);
+      g_btune[bk] = c;
+    } else {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[gk] = c;
+    }
+    ++count;
+  }
+  if (loaded) *loaded = count;
   return LOPE_OK;
 }
 

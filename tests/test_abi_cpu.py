@@ -138,3 +138,43 @@ def test_apply_arguments_are_checked_before_any_cuda_call(lope):
     with pytest.raises(lope.LopeError, match="does not support"):
         lope.lope_apply_with(g3.handle, s3.handle, [base], [base + 4096], None, 1,
                              lope.Launch(2, 64, 32, 1, -1), None)
+
+
+def test_tune_cache_file_round_trip_and_planning(lope, tmp_path, capfd):
+    """A cache file's entries are installed for the named GPU only, written back
+    unchanged, and used by the planner (visible in the plan log, which is
+    printed before any CUDA call)."""
+    gpu = "Test GB300"
+    lines = [
+        # a 1000 x 256 FP32 jacobi5 grid (extents slowest first; kind 1, radius 1,
+        # star), periodic: the direct kernel
+        "lope-tune 1 Test_GB300 grid 2 1 1000 256 1 1 1 1 0 1 1 : 3 0 0 1",
+        # a batch of two grids: 64 x 16 tiles, depth 2
+        "lope-tune 1 Test_GB300 batch 20 2 1 1 1 1 0 0 0 0 0 64 64 0 0 0 0 0 0 0 0 : 2 64 16 2",
+    ]
+    other = ["lope-tune 1 Other_GPU grid 2 1 8 8 1 1 1 1 0 1 1 : 3 0 0 1",
+             "lope-tune 1 Test_GB300 grid 2 1 8 8 1 1 1 1 0 1 1 : 9 0 0 1",  # no such path
+             "lope-tune 2 Test_GB300 grid 2 1 8 8 1 1 1 1 0 1 1 : 3 0 0 1",  # unknown version
+             "garbage", ""]
+    src = tmp_path / "tune.txt"
+    src.write_text("\n".join(lines + other) + "\n")
+    assert lope.lope_tune_cache_load(src, gpu) == 2
+    assert lope.lope_tune_cache_load(src, "Another GPU") == 0
+    out = tmp_path / "saved.txt"
+    lope.lope_tune_cache_save(out, gpu)
+    saved = set(out.read_text().splitlines())
+    assert set(lines) <= saved
+    # the planner takes the loaded choice for that grid
+    g = lope.Grid((1000, 256), halo=1)
+    s = lope.Stencil.builtin("jacobi5", 0.2)
+    base, field = 1 << 40, 256 * 1000 * 4
+    lope.lope_set_option("log", 1)
+    try:
+        with pytest.raises(lope.LopeError):  # no GPU here: fails at the first CUDA call
+            lope.lope_apply(g.handle, s.handle, [base], [base + field], None, 1, None)
+    finally:
+        lope.lope_set_option("log", 0)
+    err = capfd.readouterr().err
+    assert "grid 1000x256 f32" in err and "path=direct" in err
+    with pytest.raises(lope.LopeError, match="open"):
+        lope.lope_tune_cache_load(tmp_path / "missing.txt", gpu)
