@@ -148,9 +148,20 @@ def oracle_rates(budget_s=12.0):
     r3, s3, d3 = out["3d"]
     r2, s2, d2 = out["2d"]
     combined = (UPD3 + UPD2) / (UPD3 / r3 + UPD2 / r2)
+    # the same kernels on one thread, one sweep each
+    one = {}
+    for name, shape, kind in (("3d", (160, 160, 160), "diff7"), ("2d", (2048, 2048), "star9r2")):
+        u = LI.uniform_field(7, shape)
+        bc = [1, 1, 1] if kind == "diff7" else [0, 0]
+        t0 = time.perf_counter()
+        oracle.apply(u, kind, [0.1], 1, bc=bc, nthreads=1)
+        one[name] = u.size / (time.perf_counter() - t0)
+    single = (UPD3 + UPD2) / (UPD3 / one["3d"] + UPD2 / one["2d"])
     return {"value": combined, "unit": UNIT, "cores": th, "kind": "oracle",
             "sample": f"{s3} ({r3:.3e}/s) and {s2} ({r2:.3e}/s), FP64, combined in the "
-                      f"step's 2:1 update mix; {d3 + d2:.1f} s of CPU work"}
+                      f"step's 2:1 update mix; {d3 + d2:.1f} s of CPU work",
+            "value_1thread": single,
+            "sample_1thread": "one sweep of each on one thread, same mix"}
 
 
 def run_reference(args):
