@@ -323,3 +323,22 @@ def test_adjoint_central_differences_32cube(orc):
     # Richardson extrapolation removes the O(eps^2) term of the central difference.
     assert abs((4 * fd_c2 - fd_c) / 3 - gc) < 1e-6 * abs(gc)
     assert abs(loss - L(u0, c)) < 1e-12 * loss
+
+
+def test_corner_ghost_takes_the_slowest_crossed_axis(orc):
+    """A corner ghost cell that crosses Dirichlet sides of several axes takes the
+    value of the slowest one (z, then y, then x); a crossed periodic axis does
+    not change that.  Pinned with box weights that read only one corner."""
+    u = np.zeros((4, 5, 6))
+    w = np.zeros((3, 3, 3))
+    w[0, 0, 0] = 1.0  # the tap (dz, dy, dx) = (-1, -1, -1)
+    bval = [(7.0, 0.0), (5.0, 0.0), (3.0, 0.0)]
+    got = orc.apply(u, "linear", nsteps=1, bc=[1, 1, 1], bval=bval, weights_table=w)
+    assert got[0, 0, 0] == 7.0  # z, y and x crossed: z decides
+    assert got[1, 0, 0] == 5.0  # y and x crossed: y decides
+    assert got[1, 1, 0] == 3.0  # x only
+    assert got[1, 1, 1] == 0.0  # inside
+    # z periodic: the wrapped z does not hide the y side's value
+    got = orc.apply(u, "linear", nsteps=1, bc=[0, 1, 1], bval=[0.0, (5.0, 0.0), (3.0, 0.0)],
+                    weights_table=w)
+    assert got[0, 0, 0] == 5.0 and got[0, 1, 0] == 3.0
