@@ -135,3 +135,31 @@ def test_3d_odd_width_default_is_march_and_matches_oracle(lope, orc, capfd):
     assert normwise(to_host(got), want) <= 1e-12
     direct = _run(lope, g, st, u, T, lope.Launch(DIRECT, 0, 0, 0, -1))[0]
     assert normwise(to_host(direct), want) <= 1e-12
+
+
+def test_box_corners_across_dirichlet_sides_vs_oracle(lope, orc):
+    """Box stencils read corner ghosts that cross several Dirichlet sides with
+    different values: the slowest crossed axis decides, on every path."""
+    rng = np.random.default_rng(1460)
+    shape3, T = (9, 11, 13), 3
+    u3, u3s = to_device(LI.uniform_field(1461, shape3), "f64")
+    w3 = rng.uniform(-0.05, 0.05, (3, 3, 3))
+    bc3, bv3 = [1, 1, 1], [(0.7, -0.2), (0.5, 0.1), (-0.3, 0.9)]
+    g3 = lope.Grid(shape3, "f64", halo=1)
+    g3.set_boundaries(bc3, bv3)
+    st3 = lope.Stencil.linear(w3)
+    want3 = orc.apply(u3s, "linear", nsteps=T, bc=bc3, bval=bv3, weights_table=w3)
+    for launch in (lope.Launch(MARCH, 0, 0, 0, -1), lope.Launch(DIRECT, 0, 0, 0, -1)):
+        got = _run(lope, g3, st3, u3, T, launch)[0]
+        assert normwise(to_host(got), want3) <= 1e-12, launch
+    shape2 = (37, 41)
+    u2, u2s = to_device(LI.uniform_field(1462, shape2), "f64")
+    w2 = rng.uniform(-0.1, 0.1, (3, 3))
+    bc2, bv2 = [1, 1], [(0.5, 0.1), (-0.3, 0.9)]
+    g2 = lope.Grid(shape2, "f64", halo=1)
+    g2.set_boundaries(bc2, bv2)
+    st2 = lope.Stencil.linear(w2)
+    want2 = orc.apply(u2s, "linear", nsteps=T, bc=bc2, bval=bv2, weights_table=w2)
+    for launch in (None, lope.Launch(2, 32, 8, 3, -1), lope.Launch(DIRECT, 0, 0, 0, -1)):
+        got = _run(lope, g2, st2, u2, T, launch)[0]
+        assert normwise(to_host(got), want2) <= 1e-12, launch
