@@ -78,13 +78,19 @@ class Clocks:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.proc, self.path, self.gpu = None, None, gpu_index
+    def __init__(self, gpu_index, out_dir=None):
+        self.proc, self.path, self.gpu, self.out_dir = None, None, gpu_index, out_dir
 
     def start(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{self.gpu}.csv")
+            # the samples go to --clocks-dir when given, else to a temporary file
+            if self.out_dir:
+                os.makedirs(self.out_dir, exist_ok=True)
+                self.path = os.path.join(self.out_dir, f"clocks_rank{self.gpu}.csv")
+            else:
+                import tempfile
+                fd, self.path = tempfile.mkstemp(prefix=f"lope_clocks_rank{self.gpu}_", suffix=".csv")
+                os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
@@ -119,6 +125,11 @@ class Clocks:
                 for n, v in zip(names, f[5:9]):
                     if v.lower().startswith("active"):
                         reasons.add(n)
+        if not self.out_dir:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
@@ -235,6 +246,8 @@ def main():
     ap.add_argument("--impl", default="lope", choices=["lope", "reference"])
     ap.add_argument("--main-only", action="store_true", help="skip the extra forms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="keep the nvidia-smi clock samples of the timed region in this folder")
     ap.add_argument("--profile", default=None,
                     help="run one kernel workload for --steps launches and exit (for ncu): "
                          "diff7:N, diff7p:N, star9r2:N, jacobi5:N, swe:N, swebf16:N, with an "
@@ -290,7 +303,7 @@ def main():
     L.sync_status()
 
     # ---------------- timed region: device-resident inputs
-    clocks = Clocks(local)
+    clocks = Clocks(local, args.clocks_dir)
     clocks.start()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
