@@ -178,3 +178,41 @@ def test_tune_cache_file_round_trip_and_planning(lope, tmp_path, capfd):
     assert "grid 1000x256 f32" in err and "path=direct" in err
     with pytest.raises(lope.LopeError, match="open"):
         lope.lope_tune_cache_load(tmp_path / "missing.txt", gpu)
+
+
+PLAN_CASES = [  # shape, dtype, builtin, params, halo, scheme, bc, expected plan-log fragment
+    ((512, 512, 512), "f32", "diff7", [0.1], 1, "euler", [1, 1, 1], "path=tma"),
+    ((8192, 8192), "f32", "star9r2", [0.1], 2, "euler", [0, 0], "path=tma"),
+    ((256, 256), "f64", "jacobi5", [0.2], 1, "euler", [0, 0], "path=trapezoid tile=64x16 k=4"),
+    ((7094, 7094), "f32", "jacobi5", [0.2], 1, "euler", [0, 1], "path=trapezoid tile=128x32 k=4"),
+    ((7094, 7094), "f32", "swe_flux", [0.02, 1.0, 0.5, 1.0], 1, "euler", [0, 0],
+     "path=trapezoid tile=64x16 k=4"),
+    ((130, 500, 510), "f32", "diff7", [0.1], 1, "euler", [1, 0, 1], "path=march"),
+    ((8192, 8192), "f32", "jacobi5", [0.2], 1, "rk3", [0, 0], "path=trapezoid tile=128x16 k=1"),
+    ((4096, 4096), "f32", "swe_flux", [0.02, 1.0, 0.5, 1.0], 1, "rk3", [0, 0], "path=tma"),
+]
+
+
+@pytest.mark.parametrize("case", PLAN_CASES, ids=lambda c: f"{c[2]}-{'x'.join(map(str, c[0]))}-{c[5]}")
+def test_planner_default_choices(lope, capfd, case):
+    """The planner's documented defaults, read from the plan log (printed before
+    the first CUDA call; fake device addresses, never dereferenced)."""
+    shape, dtype, name, prm, halo, scheme, bc, want = case
+    nf = 3 if name.startswith("swe") else 1
+    g = lope.Grid(shape, dtype, halo=halo, nfields=nf)
+    g.set_boundaries(bc)
+    st = lope.Stencil.builtin(name, *prm).set_scheme(scheme)
+    esz = {"f32": 4, "f64": 8, "bf16": 2}[dtype]
+    field = int(np.prod(shape)) * esz
+    base = 1 << 44
+    ins = [base + k * field for k in range(nf)]
+    outs = [base + (nf + k) * field for k in range(nf)]
+    works = [base + (2 * nf + 2 * k) * field for k in range(nf)]
+    lope.lope_set_option("log", 1)
+    try:
+        with pytest.raises(lope.LopeError):  # no GPU here: fails at the first CUDA call
+            lope.lope_apply(g.handle, st.handle, ins, outs, works, 10, None)
+    finally:
+        lope.lope_set_option("log", 0)
+    err = capfd.readouterr().err
+    assert want in err, err
