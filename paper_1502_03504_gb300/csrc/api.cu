@@ -459,9 +459,12 @@ lope_status run_graph(const GraphKey& key, cudaStream_t st, F&& body) {
   return LOPE_OK;
 }
 
-lope_status apply_impl(const lope_grid* grid, const lope_stencil* st, const void* const* in,
-                       void* const* out, void* const* work, int64_t nsteps, const lope_launch* cfg,
-                       cudaStream_t stream) {
+// The host-only part of an apply: compile a source stencil for the storage
+// type, resolve the plan, and check every buffer argument.  A bad call fails
+// here, before any CUDA call is made.
+lope_status prepare_apply(const lope_grid* grid, const lope_stencil* st, const void* const* in,
+                          void* const* out, void* const* work, int64_t nsteps,
+                          const lope_launch* cfg, Choice* c, int64_t* L) {
   lope_status rs = check_pair(grid, st);
   if (rs != LOPE_OK) return rs;
   if (nsteps < 0) return fail(LOPE_ERR_INVALID, "nsteps < 0");
@@ -471,15 +474,22 @@ lope_status apply_impl(const lope_grid* grid, const lope_stencil* st, const void
     std::string err;
     if ((rs = jit_compile(st->jit, g.dtype, &err)) != LOPE_OK) return fail(rs, err);
   }
-  // Plan and argument checks are host-only: a bad call fails before any CUDA
-  // call is made.
+  if ((rs = resolve(g, s, in, cfg, nullptr, c)) != LOPE_OK) return rs;
+  *L = nsteps == 0 ? 0 : (nsteps + c->k - 1) / c->k;
+  const bool staged = s.stages >= 2 && c->path != kPathTrap;  // one launch per stage
+  if (staged) *L = nsteps * s.stages;
+  return check_fields(g, in, out, work, staged ? nsteps >= 1 : *L >= 2, work_states(s));
+}
+
+lope_status apply_impl(const lope_grid* grid, const lope_stencil* st, const void* const* in,
+                       void* const* out, void* const* work, int64_t nsteps, const lope_launch* cfg,
+                       cudaStream_t stream) {
   Choice c;
-  if ((rs = resolve(g, s, in, cfg, nullptr, &c)) != LOPE_OK) return rs;
-  int64_t L = nsteps == 0 ? 0 : (nsteps + c.k - 1) / c.k;
-  const bool staged = s.stages >= 2 && c.path != kPathTrap;  // one launch per stage
-  if (staged) L = nsteps * s.stages;
-  if ((rs = check_fields(g, in, out, work, staged ? nsteps >= 1 : L >= 2, work_states(s))) != LOPE_OK)
-    return rs;
+  int64_t L = 0;
+  lope_status rs = prepare_apply(grid, st, in, out, work, nsteps, cfg, &c, &L);
+  if (rs != LOPE_OK) return rs;
+  const Geom& g = grid->g;
+  const StencilDesc& s = st->s;
   const int gmode = cfg ? cfg->graph : 0;
   const bool use_graph = gmode == 1 || (gmode == 0 && L >= 8 && npts(g) <= (int64_t(1) << 22));
   if (nsteps > 0 && log_enabled()) log_plan(g, s, c, nsteps, L, use_graph);
@@ -1005,6 +1015,13 @@ lope_status lope_apply_host(const lope_grid* grid, const lope_stencil* stencil,
   lope_status rs = check_pair(grid, stencil);
   if (rs != LOPE_OK) return rs;
   if (!host_in || !host_out || !dev_in) return fail(LOPE_ERR_INVALID, "NULL field array");
+  {  // every device-side argument is checked before the first copy is issued
+    Choice c;
+    int64_t L = 0;
+    if ((rs = prepare_apply(grid, stencil, dev_in, dev_out, dev_work, nsteps, nullptr, &c, &L)) !=
+        LOPE_OK)
+      return rs;
+  }
   const Geom& g = grid->g;
   const size_t bytes = size_t(npts(g)) * esize(g.dtype);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

@@ -216,3 +216,19 @@ def test_planner_default_choices(lope, capfd, case):
         lope.lope_set_option("log", 0)
     err = capfd.readouterr().err
     assert want in err, err
+
+
+def test_apply_host_checks_device_buffers_before_copying(lope):
+    """lope_apply_host refuses bad device buffers before it issues any copy (on a
+    machine without a GPU the error is the argument's, not a CUDA error)."""
+    g = lope.Grid((64, 64), halo=1)
+    s = lope.Stencil.builtin("jacobi5", 0.2)
+    host_in, host_out = np.zeros((64, 64), np.float32), np.zeros((64, 64), np.float32)
+    base, field = 1 << 40, 64 * 64 * 4
+    hin, hout = [host_in.ctypes.data], [host_out.ctypes.data]
+    with pytest.raises(lope.LopeError, match="aligned"):
+        lope.lope_apply_host(g.handle, s.handle, hin, hout, [base], [base + field + 8], None, 1, None)
+    with pytest.raises(lope.LopeError, match="aliases"):
+        lope.lope_apply_host(g.handle, s.handle, hin, hout, [base], [base], None, 1, None)
+    with pytest.raises(lope.LopeError, match="nsteps"):
+        lope.lope_apply_host(g.handle, s.handle, hin, hout, [base], [base + field], None, -2, None)
