@@ -210,6 +210,18 @@ lope_status lope_apply_with(const lope_grid* grid, const lope_stencil* stencil,
                             const void* const* in, void* const* out, void* const* work,
                             int64_t nsteps, const lope_launch* cfg, void* cuda_stream);
 
+/* The plan lope_apply_with would run for these arguments, without running
+ * it: *plan receives the launch path, tile, temporal depth and whether the
+ * launch sequence is replayed from a CUDA graph (1) or not (-1), and
+ * *launches (may be NULL) the number of kernel launches.  Host only: no CUDA
+ * call is made, so it also works on a machine without a GPU.  Pointers are
+ * checked (alignment, aliasing, work buffers) but never dereferenced.
+ * Errors: those of lope_apply_with's argument checks; LOPE_ERR_INVALID for a
+ * NULL plan. */
+lope_status lope_plan(const lope_grid* grid, const lope_stencil* stencil, const void* const* in,
+                      void* const* out, void* const* work, int64_t nsteps, const lope_launch* cfg,
+                      lope_launch* plan, int64_t* launches);
+
 /* Time candidate launch choices on the caller's buffers (out and work are
  * overwritten) and remember the fastest for this grid shape, dtype, stencil and
  * boundary; later lope_apply calls use it.  *best receives the choice and

@@ -62,6 +62,7 @@ from ._lib import (  # noqa: F401  (C ABI names)
     lope_stencil_create_source,
     lope_stencil_destroy,
     lope_stencil_set_scheme,
+    lope_plan,
     lope_sync_status,
     lope_tune_cache_load,
     lope_tune_cache_save,

@@ -57,6 +57,8 @@ _SIGS = {
     "lope_grid_create": (_INT, [ctypes.POINTER(_P), _INT, ctypes.POINTER(_I64),
                                 ctypes.POINTER(_INT), ctypes.POINTER(_INT), _INT, _INT]),
     "lope_grid_destroy": (None, [_P]),
+    "lope_plan": (_INT, [_P, _P, _PP, _PP, _PP, _I64, ctypes.POINTER(Launch), ctypes.POINTER(Launch),
+                         ctypes.POINTER(_I64)]),
     "lope_tune_cache_save": (_INT, [ctypes.c_char_p, ctypes.c_char_p]),
     "lope_tune_cache_load": (_INT, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(_INT)]),
     "lope_set_boundary": (_INT, [_P, _INT, _INT, _INT, _D]),
@@ -277,6 +279,17 @@ def lope_reduce_noalloc(op, dtype, x, y, n, result_dev, stream):
     """FP64 reduction whose partial sums live in the library's own static
     device array: no scratch buffer from the caller (see include/lope.h)."""
     _check(load().lope_reduce_noalloc(op, dtype, x, y, int(n), result_dev, stream))
+
+
+def lope_plan(grid, stencil, ins, outs, works, nsteps, launch=None):
+    """The plan lope_apply_with would run: (Launch, number of launches)."""
+    plan = Launch()
+    n = _I64(0)
+    _check(load().lope_plan(grid, stencil, _ptrs(ins), _ptrs(outs),
+                            _ptrs(works) if works is not None else None, int(nsteps),
+                            ctypes.byref(launch) if launch is not None else None,
+                            ctypes.byref(plan), ctypes.byref(n)))
+    return plan, n.value
 
 
 def lope_tune_cache_save(path: str, gpu_name=None):

@@ -1008,6 +1008,25 @@ lope_status lope_apply_with(const lope_grid* grid, const lope_stencil* stencil,
                     static_cast<cudaStream_t>(cuda_stream));
 }
 
+lope_status lope_plan(const lope_grid* grid, const lope_stencil* stencil, const void* const* in,
+                      void* const* out, void* const* work, int64_t nsteps, const lope_launch* cfg,
+                      lope_launch* plan, int64_t* launches) {
+  if (!plan) return fail(LOPE_ERR_INVALID, "NULL plan");
+  Choice c;
+  int64_t L = 0;
+  lope_status rs = prepare_apply(grid, stencil, in, out, work, nsteps, cfg, &c, &L);
+  if (rs != LOPE_OK) return rs;
+  const int gmode = cfg ? cfg->graph : 0;
+  const bool use_graph = gmode == 1 || (gmode == 0 && L >= 8 && npts(grid->g) <= (int64_t(1) << 22));
+  plan->path = c.path;
+  plan->tile_x = c.tile_x;
+  plan->tile_y = c.tile_y;
+  plan->tsteps = c.k;
+  plan->graph = use_graph ? 1 : -1;
+  if (launches) *launches = L;
+  return LOPE_OK;
+}
+
 lope_status lope_apply_host(const lope_grid* grid, const lope_stencil* stencil,
                             const void* const* host_in, void* const* host_out,
                             void* const* dev_in, void* const* dev_out, void* const* dev_work,

@@ -216,6 +216,13 @@ def test_planner_default_choices(lope, capfd, case):
         lope.lope_set_option("log", 0)
     err = capfd.readouterr().err
     assert want in err, err
+    # the same plan through the query call, which makes no CUDA call at all
+    plan, launches = lope.lope_plan(g.handle, st.handle, ins, outs, works, 10)
+    names = {1: "tma", 2: "trapezoid", 3: "direct", 4: "march"}
+    assert f"path={names[plan.path]}" in want
+    if plan.path == 2:
+        assert f"tile={plan.tile_x}x{plan.tile_y} k={plan.tsteps}" in want
+    assert f"launches={launches}" in err
 
 
 def test_apply_host_checks_device_buffers_before_copying(lope):
