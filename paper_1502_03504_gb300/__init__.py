@@ -22,6 +22,7 @@ from ._lib import (  # noqa: F401
     apply,
     apply_batch,
     apply_host,
+    plan,
     adjoint,
     autotune,
     autotune_batch,

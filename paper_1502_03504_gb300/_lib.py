@@ -450,6 +450,14 @@ def apply(grid: Grid, stencil: Stencil, inputs, out=None, work=None, nsteps=1, l
     return outs if isinstance(inputs, (list, tuple)) else outs[0]
 
 
+def plan(grid: Grid, stencil: Stencil, inputs, out, work=None, nsteps=1, launch=None):
+    """The launch plan apply() would run on these tensors: (Launch, launches)."""
+    ins, outs = _as_list(inputs), _as_list(out)
+    works = _as_list(work) if work is not None else None
+    return lope_plan(grid.handle, stencil.handle, [_dptr(t) for t in ins], [_dptr(t) for t in outs],
+                     [_dptr(t) for t in works] if works is not None else None, nsteps, launch)
+
+
 def lope_apply_host(grid, stencil, host_in, host_out, dev_in, dev_out, dev_work, nsteps, stream):
     _check(load().lope_apply_host(grid, stencil, _ptrs(host_in), _ptrs(host_out), _ptrs(dev_in),
                                   _ptrs(dev_out), _ptrs(dev_work) if dev_work is not None else None,

@@ -239,3 +239,17 @@ def test_apply_host_checks_device_buffers_before_copying(lope):
         lope.lope_apply_host(g.handle, s.handle, hin, hout, [base], [base], None, 1, None)
     with pytest.raises(lope.LopeError, match="nsteps"):
         lope.lope_apply_host(g.handle, s.handle, hin, hout, [base], [base + field], None, -2, None)
+
+
+def test_plan_on_tensors(lope):
+    import torch
+
+    g = lope.Grid((300, 301), "f32")
+    st = lope.Stencil.builtin("jacobi5", 0.2)
+    u, o, w = (torch.zeros(300, 301) for _ in range(3))  # addresses only
+    plan, launches = lope.plan(g, st, u, o, w, nsteps=10)
+    assert (plan.path, plan.tile_x, plan.tile_y, plan.tsteps, launches) == (2, 64, 16, 4, 3)
+    plan, launches = lope.plan(g, st, u, o, w, nsteps=10, launch=lope.Launch(3, 0, 0, 0, -1))
+    assert (plan.path, launches, plan.graph) == (3, 10, -1)
+    with pytest.raises(lope.LopeError, match="aliases"):
+        lope.plan(g, st, u, u, w, nsteps=10)
