@@ -324,6 +324,11 @@ lope_status lope_reduce(int op, lope_dtype dtype, const void* x, const void* y, 
  *                        run out and lope_sync_status reports LOPE_ERR_TIMEOUT
  *                        (-1, the default, disables it).  No fault is raised on
  *                        the GPU: every wait ends by itself.
+ *   "fail_alloc"         fault injection on the host: the next `value` calls
+ *                        that may allocate library-owned memory (the
+ *                        per-device state of the first apply, a new batch
+ *                        plan) fail with LOPE_ERR_ALLOC before any CUDA call;
+ *                        0 (the default) disables it.
  *   "log"                1: print each distinct plan that lope_apply and
  *                        lope_apply_with resolve, once, as one line on stderr
  *                        (grid, boundaries, local function, scheme, path, tile,

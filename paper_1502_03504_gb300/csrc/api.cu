@@ -44,6 +44,16 @@ namespace {
 thread_local std::string g_last_error = "no error";
 std::atomic<int64_t> g_wait_limit_ms{1000};
 std::atomic<int64_t> g_skip_arrive{-1};
+// Fault injection on the host: the next g_fail_alloc calls that may allocate
+// library-owned memory fail with LOPE_ERR_ALLOC before touching CUDA.
+std::atomic<int64_t> g_fail_alloc{0};
+
+bool take_alloc_failure() {
+  int64_t v = g_fail_alloc.load();
+  while (v > 0)
+    if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return true;
+  return false;
+}
 thread_local bool g_capturing = false;
 thread_local int64_t g_captured = 0;  // kernels recorded by the capture in progress
 std::atomic<int64_t> g_launches{0};
@@ -72,6 +82,7 @@ std::mutex g_dev_mu;
 std::map<int, DevState> g_dev;
 
 lope_status dev_state(DevState** out) {
+  if (take_alloc_failure()) return fail(LOPE_ERR_ALLOC, "allocation refused (fail_alloc option)");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -1201,6 +1212,7 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
       b.first_item = items;
       items += b.tiles_x * ((b.ny + ty - 1) / ty);
     }
+    if (take_alloc_failure()) return fail(LOPE_ERR_ALLOC, "allocation refused (fail_alloc option)");
     cudaError_t e = cudaMallocHost(&plan->pinned, sizeof(BatchGrid) * n);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
     std::memcpy(plan->pinned, plan->host.data(), sizeof(BatchGrid) * n);
@@ -1412,6 +1424,11 @@ lope_status lope_set_option(const char* name, int64_t value) {
   if (n == "wait_limit_ms") {
     if (value < 1 || value > 600000) return fail(LOPE_ERR_INVALID, "wait_limit_ms out of range");
     g_wait_limit_ms = value;
+    return LOPE_OK;
+  }
+  if (n == "fail_alloc") {
+    if (value < 0 || value > 1000000) return fail(LOPE_ERR_INVALID, "fail_alloc out of range");
+    g_fail_alloc = value;
     return LOPE_OK;
   }
   if (n == "log") {

@@ -253,3 +253,23 @@ def test_plan_on_tensors(lope):
     assert (plan.path, launches, plan.graph) == (3, 10, -1)
     with pytest.raises(lope.LopeError, match="aliases"):
         lope.plan(g, st, u, u, w, nsteps=10)
+
+
+def test_forced_allocation_failure_is_reported_before_cuda(lope):
+    """The fail_alloc option makes the next call that may allocate fail with
+    LOPE_ERR_ALLOC on the host; the one after it proceeds normally (here it
+    then reaches CUDA, which this machine does not have)."""
+    g = lope.Grid((64, 64), halo=1)
+    s = lope.Stencil.builtin("jacobi5", 0.2)
+    base, field = 1 << 40, 64 * 64 * 4
+    with pytest.raises(lope.LopeError):
+        lope.lope_set_option("fail_alloc", -1)
+    lope.lope_set_option("fail_alloc", 1)
+    try:
+        with pytest.raises(lope.LopeError, match="LOPE_ERR_ALLOC"):
+            lope.lope_apply(g.handle, s.handle, [base], [base + field], None, 1, None)
+        with pytest.raises(lope.LopeError) as e:
+            lope.lope_apply(g.handle, s.handle, [base], [base + field], None, 1, None)
+        assert "LOPE_ERR_ALLOC" not in str(e.value)
+    finally:
+        lope.lope_set_option("fail_alloc", 0)
