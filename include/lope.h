@@ -346,8 +346,11 @@ lope_status lope_set_option(const char* name, int64_t value);
  * The per-block partial sums live in a 512 KiB array that is part of the
  * library image (held on every GPU that loads the library until the process
  * exits).  n must not exceed 2^28 elements (LOPE_ERR_INVALID otherwise).
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  All calls on a device share the
+ * The first call on a device looks up the array's device address, once, and
+ * keeps it for the life of the process; make that first call before any
+ * stream capture.  A device reset (cudaDeviceReset) unloads the array, so the
+ * kept address is no longer valid: do not call this entry point on a device
+ * after resetting it in the same process.  All calls on a device share the
  * array, so calls that overlap on the GPU race: order them on one stream or
  * synchronise between them.  Every element of the array that a call reads was
  * written earlier in that call, so results never depend on previous calls.

@@ -1045,18 +1045,20 @@ lope_status lope_apply_host(const lope_grid* grid, const lope_stencil* stencil,
   lope_status rs = check_pair(grid, stencil);
   if (rs != LOPE_OK) return rs;
   if (!host_in || !host_out || !dev_in) return fail(LOPE_ERR_INVALID, "NULL field array");
-  {  // every device-side argument is checked before the first copy is issued
+  const Geom& g = grid->g;
+  // every argument, host pointers included, is checked before the first copy is issued
+  for (int f = 0; f < g.nf; ++f)
+    if (!host_in[f] || !host_out[f]) return fail(LOPE_ERR_INVALID, "NULL host field pointer");
+  {
     Choice c;
     int64_t L = 0;
     if ((rs = prepare_apply(grid, stencil, dev_in, dev_out, dev_work, nsteps, nullptr, &c, &L)) !=
         LOPE_OK)
       return rs;
   }
-  const Geom& g = grid->g;
   const size_t bytes = size_t(npts(g)) * esize(g.dtype);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   for (int f = 0; f < g.nf; ++f) {
-    if (!host_in[f] || !host_out[f] || !dev_in[f]) return fail(LOPE_ERR_INVALID, "NULL field pointer");
     cudaError_t e = cudaMemcpyAsync(dev_in[f], host_in[f], bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (host to device)");
   }

@@ -72,3 +72,27 @@ def test_plan_log_one_line_per_distinct_plan(lope, capfd):
     assert "grid 96x200 f32 nf=1 bc=[dirichlet,periodic]" in lines[0]
     assert "jacobi5 r=1 euler" in lines[0] and "path=tma" in lines[0]
     assert "launches=3" in lines[0] and "path=direct" in lines[1]
+
+
+def test_forced_allocation_failure_then_next_call_runs(lope):
+    """fail_alloc = 1: the first apply fails with LOPE_ERR_ALLOC before any
+    CUDA call and computes nothing; the next apply runs normally."""
+    shape = (64, 128)
+    u = torch.rand(shape, device="cuda")
+    g = lope.Grid(shape, "f32", halo=1)
+    st = lope.Stencil.builtin("jacobi5", 0.2)
+    ref = lope.apply(g, st, u, nsteps=3)
+    torch.cuda.synchronize()
+    out = torch.full_like(u, -1.0)
+    lope.lope_set_option("fail_alloc", 1)
+    try:
+        with pytest.raises(lope.LopeError, match="LOPE_ERR_ALLOC"):
+            lope.apply(g, st, u, nsteps=3, out=out)
+        torch.cuda.synchronize()
+        assert bool((out == -1.0).all())
+        lope.apply(g, st, u, nsteps=3, out=out)
+        torch.cuda.synchronize()
+    finally:
+        lope.lope_set_option("fail_alloc", 0)
+    lope.sync_status()
+    assert torch.equal(out, ref)
