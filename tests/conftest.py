@@ -30,3 +30,23 @@ def lope():
 
     L.load()
     return L
+
+
+# Measured errors of the reduced-precision parity tests against the FP64
+# oracle, next to the bound each test asserts: one entry per configuration.
+# When LOPE_ERROR_REPORT names a file, the session writes them there as JSON.
+_ERRORS = {}
+
+
+@pytest.fixture(scope="session")
+def error_report():
+    return _ERRORS
+
+
+def pytest_sessionfinish(session, exitstatus):
+    path = os.environ.get("LOPE_ERROR_REPORT")
+    if path and _ERRORS:
+        import json
+
+        with open(path, "w") as fh:
+            json.dump(_ERRORS, fh, indent=1, sort_keys=True)

@@ -153,7 +153,7 @@ def test_box_linear_tma_fp64_and_bitwise(lope, orc, r, bc):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_full_size_swe_flux_4096_200_sampled(lope, orc, dtype):
+def test_full_size_swe_flux_4096_200_sampled(lope, orc, dtype, error_report):
     """Nonlinear shallow water at 4096^2 x 3 fields, 200 steps, periodic.
     Sampled points are checked against the oracle on their domain of
     dependence.  FP32: the stated bound 2e-4 (linearised growth <= 1.4 over 200
@@ -170,5 +170,7 @@ def test_full_size_swe_flux_4096_200_sampled(lope, orc, dtype):
     M = max(np.max(np.abs(s)) for s in stored)
     tol = (lambda k, w: 2e-4) if dtype == "f32" else (lambda k, w: 1.4 * T * (2.0 ** -9) * M)
     pts = [(0, 0), (4095, 4095), (2048, 17), (9, 3000)]
-    _sampled_check(lope, orc, "swe_flux", PRM, shape, [0, 0], T, 1, dtype, 3, outs,
-                   list(stored), pts, tol)
+    worst = _sampled_check(lope, orc, "swe_flux", PRM, shape, [0, 0], T, 1, dtype, 3, outs,
+                           list(stored), pts, tol)
+    error_report[f"F1 swe_flux {dtype.upper()} 4096^2 x200 (sampled)"] = {
+        "max_abs": worst, "bound": tol(0, 0.0)}

@@ -13,7 +13,8 @@ import pytest
 import torch
 
 import lope_inputs as LI
-from gpu_helpers import bound_f32, normwise, to_device, to_host
+from error_bounds import gray_scott_majorant
+from gpu_helpers import normwise, to_device, to_host
 from user_bodies import DIFF7, GRAY_SCOTT, GRAY_SCOTT_PRM, JACOBI5, SWE_FLUX
 
 pytestmark = pytest.mark.gpu
@@ -114,19 +115,25 @@ def test_gray_scott_fp64_vs_oracle_every_path(lope, orc, scheme, bc, bval):
             assert normwise(to_host(outs[k]), want[k]) <= 1e-12, (launch, k)
 
 
-def test_gray_scott_f32_bound_and_paths_bitwise(lope, orc):
+def test_gray_scott_f32_bound_and_paths_bitwise(lope, orc, error_report):
+    """FP32 Gray-Scott against the oracle within the elementwise first-order
+    bound of error_bounds.py (local error from the body's operation tree,
+    carried by |J_t| along the oracle's trajectory; below 1e-3 here)."""
     shape, T = (100, 200), 20
     fl = _gs_fields(1204, shape)
     dev, stored = zip(*(to_device(f, "f32") for f in fl))
     g = _grid(lope, shape, "f32", 1, [0, 0], nf=2)
     st = lope.Stencil.source(GRAY_SCOTT, ndim=2, radius=1, nfields=2, params=GRAY_SCOTT_PRM)
-    want = orc.apply_source(list(stored), GRAY_SCOTT, GRAY_SCOTT_PRM, T)
-    # one step's Jacobian, infinity norm, for 0 <= u, v <= 1: diffusion part
-    # |1 - 4 D dt| + 4 D dt = 1 and reaction derivatives bounded by dt (F + 3)
-    G = 1 + GRAY_SCOTT_PRM[0] * (GRAY_SCOTT_PRM[3] + GRAY_SCOTT_PRM[4] + 3)
+    B, want = gray_scott_majorant(orc, GRAY_SCOTT, GRAY_SCOTT_PRM, list(stored), T)
+    assert max(float(np.max(b)) for b in B) < 1e-3
     ref = _run(lope, g, st, list(dev), T, _launch(lope, TMA))
+    worst = []
     for k in range(2):
-        assert np.max(np.abs(to_host(ref[k]) - want[k])) <= bound_f32(T, 1.0, 12, G), k
+        err = np.abs(to_host(ref[k]) - want[k])
+        worst.append(float(np.max(err)))
+        assert np.all(err <= B[k]), (k, float(np.max(err / B[k])))
+    error_report["F4 Gray-Scott source FP32 100x200 x20"] = {
+        "max_abs": worst, "bound": [float(np.max(b)) for b in B]}
     for launch in (_launch(lope, TRAP, 64, 32, 2), _launch(lope, DIRECT)):
         outs = _run(lope, g, st, list(dev), T, launch)
         for k in range(2):

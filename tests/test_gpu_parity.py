@@ -11,6 +11,7 @@ import pytest
 import torch
 
 import lope_inputs as LI
+from error_bounds import growth, impulse_norms, local_eps, sup_bound
 from gpu_helpers import bound_bf16, bound_f32, normwise, sub_box, to_device, to_host
 
 pytestmark = pytest.mark.gpu
@@ -37,14 +38,20 @@ def _run(L, g, st, fields, nsteps, launch=None):
 
 # ------------------------------------------------------------------ K1: FP64, 1e-12
 @pytest.mark.parametrize("path", [0, TMA, TRAP, DIRECT])
-def test_jacobi5_fp64_256_periodic_100(lope, orc, path):
+def test_jacobi5_fp64_256_periodic_100(lope, orc, path, error_report):
     shape, c, T = (256, 256), 0.2, 100
     u0, u0s = to_device(LI.uniform_field(1000, shape), "f64")
     g = _grid(lope, shape, "f64", 1, [0, 0])
     st = lope.Stencil.builtin("jacobi5", c)
     got = to_host(_run(lope, g, st, u0, T, None if path == 0 else _launch(lope, path, k=1)))
     want = orc.apply(u0s, "jacobi5", [c], T)
-    assert normwise(got, want) <= 1e-12
+    rel = normwise(got, want)
+    key = "K1 jacobi5 FP64 256^2 x100 (normwise relative, every path)"
+    prev = error_report.get(key, {}).get("normwise", 0.0)
+    error_report[key] = {"normwise": max(prev, rel), "bound": 1e-12,
+                         "max_abs": max(error_report.get(key, {}).get("max_abs", 0.0),
+                                        float(np.max(np.abs(got - want))))}
+    assert rel <= 1e-12
 
 
 def test_jacobi5_fp64_all_paths_bitwise(lope):
@@ -162,24 +169,33 @@ def test_linear_asymmetric_fp64(lope, orc, ndim, r, box):
 
 
 # ------------------------------------------------------------------ multi-field
-def test_swe_f32_and_bf16(lope, orc):
+def test_swe_f32_and_bf16(lope, orc, error_report):
+    """Small linear shallow-water runs on every path against the derived
+    sup-norm and mean bounds (see test_full_size_swe_4096_200_sampled)."""
     shape, T = (40, 72), 20
-    dt, gr, H = 0.02, 1.0, 1.0
+    prm = [0.02, 1.0, 1.0]
     h, u, v = LI.swe_fields(1002, shape)
-    st = lope.Stencil.builtin("swe_cgrid", dt, gr, H)
-    G = 1 + 4 * dt  # ||G||_inf of one step
+    st = lope.Stencil.builtin("swe_cgrid", *prm)
+    norms = impulse_norms(orc, "swe_cgrid", prm, 3, 2, 1, T)
     # FP32 stores h; BF16 stores eta = h - H (perturbation storage)
-    for dtype, first in (("f32", h), ("bf16", h - H)):
+    for dtype, first in (("f32", h), ("bf16", h - 1.0)):
         dev, stored = zip(*(to_device(f, dtype) for f in (first, u, v)))
         g = _grid(lope, shape, dtype, 1, [0, 0], nf=3)
+        _, M, D = _stepwise_swe(lope, g, st, dev, T)
+        eps = local_eps("swe_cgrid", prm, M, dtype, dh=D)
+        sup = sup_bound(norms, eps)
+        want = orc.apply(list(stored), "swe_cgrid", prm, T)
+        worst = [0.0] * 3
         for launch in (None, _launch(lope, TRAP, 64, 32, 2), _launch(lope, DIRECT)):
             outs = _run(lope, g, st, list(dev), T, launch)
-            want = orc.apply(list(stored), "swe_cgrid", [dt, gr, H], T)
-            M = max(np.max(np.abs(w)) for w in want)
             for k in range(3):
                 got = to_host(outs[k])
-                bound = bound_f32(T, M, 6, G) if dtype == "f32" else bound_bf16(T, M, 6, G)
-                assert np.max(np.abs(got - want[k])) <= bound, (dtype, k, launch)
+                err = float(np.max(np.abs(got - want[k])))
+                worst[k] = max(worst[k], err)
+                assert err <= sup[k], (dtype, k, launch, err, sup[k])
+                assert abs(np.mean(got) - np.mean(stored[k])) <= T * eps[k], (dtype, k, launch)
+        error_report[f"K4 swe_cgrid {dtype.upper()} 40x72 x20 (every path)"] = {
+            "max_abs": worst, "bound": list(map(float, sup))}
 
 
 # ------------------------------------------------------------------ edge cases
@@ -260,8 +276,11 @@ def test_sum_conserved_periodic_on_gpu(lope):
 # ------------------------------------------------------------------ full-size, sampled
 def _sampled_check(lope, orc, kind, prm, shape, bc, T, R, dtype, nf_fields, got_fields, stored,
                    points, tol_fn):
+    """Compare sampled outputs with the oracle on their domains of dependence;
+    returns the largest error seen per field."""
     periodic = [b == 0 for b in bc]
     rho = R * T + 1
+    worst = [0.0] * nf_fields
     for p in points:
         idx, pos = sub_box(shape, p, rho, periodic)
         sub = [s[np.ix_(*idx)] for s in stored]
@@ -275,48 +294,127 @@ def _sampled_check(lope, orc, kind, prm, shape, bc, T, R, dtype, nf_fields, got_
         for k in range(nf_fields):
             w = want[k][pos]
             gv = float(got_fields[k][p].item())
+            worst[k] = max(worst[k], abs(gv - w))
             assert abs(gv - w) <= tol_fn(k, w), (p, k, gv, w)
+    return worst
 
 
-def test_full_size_diff7_512_dirichlet_50_sampled(lope, orc):
+def _scalar_bound(orc, kind, prm, ndim, R, T, M):
+    """Sup-norm bound of an FP32 run of a one-field builtin (error_bounds.py):
+    the local error of one step, from the operation tree, carried by the
+    impulse-response norms of the exact steps."""
+    norms = impulse_norms(orc, kind, prm, 1, ndim, R, T)
+    return float(sup_bound(norms, local_eps(kind, prm, [growth(norms) * M], "f32"))[0])
+
+
+def test_full_size_diff7_512_dirichlet_50_sampled(lope, orc, error_report):
     shape, c, T = (512, 512, 512), 0.1, 50
     u0, u0s = to_device(LI.uniform_field(1001, shape), "f32")
     g = _grid(lope, shape, "f32", 1, [1, 1, 1])
     st = lope.Stencil.builtin("diff7", c)
     out = _run(lope, g, st, u0, T)
+    bound = _scalar_bound(orc, "diff7", [c], 3, 1, T, np.max(np.abs(u0s)))
     pts = [(0, 0, 0), (511, 511, 511), (0, 255, 511), (256, 256, 256), (100, 3, 400), (511, 0, 7)]
-    _sampled_check(lope, orc, "diff7", [c], shape, [1, 1, 1], T, 1, "f32", 1, [out], [u0s], pts,
-                   lambda k, w: 3e-5)
+    worst = _sampled_check(lope, orc, "diff7", [c], shape, [1, 1, 1], T, 1, "f32", 1, [out], [u0s],
+                           pts, lambda k, w: bound)
+    error_report["K2 diff7 FP32 512^3 x50 (sampled)"] = {"max_abs": worst[0], "bound": bound}
 
 
-def test_full_size_star9r2_8192_periodic_50_sampled(lope, orc):
+def test_full_size_star9r2_8192_periodic_50_sampled(lope, orc, error_report):
     shape, c, T = (8192, 8192), 0.1, 50
     u0, u0s = to_device(LI.uniform_field(1001, shape, offset=1 << 32), "f32")
     g = _grid(lope, shape, "f32", 2, [0, 0])
     st = lope.Stencil.builtin("star9r2", c)
     out = _run(lope, g, st, u0, T)
+    bound = _scalar_bound(orc, "star9r2", [c], 2, 2, T, np.max(np.abs(u0s)))
     pts = [(0, 0), (8191, 8191), (0, 4096), (4000, 8191), (1234, 5678), (8190, 1)]
-    _sampled_check(lope, orc, "star9r2", [c], shape, [0, 0], T, 2, "f32", 1, [out], [u0s], pts,
-                   lambda k, w: 2.5e-4)
+    worst = _sampled_check(lope, orc, "star9r2", [c], shape, [0, 0], T, 2, "f32", 1, [out], [u0s],
+                           pts, lambda k, w: bound)
+    error_report["K3 star9r2 FP32 8192^2 x50 (sampled)"] = {"max_abs": worst[0], "bound": bound}
+
+
+def _full_field(lope, orc, kind, c, shape, bc, T, R, seed_args, error_report, key):
+    """The complete output of a headline workload against the oracle, element by
+    element (the oracle on every host core)."""
+    u0, u0s = to_device(LI.uniform_field(*seed_args), "f32")
+    g = _grid(lope, shape, "f32", R, bc)
+    st = lope.Stencil.builtin(kind, c)
+    out = to_host(_run(lope, g, st, u0, T))
+    del u0
+    want = orc.apply(u0s, kind, [c], T, bc=bc, nthreads=orc.max_threads())
+    err = float(np.max(np.abs(out - want)))
+    bound = _scalar_bound(orc, kind, [c], len(shape), R, T, np.max(np.abs(u0s)))
+    error_report[key] = {"max_abs": err, "bound": bound, "points": int(out.size)}
+    assert err <= bound, (err, bound)
+
+
+def test_full_field_diff7_512_dirichlet_50(lope, orc, error_report):
+    _full_field(lope, orc, "diff7", 0.1, (512, 512, 512), [1, 1, 1], 50, 1,
+                (1001, (512, 512, 512)), error_report, "K2 diff7 FP32 512^3 x50 (full field)")
+
+
+def test_full_field_star9r2_8192_periodic_50(lope, orc, error_report):
+    _full_field(lope, orc, "star9r2", 0.1, (8192, 8192), [0, 0], 50, 2,
+                (1001, (8192, 8192), 1 << 32), error_report,
+                "K3 star9r2 FP32 8192^2 x50 (full field)")
+
+
+def _stepwise_swe(lope, g, st, dev, T):
+    """The run one step at a time (bitwise the same as one call of T steps);
+    returns the final state, the largest magnitude of each field over all
+    states, and the largest neighbour difference of field 0 (the magnitudes the
+    local error bound of every step depends on)."""
+    cur = list(dev)
+    M = [float(x.float().abs().max()) for x in cur]
+
+    def maxdiff(x):
+        x = x.float()
+        return max(float((torch.roll(x, -1, d) - x).abs().max()) for d in (0, 1))
+
+    D = maxdiff(cur[0])
+    for _ in range(T):
+        cur = lope.apply(g, st, cur, nsteps=1)
+        M = [max(m, float(x.float().abs().max())) for m, x in zip(M, cur)]
+        D = max(D, maxdiff(cur[0]))
+    torch.cuda.synchronize()
+    return cur, M, D
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_full_size_swe_4096_200_sampled(lope, orc, dtype):
+def test_full_size_swe_4096_200_sampled(lope, orc, dtype, error_report):
+    """Linear C-grid shallow water at 4096^2 x 3 fields, 200 steps, periodic.
+    Sup-norm bound: the local error of one step (from the operation tree and
+    the magnitudes of the run's own states) carried by the impulse-response
+    norms of 200 exact steps (FP32 about 1e-4; BF16 storage has no useful
+    worst case at this length).  Mean bound: every field's mean is conserved
+    by the exact step, so the mean drifts by at most T eps per field, which a
+    bias of one ulp per step exceeds (FP32 and BF16)."""
     shape, T = (4096, 4096), 200
-    dt, gr, H = 0.02, 1.0, 1.0
+    prm = [0.02, 1.0, 1.0]
     h, u, v = LI.swe_fields(1002, shape)
-    first = h if dtype == "f32" else h - H
+    first = h if dtype == "f32" else h - 1.0
     dev, stored = zip(*(to_device(f, dtype) for f in (first, u, v)))
     g = _grid(lope, shape, dtype, 1, [0, 0], nf=3)
-    st = lope.Stencil.builtin("swe_cgrid", dt, gr, H)
+    st = lope.Stencil.builtin("swe_cgrid", *prm)
     outs = _run(lope, g, st, list(dev), T)
-    G = 1 + 4 * dt
-    M = max(np.max(np.abs(s)) for s in stored) * 1.5
-    tol = (lambda k, w: bound_f32(T, M, 6, G)) if dtype == "f32" else (
-        lambda k, w: bound_bf16(T, M, 6, G))
+    steps, M, D = _stepwise_swe(lope, g, st, dev, T)
+    for k in range(3):
+        assert torch.equal(steps[k], outs[k]), k
+    norms = impulse_norms(orc, "swe_cgrid", prm, 3, 2, 1, T)
+    eps = local_eps("swe_cgrid", prm, M, dtype, dh=D)
+    sup = sup_bound(norms, eps)
     pts = [(0, 0), (4095, 4095), (2048, 17), (9, 3000)]
-    _sampled_check(lope, orc, "swe_cgrid", [dt, gr, H], shape, [0, 0], T, 1, dtype, 3, outs,
-                   list(stored), pts, tol)
+    worst = _sampled_check(lope, orc, "swe_cgrid", prm, shape, [0, 0], T, 1, dtype, 3, outs,
+                           list(stored), pts, lambda k, w: sup[k])
+    drift = []
+    for k in range(3):
+        m0 = float(np.mean(stored[k]))
+        m1 = float(lope.reduce_sum(outs[k]).item()) / outs[k].numel()
+        drift.append(abs(m1 - m0))
+        assert drift[k] <= T * eps[k], (k, drift[k], T * eps[k])
+    error_report[f"K4 swe_cgrid {dtype.upper()} 4096^2 x200 (sampled)"] = {
+        "max_abs": worst, "bound": list(map(float, sup)), "mean_drift": drift,
+        "mean_bound": list(map(float, T * eps))}
 
 
 # ------------------------------------------------------------------ planner / autotuner

@@ -153,7 +153,7 @@ def test_rk3_mass_conserved_swe_flux_on_gpu(lope):
     assert abs(a - b) <= 1e-13 * float(lope.reduce_sum(fl[0].abs()).item())
 
 
-def test_full_size_rk3_swe_flux_4096_sampled(lope, orc):
+def test_full_size_rk3_swe_flux_4096_sampled(lope, orc, error_report):
     """RK3 steps of the nonlinear shallow water at 4096^2, periodic, 50 steps
     (150 sweeps): sampled points against the oracle on their domain of
     dependence (R * stages * T cells).  Stated FP32 bound 1e-4 (150 sweeps of
@@ -167,13 +167,17 @@ def test_full_size_rk3_swe_flux_4096_sampled(lope, orc):
     st = lope.Stencil.builtin("swe_flux", *FLUX).set_scheme("rk3")
     outs = _run(lope, g, st, list(dev), T)
     rho = 3 * T + 1
+    worst = [0.0] * 3
     for p in [(0, 0), (4095, 4095), (2048, 17), (9, 3000)]:
         idx, pos = sub_box(shape, p, rho, [True, True])
         sub = [s[np.ix_(*idx)] for s in stored]
         want = orc.apply(sub, "swe_flux", FLUX, T, bc=[1, 1], scheme="rk3",
                          nthreads=orc.max_threads())
         for k in range(3):
-            assert abs(float(outs[k][p].item()) - want[k][pos]) <= 1e-4, (p, k)
+            err = abs(float(outs[k][p].item()) - want[k][pos])
+            worst[k] = max(worst[k], err)
+            assert err <= 1e-4, (p, k)
+    error_report["F2 RK3 swe_flux FP32 4096^2 x50 (sampled)"] = {"max_abs": worst, "bound": 1e-4}
 
 
 @pytest.mark.parametrize("scheme", ["rk2", "rk3"])

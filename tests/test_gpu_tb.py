@@ -1,0 +1,107 @@
+"""The two-sweep 3D z-march (TMA path, temporal depth 2).
+
+One launch applies the local function twice, keeping the intermediate state
+on chip; every sweep rounds to the storage precision, so the result must equal
+one sweep per launch bitwise (and the direct kernel), on grids with ragged
+tiles in every axis, Dirichlet-0 x and y sides, Dirichlet or periodic z, both
+tile heights, FP32 and BF16 storage, even and odd step counts (an odd count
+ends with a one-sweep launch).  One case per shape is checked against the FP64
+oracle within the derived bound, and the kernel writes only its output.
+"""
+import numpy as np
+import pytest
+import torch
+
+import lope_inputs as LI
+from error_bounds import local_eps
+from gpu_helpers import to_device, to_host
+
+pytestmark = pytest.mark.gpu
+
+TMA, DIRECT = 1, 3
+SHORT, TALL = 1, 2
+
+
+def _run(L, g, st, u, T, launch, out=None, work=None):
+    o = L.apply(g, st, u, out=out, work=work, nsteps=T, launch=launch)
+    torch.cuda.synchronize()
+    L.sync_status()
+    return o
+
+
+def _grid(L, shape, dtype, zbc):
+    g = L.Grid(shape, dtype, halo=1)
+    g.set_boundaries([zbc, 1, 1])
+    return g
+
+
+SHAPES = [(37, 50, 72), (40, 130, 136), (5, 64, 64), (70, 33, 200), (1, 8, 8)]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("zbc", [1, 0])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_two_sweeps_bitwise_equal_one_sweep(lope, orc, dtype, zbc, shape):
+    u0, u0s = to_device(LI.uniform_field(1700, shape), dtype)
+    g = _grid(lope, shape, dtype, zbc)
+    st = lope.Stencil.builtin("diff7", 0.1)
+    for T in (2, 7):
+        ref = _run(lope, g, st, u0, T, lope.Launch(TMA, 0, 0, 1, -1))
+        direct = _run(lope, g, st, u0, T, lope.Launch(DIRECT, 0, 0, 0, -1))
+        assert torch.equal(ref, direct)
+        for tile in (SHORT, TALL):
+            got = _run(lope, g, st, u0, T, lope.Launch(TMA, 0, tile, 2, -1))
+            assert torch.equal(got, ref), (T, tile)
+        if dtype == "f32" and T == 7:
+            want = orc.apply(u0s, "diff7", [0.1], T, bc=[zbc, 1, 1])
+            bound = T * float(local_eps("diff7", [0.1], [float(np.max(np.abs(u0s)))], "f32")[0])
+            assert np.max(np.abs(to_host(ref) - want)) <= bound
+
+
+def test_two_sweeps_linear_table_asymmetric(lope):
+    """An asymmetric radius-1 star table: any transposed tap shows up."""
+    w = np.zeros((3, 3, 3))
+    rng = np.random.default_rng(1701)
+    for ax in range(3):
+        for d in (0, 2):
+            idx = [1, 1, 1]
+            idx[ax] = d
+            w[tuple(idx)] = rng.uniform(0.02, 0.12)
+    w[1, 1, 1] = 1.0 - w.sum()
+    shape = (33, 70, 136)
+    u0, _ = to_device(LI.uniform_field(1702, shape), "f32")
+    st = lope.Stencil.linear(w)
+    for zbc in (0, 1):
+        g = _grid(lope, shape, "f32", zbc)
+        ref = _run(lope, g, st, u0, 6, lope.Launch(DIRECT, 0, 0, 0, -1))
+        for tile in (SHORT, TALL):
+            assert torch.equal(_run(lope, g, st, u0, 6, lope.Launch(TMA, 0, tile, 2, -1)), ref)
+
+
+def test_two_sweeps_refused_where_it_does_not_apply(lope):
+    shape = (16, 32, 64)
+    u0 = torch.rand(shape, device="cuda")
+    st = lope.Stencil.builtin("diff7", 0.1)
+    g = lope.Grid(shape, "f32", halo=1)  # periodic x and y: the one-sweep march only
+    with pytest.raises(lope.LopeError, match="UNSUPPORTED"):
+        lope.apply(g, st, u0, nsteps=4, launch=lope.Launch(TMA, 0, 0, 2, -1))
+    g.set_boundaries([1, 1, 1], [0.0, 0.5, 0.0])  # non-zero Dirichlet value
+    with pytest.raises(lope.LopeError, match="UNSUPPORTED"):
+        lope.apply(g, st, u0, nsteps=4, launch=lope.Launch(TMA, 0, 0, 2, -1))
+
+
+def test_two_sweeps_write_only_their_output(lope):
+    shape = (21, 70, 136)
+    n = int(np.prod(shape))
+    guard, sentinel = 4096, -7.0e30
+    u0, _ = to_device(LI.uniform_field(1703, shape), "f32")
+    keep = u0.clone()
+    g = _grid(lope, shape, "f32", 1)
+    st = lope.Stencil.builtin("diff7", 0.1)
+    bufs = [torch.full((n + 2 * guard,), sentinel, device="cuda") for _ in range(2)]
+    out, work = (b[guard:guard + n].view(shape) for b in bufs)
+    for tile in (SHORT, TALL):
+        _run(lope, g, st, u0, 5, lope.Launch(TMA, 0, tile, 2, -1), out=out, work=work)
+        for b in bufs:
+            assert bool((b[:guard] == sentinel).all()) and bool((b[guard + n:] == sentinel).all())
+        assert torch.equal(u0, keep)
