@@ -252,7 +252,7 @@ def main():
                     help="run one kernel workload for --steps launches and exit (for ncu): "
                          "diff7:N, diff7p:N, star9r2:N, jacobi5:N, swe:N, swebf16:N, with an "
                          "optional boundary spec per axis, slowest first, e.g. diff7:512:DDP "
-                         "(D Dirichlet 0, P periodic)")
+                         "(D Dirichlet 0, P periodic), and :k2 for two sweeps per launch")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -338,14 +338,13 @@ def main():
     h_o2 = [torch.empty_like(u2_h).pin_memory() for _ in range(nset)]
     d3 = [(u3, o3, w3)] + [tuple(torch.empty_like(u3) for _ in range(3)) for _ in range(nset - 1)]
     d2 = [(u2, o2, w2)] + [tuple(torch.empty_like(u2) for _ in range(3)) for _ in range(nset - 1)]
-    st3 = [torch.cuda.Stream(dev) for _ in range(nset)]
-    st2 = [torch.cuda.Stream(dev) for _ in range(nset)]
+    sts = [torch.cuda.Stream(dev) for _ in range(nset)]
     e2e_steps = max(4, args.steps // 2)
 
     def e2e_step(i):
         k = i % nset
-        L.apply_host(g3, s3, u3_h, h_o3[k], d3[k][0], d3[k][1], d3[k][2], nsteps=T3, stream=st3[k])
-        L.apply_host(g2, s2, u2_h, h_o2[k], d2[k][0], d2[k][1], d2[k][2], nsteps=T2, stream=st2[k])
+        L.apply_host(g3, s3, u3_h, h_o3[k], d3[k][0], d3[k][1], d3[k][2], nsteps=T3, stream=sts[k])
+        L.apply_host(g2, s2, u2_h, h_o2[k], d2[k][0], d2[k][1], d2[k][2], nsteps=T2, stream=sts[k])
 
     e2e_step(0)  # warm-up of the host-buffer path
     e2e_step(1)
@@ -353,62 +352,86 @@ def main():
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for st_ in st3 + st2:
+    for st_ in sts:
         st_.wait_event(e0)
     for i in range(e2e_steps):
         e2e_step(i)
-    for st_ in st3 + st2:
+    for st_ in sts:
         stream.wait_stream(st_)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
-    # The same steps without the pipeline: each grid's steps on one stream, so
-    # a step's copies wait for the previous step's sweeps (copies overlap only
-    # the other grid's work).
+    # The same steps without the pipeline: all on one stream, so every copy
+    # waits for the sweeps before it.
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s0.record(stream)
-    st3[0].wait_event(s0)
-    st2[0].wait_event(s0)
+    sts[0].wait_event(s0)
     for _ in range(e2e_steps):
         e2e_step(0)
-    stream.wait_stream(st3[0])
-    stream.wait_stream(st2[0])
+    stream.wait_stream(sts[0])
     s1.record(stream)
     torch.cuda.synchronize()
     serial_ms = max_over_ranks(s0.elapsed_time(s1), pg, dev)
     e2e = {"value": upd_step * e2e_steps * ws / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": u3.numel() * 4 + u2.numel() * 4,
            "d2h_bytes_per_step": o3.numel() * 4 + o2.numel() * 4,
-           "api": "lope_apply_host per grid (pinned host buffers); steps pipelined over 2 streams "
-                  "and 2 device-buffer sets per grid",
+           "api": "lope_apply_host per grid (pinned host buffers); consecutive steps alternate "
+                  "between 2 streams and 2 device-buffer sets, so one step's copies overlap "
+                  "the other's sweeps",
            "steps": e2e_steps,
            "unpipelined_value": upd_step * e2e_steps * ws / (serial_ms / 1e3)}
     del d3, d2
 
     # ---------------- roofline of the dominant kernel (3D TMA z-march)
+    # The plan of each grid (path, temporal depth k, launches) comes from the
+    # library.  One launch reads each point once and writes it once (8 B per
+    # FP32 point) while it advances k sweeps, so its algorithmic bytes are
+    # 8 B x points and an update costs 8/k B; "effective" counts 8 B per update.
     peak, peak_kind = peaks()
-    alg3 = 8.0 * N3 ** 3  # one FP32 read + one FP32 write per point per launch
+    plan3, nl3 = L.plan(g3, s3, u3, o3, w3, nsteps=T3)
+    plan2, nl2 = L.plan(g2, s2, u2, o2, w2, nsteps=T2)
+    k3, k2 = plan3.tsteps, plan2.tsteps
+    alg3 = 8.0 * N3 ** 3
     alg2 = 8.0 * N2 ** 2
-    launch3_s = t3 / 1e3 / T3
-    launch2_s = t2 / 1e3 / T2
+    launch3_s = t3 / 1e3 / nl3
+    launch2_s = t2 / 1e3 / nl2
     ach3 = alg3 / launch3_s / 1e9
     ach2 = alg2 / launch2_s / 1e9
     tr = traffic_record()
+    name3 = ("tma3d_tb2_kernel<OpDiff7, float> (512^3, two sweeps per launch)" if k3 == 2 else
+             "tma3d_kernel<OpDiff7, float> (512^3, one sweep per launch)")
     roofline = {"bound": "hbm", "achieved": ach3, "peak": peak, "unit": "GB/s",
-                "frac": ach3 / peak, "traffic": tr["diff7_512_bytes_per_launch"] if tr else None,
-                "kernel": "tma3d_kernel<OpDiff7, float> (512^3, one sweep per launch)",
+                "frac": ach3 / peak,
+                "traffic": tr.get(f"diff7_512_k{k3}_bytes_per_launch") if tr else None,
+                "kernel": name3, "sweeps_per_launch": k3,
                 "alg_bytes_per_launch": alg3, "avg_launch_us": launch3_s * 1e6,
+                "effective_GBps": ach3 * k3, "effective_frac": ach3 * k3 / peak,
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
     kernels = {
-        "diff7_512": {"share_of_step": t3 / (t3 + t2), "avg_launch_us": launch3_s * 1e6,
-                      "alg_GBps": ach3, "frac_of_peak": ach3 / peak,
-                      "updates_per_s": N3 ** 3 / launch3_s},
-        "star9r2_8192": {"share_of_step": t2 / (t3 + t2), "avg_launch_us": launch2_s * 1e6,
+        "diff7_512": {"share_of_step": t3 / (t3 + t2), "sweeps_per_launch": k3, "launches": nl3,
+                      "avg_launch_us": launch3_s * 1e6, "alg_GBps": ach3, "frac_of_peak": ach3 / peak,
+                      "updates_per_s": N3 ** 3 * T3 / (t3 / 1e3)},
+        "star9r2_8192": {"share_of_step": t2 / (t3 + t2), "sweeps_per_launch": k2, "launches": nl2,
+                         "avg_launch_us": launch2_s * 1e6,
                          "alg_GBps": ach2, "frac_of_peak": ach2 / peak,
-                         "updates_per_s": N2 ** 2 / launch2_s,
+                         "updates_per_s": N2 ** 2 * T2 / (t2 / 1e3),
                          "traffic": tr.get("star9r2_8192_bytes_per_launch") if tr else None},
     }
+    # the one-sweep z-march on the same grid (the k = 1 form of the roofline
+    # gate), timed after the step
+    one = L.Launch(1, 0, 0, 1, -1)
+    L.apply(g3, s3, u3, out=o3, work=w3, nsteps=T3, launch=one)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    L.apply(g3, s3, u3, out=o3, work=w3, nsteps=T3, launch=one)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    k1_s = g0.elapsed_time(g1) / 1e3 / T3
+    kernels["diff7_512_one_sweep_per_launch"] = {
+        "avg_launch_us": k1_s * 1e6, "alg_GBps": alg3 / k1_s / 1e9,
+        "frac_of_peak": alg3 / k1_s / 1e9 / peak, "updates_per_s": N3 ** 3 / k1_s,
+        "traffic": tr.get("diff7_512_k1_bytes_per_launch") if tr else None}
 
     forms = {}
     if not args.main_only and rank == 0:
@@ -434,7 +457,8 @@ def main():
             "config": {"workload": WORKLOAD, "updates_per_step": upd_step,
                        "parallelism": f"replicas{ws}" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (512 MiB and 256 MiB per buffer); no flush",
-                       "launch": "lope_apply auto plan: TMA z-march (3D), TMA tiles (2D), k=1"},
+                       "launch": f"lope_apply auto plan: TMA z-march (3D, {k3} sweeps per launch), "
+                                 f"TMA tiles (2D, {k2} sweep per launch)"},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roofline,
             "kernels": kernels, "cpu_baseline": cpu, "forms": forms,
         }
@@ -454,6 +478,8 @@ def run_profile(args):
 
     B.build()
     parts = args.profile.split(":")
+    ksw = 2 if "k2" in parts[2:] else 1  # sweeps per launch (the two-sweep z-march)
+    parts = [q for q in parts if q != "k2"]
     name = parts[0]
     dims = [int(x) for x in parts[1].split("x")]
     n = dims[0]
@@ -492,13 +518,15 @@ def run_profile(args):
     fields = [torch.from_numpy(LI.uniform(1001, pts, k * pts).astype(np.float32).reshape(shape))
               .to(dev).to(tdt) for k in range(nf)]
     outs = [torch.empty_like(f) for f in fields]
+    works = [torch.empty_like(f) for f in fields]
+    launch = L.Launch(1, 0, 0, ksw, -1) if ksw == 2 else None
     for _ in range(args.warmup):
-        L.apply(g, st, fields, out=outs, nsteps=1)
+        L.apply(g, st, fields, out=outs, work=works, nsteps=ksw, launch=launch)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(args.steps):
-        L.apply(g, st, fields, out=outs, nsteps=1)
+        L.apply(g, st, fields, out=outs, work=works, nsteps=ksw, launch=launch)
     b.record()
     torch.cuda.synchronize()
     L.sync_status()

@@ -43,8 +43,16 @@ typedef enum { LOPE_F64 = 0, LOPE_F32 = 1, LOPE_BF16 = 2 } lope_dtype;
 
 /* Halo contents (Sec. 2.2 "Halo regions": the halo holds boundary-value
  * information).  PERIODIC is the paper's BC=CYCLIC (Sec. 3.2); DIRICHLET holds a
- * fixed value in the halo for every step. */
-typedef enum { LOPE_BC_PERIODIC = 0, LOPE_BC_DIRICHLET = 1 } lope_bc;
+ * fixed value in the halo for every step.  EXTERNAL (slowest axis only) is the
+ * halo of one slab of a decomposed grid, the data that HALO_TRANSFER brings
+ * from the neighbouring image (Sec. 3.2, Sec. 3.3): the input buffer must hold,
+ * right beyond the grid on that side, at least `radius` planes (3D) or rows
+ * (2D) of the neighbour's current state -- in[f] - radius * plane .. in[f] is
+ * read for the low side, the planes after the grid for the high side.  The
+ * caller refreshes them between sweeps (a halo exchange), so such a grid takes
+ * nsteps <= 1 per lope_apply; the TMA and direct kernels read it (trapezoid,
+ * plane march, batched, adjoint and multi-stage calls return UNSUPPORTED). */
+typedef enum { LOPE_BC_PERIODIC = 0, LOPE_BC_DIRICHLET = 1, LOPE_BC_EXTERNAL = 2 } lope_bc;
 
 typedef struct lope_grid lope_grid;
 typedef struct lope_stencil lope_stencil;
@@ -62,8 +70,10 @@ void lope_grid_destroy(lope_grid* grid);
 
 /* Boundary condition of one side of one axis (axis 0..ndim-1 slowest first, or
  * -1 for all axes; side 0 low, 1 high, -1 both).  A periodic axis must be
- * periodic on both sides.  Changing the boundary does not change the local
- * function (Sec. 3.4, first advantage).  value is the Dirichlet halo value. */
+ * periodic on both sides (setting one side of a periodic axis to another kind
+ * makes the other side Dirichlet 0).  EXTERNAL is accepted on axis 0 only.
+ * Changing the boundary does not change the local function (Sec. 3.4, first
+ * advantage).  value is the Dirichlet halo value. */
 lope_status lope_set_boundary(lope_grid* grid, int axis, int side, lope_bc kind, double value);
 
 /* Built-in local functions (Sec. 2.2, Fig. 1 and its generalisations):

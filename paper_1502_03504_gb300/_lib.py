@@ -21,6 +21,7 @@ _lib = None
 
 BC_PERIODIC = 0
 BC_DIRICHLET = 1
+BC_EXTERNAL = 2
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2}
 _ESIZE = {"f64": 8, "f32": 4, "bf16": 2}
 _STATUS = {0: "LOPE_OK", 1: "LOPE_ERR_INVALID", 2: "LOPE_ERR_UNSUPPORTED", 3: "LOPE_ERR_CUDA",
@@ -340,12 +341,14 @@ class Grid:
         self.handle = lope_grid_create(self.ndim, self.shape, hl, hl, DTYPES[dtype], nfields)
 
     def set_boundary(self, axis=-1, side=-1, kind="periodic", value=0.0):
-        k = BC_PERIODIC if kind in ("periodic", BC_PERIODIC) else BC_DIRICHLET
+        names = {"periodic": BC_PERIODIC, "dirichlet": BC_DIRICHLET, "external": BC_EXTERNAL}
+        k = names[kind] if isinstance(kind, str) else int(kind)
         lope_set_boundary(self.handle, axis, side, k, value)
         return self
 
     def set_boundaries(self, bc, bval=None):
-        """bc: list per axis of kind (0/1) or (low, high); bval likewise."""
+        """bc: list per axis of kind (0 periodic / 1 Dirichlet / 2 external) or
+        (low, high); bval likewise."""
         bval = bval if bval is not None else [0.0] * self.ndim
         for ax in range(self.ndim):
             k, v = bc[ax], bval[ax]

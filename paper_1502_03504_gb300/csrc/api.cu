@@ -123,10 +123,21 @@ lope_status check_pair(const lope_grid* grid, const lope_stencil* st) {
 // otherwise.
 int work_states(const StencilDesc& s) { return s.stages == 3 ? 2 : 1; }
 
+// Bytes of the caller's buffer an input reads beyond the grid on its external
+// sides (radius planes / rows each), before and after the grid.
+void external_pads(const Geom& g, int radius, size_t* before, size_t* after) {
+  const int sax = 3 - g.ndim;
+  const size_t slice = size_t(npts(g) / g.n[sax]) * esize(g.dtype);
+  *before = g.bc[sax][0] == kExternal ? size_t(radius) * slice : 0;
+  *after = g.bc[sax][1] == kExternal ? size_t(radius) * slice : 0;
+}
+
 lope_status check_fields(const Geom& g, const void* const* in, void* const* out, void* const* work,
-                         bool need_work, int wstates = 1) {
+                         bool need_work, int wstates = 1, int radius = 0) {
   if (!in || !out) return fail(LOPE_ERR_INVALID, "NULL field array");
   if (need_work && !work) return fail(LOPE_ERR_INVALID, "nsteps >= 2 needs work buffers");
+  size_t pad_lo = 0, pad_hi = 0;
+  external_pads(g, radius, &pad_lo, &pad_hi);
   for (int f = 0; f < g.nf; ++f) {
     if (!in[f] || !out[f]) return fail(LOPE_ERR_INVALID, "NULL field pointer");
     if (!aligned16(in[f]) || !aligned16(out[f])) return fail(LOPE_ERR_INVALID, "field pointer not 16-byte aligned");
@@ -138,8 +149,11 @@ lope_status check_fields(const Geom& g, const void* const* in, void* const* out,
       return x < y + nb && y < x + na;
     };
     const size_t wbytes = bytes * size_t(wstates);
+    // the input as read: the grid and its external halo planes
+    const void* in_read = static_cast<const char*>(in[f]) - pad_lo;
+    const size_t in_bytes = bytes + pad_lo + pad_hi;
     for (int h = 0; h < g.nf; ++h) {
-      if (overlap(in[f], bytes, out[h], bytes))
+      if (overlap(in_read, in_bytes, out[h], bytes))
         return fail(LOPE_ERR_INVALID, "out aliases in (double buffering required)");
       if (need_work && (overlap(work[f], wbytes, out[h], bytes) || overlap(work[f], wbytes, in[h], bytes)))
         return fail(LOPE_ERR_INVALID, "work aliases in or out");
@@ -160,9 +174,13 @@ std::mutex g_tune_mu;
 std::map<TuneKey, Choice> g_tune;
 
 TuneKey tune_key(const Geom& g, const StencilDesc& s) {
-  int bcs = 0;
+  int bcs = 0, ext = 0;
   for (int ax = 0; ax < 3; ++ax)
-    for (int sd = 0; sd < 2; ++sd) bcs = bcs * 2 + (g.bc[ax][sd] == kDirichlet);
+    for (int sd = 0; sd < 2; ++sd) {
+      bcs = bcs * 2 + (g.bc[ax][sd] == kDirichlet);
+      ext = ext * 2 + (g.bc[ax][sd] == kExternal);
+    }
+  bcs |= ext << 6;
   return TuneKey(g.ndim, g.n[0], g.n[1], g.n[2], g.dtype, s.kind, s.radius, int(s.star), bcs,
                  g.nf, s.stages, int64_t(reinterpret_cast<uintptr_t>(s.jit)));
 }
@@ -228,7 +246,19 @@ Choice default_choice(const Geom& g, const StencilDesc& s, int* err) {
     if (trap2d_supported(a)) return {kPathTrap, 64, 16, 4};
     a.ksteps = 1;
   }
+  if (g.ndim == 3 && s.stages == 1 && g.dtype == kF32 && npts(g) >= (int64_t(1) << 21)) {
+    // Two sweeps per launch on the z-march halve the HBM bytes per sweep.
+    // Measured on GB300, diff7 FP32 Dirichlet 0, 50 sweeps: 512^3 5.91 ms
+    // against 8.98 ms with one sweep per launch, 384^3 2.79 / 3.98 ms, 256^3
+    // 1.02 / 1.05 ms, 128^3 0.27 / 0.32 ms.  BF16 storage was slower at
+    // 512^3 (7.46 / 6.67 ms): its one-sweep march is far from the copy peak
+    // already, and the two-sweep tile is bound by instruction issue.
+    a.ksteps = 2;
+    if (tma_supported(a)) return {kPathTma, 0, 0, 2};
+    a.ksteps = 1;
+  }
   if (tma_supported(a)) return {kPathTma, 0, 0, 1};
+  if (has_external(g)) return {kPathDirect, 0, 0, 1};
   if (g.ndim == 2) {
     // Rows whose pitch is not a multiple of 16 bytes cannot be TMA-staged.
     // Trapezoid tiles fusing 4 sweeps measured 2.4x faster than one sweep per
@@ -299,7 +329,7 @@ void log_plan(const Geom& g, const StencilDesc& s, const Choice& c, int64_t nste
                                 "source"};
   static const char* dtypes[] = {"f64", "f32", "bf16"};
   static const char* paths[] = {"auto", "tma", "trapezoid", "direct", "march"};
-  static const char* bcs[] = {"periodic", "dirichlet"};
+  static const char* bcs[] = {"periodic", "dirichlet", "external"};
   std::vector<int64_t> key{g.ndim, g.n[0], g.n[1], g.n[2], g.dtype, g.nf, s.kind, s.radius,
                            s.stages, c.path, c.tile_x, c.tile_y, c.k, nsteps, graph};
   for (int ax = 0; ax < 3; ++ax) key.insert(key.end(), {g.bc[ax][0], g.bc[ax][1]});
@@ -315,8 +345,8 @@ void log_plan(const Geom& g, const StencilDesc& s, const Choice& c, int64_t nste
   std::string bc;
   for (int ax = 3 - g.ndim; ax < 3; ++ax) {
     if (ax > 3 - g.ndim) bc += ",";
-    bc += bcs[g.bc[ax][0] == kDirichlet];
-    if (g.bc[ax][1] != g.bc[ax][0]) bc += std::string("/") + bcs[g.bc[ax][1] == kDirichlet];
+    bc += bcs[g.bc[ax][0]];
+    if (g.bc[ax][1] != g.bc[ax][0]) bc += std::string("/") + bcs[g.bc[ax][1]];
   }
   std::fprintf(stderr,
                "lope: grid %s %s nf=%d bc=[%s] | %s r=%d %s | path=%s tile=%dx%d k=%d | "
@@ -485,11 +515,18 @@ lope_status prepare_apply(const lope_grid* grid, const lope_stencil* st, const v
     std::string err;
     if ((rs = jit_compile(st->jit, g.dtype, &err)) != LOPE_OK) return fail(rs, err);
   }
+  if (has_external(g)) {
+    // the caller refreshes an external halo between sweeps (a halo exchange)
+    if (nsteps > 1)
+      return fail(LOPE_ERR_INVALID, "a grid with an external halo takes one sweep per call");
+    if (s.stages != 1)
+      return fail(LOPE_ERR_UNSUPPORTED, "multi-stage schemes need a halo exchange per stage");
+  }
   if ((rs = resolve(g, s, in, cfg, nullptr, c)) != LOPE_OK) return rs;
   *L = nsteps == 0 ? 0 : (nsteps + c->k - 1) / c->k;
   const bool staged = s.stages >= 2 && c->path != kPathTrap;  // one launch per stage
   if (staged) *L = nsteps * s.stages;
-  return check_fields(g, in, out, work, staged ? nsteps >= 1 : *L >= 2, work_states(s));
+  return check_fields(g, in, out, work, staged ? nsteps >= 1 : *L >= 2, work_states(s), s.radius);
 }
 
 lope_status apply_impl(const lope_grid* grid, const lope_stencil* st, const void* const* in,
@@ -563,6 +600,8 @@ lope_status check_linear_for_adjoint(const lope_grid* grid, const lope_stencil* 
   const StencilDesc& s = st->s;
   if (s.kind == kSwe || s.kind == kSweFlux || s.kind == kUser)
     return fail(LOPE_ERR_UNSUPPORTED, "adjoint needs a single-field linear stencil");
+  if (has_external(grid->g))
+    return fail(LOPE_ERR_UNSUPPORTED, "adjoint of a grid with an external halo is not implemented");
   if (s.stages != 1) return fail(LOPE_ERR_UNSUPPORTED, "adjoint of a multi-stage scheme is not implemented");
   if (s.kind != kLinear) {
     for (int ax = 0; ax < 3; ++ax)
@@ -861,21 +900,28 @@ lope_status lope_set_boundary(lope_grid* grid, int axis, int side, lope_bc kind,
   if (!grid) return fail(LOPE_ERR_INVALID, "NULL grid");
   const int nd = grid->g.ndim;
   if (axis < -1 || axis >= nd || side < -1 || side > 1) return fail(LOPE_ERR_INVALID, "bad axis or side");
-  if (kind != LOPE_BC_PERIODIC && kind != LOPE_BC_DIRICHLET) return fail(LOPE_ERR_INVALID, "bad boundary kind");
+  if (kind != LOPE_BC_PERIODIC && kind != LOPE_BC_DIRICHLET && kind != LOPE_BC_EXTERNAL)
+    return fail(LOPE_ERR_INVALID, "bad boundary kind");
   if (kind == LOPE_BC_PERIODIC && side != -1) return fail(LOPE_ERR_INVALID, "periodic applies to both sides");
+  if (kind == LOPE_BC_EXTERNAL && axis != 0)
+    return fail(LOPE_ERR_INVALID, "an external halo belongs to the slowest axis (axis 0)");
   if (!std::isfinite(value)) return fail(LOPE_ERR_INVALID, "non-finite Dirichlet value");
   const int off = 3 - nd;
   for (int a = 0; a < nd; ++a) {
     if (axis != -1 && a != axis) continue;
     for (int sd = 0; sd < 2; ++sd) {
       if (side != -1 && sd != side) continue;
-      grid->g.bc[off + a][sd] = kind == LOPE_BC_PERIODIC ? kPeriodic : kDirichlet;
-      grid->g.bval[off + a][sd] = kind == LOPE_BC_PERIODIC ? 0.0 : value;
+      grid->g.bc[off + a][sd] = kind == LOPE_BC_PERIODIC ? kPeriodic
+                                : kind == LOPE_BC_EXTERNAL ? kExternal : kDirichlet;
+      grid->g.bval[off + a][sd] = kind == LOPE_BC_DIRICHLET ? value : 0.0;
     }
-    // an axis cannot be periodic on one side only
-    if (grid->g.bc[off + a][0] != grid->g.bc[off + a][1]) {
-      grid->g.bc[off + a][0] = grid->g.bc[off + a][1] = kDirichlet;
-    }
+    // an axis cannot be periodic on one side only: the other side becomes
+    // Dirichlet 0
+    for (int sd = 0; sd < 2; ++sd)
+      if (grid->g.bc[off + a][sd] == kPeriodic && grid->g.bc[off + a][1 - sd] != kPeriodic) {
+        grid->g.bc[off + a][sd] = kDirichlet;
+        grid->g.bval[off + a][sd] = 0.0;
+      }
   }
   return LOPE_OK;
 }
@@ -1146,6 +1192,8 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
     if (rs != LOPE_OK) return rs;
     if (grids[i]->g.ndim != 2 || grids[i]->g.nf != 1 || grids[i]->g.dtype != dtype)
       return fail(LOPE_ERR_INVALID, "batch grids must be 2D, single-field, same dtype");
+    if (has_external(grids[i]->g))
+      return fail(LOPE_ERR_UNSUPPORTED, "batched grids take periodic or Dirichlet boundaries");
     const void* in1[1] = {in[i]};
     void* out1[1] = {out[i]};
     void* work1[1] = {work ? work[i] : nullptr};

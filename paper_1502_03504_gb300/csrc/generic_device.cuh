@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(256) trap2d_rk_kernel(Op op, TrapGrid g, const
 // Taps of one output point.  A point whose whole halo box lies inside the
 // grid reads at constant offsets from its own index; any other point applies
 // the boundary rule per axis (a Dirichlet side gives its value; a periodic
-// side wraps by one period, since the radius never exceeds a periodic extent).
+// side wraps by one period, since the radius never exceeds a periodic extent;
+// an external side reads the caller's planes beyond the grid).
 template <class T, int NF>
 struct GlobalAcc {
   using C = C_t<T>;
@@ -67,10 +68,10 @@ struct GlobalAcc {
       const int n = int(g->n[ax]);
       if (q[ax] < 0) {
         if (g->bc[ax][0] == kDirichlet) return C(g->bval[ax][0]);
-        q[ax] += n;
+        if (g->bc[ax][0] == kPeriodic) q[ax] += n;
       } else if (q[ax] >= n) {
         if (g->bc[ax][1] == kDirichlet) return C(g->bval[ax][1]);
-        q[ax] -= n;
+        if (g->bc[ax][1] == kPeriodic) q[ax] -= n;
       }
     }
     return to_c(__ldg(f[fi] + (int64_t(q[0]) * g->n[1] + q[1]) * nx + q[2]));

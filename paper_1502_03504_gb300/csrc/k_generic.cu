@@ -11,8 +11,17 @@ size_t trap_smem_bytes(int dtype, int nf, int tile_x, int tile_y, int halo, int 
   return nbuf * size_t(nf) * size_t(tile_x + 2 * halo) * size_t(tile_y + 2 * halo) * csz;
 }
 
+// Whether any side of the grid reads an external halo (decomposed slabs);
+// only the TMA and direct kernels read those.
+bool has_external(const Geom& g) {
+  for (int ax = 0; ax < 3; ++ax)
+    for (int sd = 0; sd < 2; ++sd)
+      if (g.bc[ax][sd] == kExternal) return true;
+  return false;
+}
+
 bool trap2d_supported(const StepArgs& a) {
-  if (a.g.ndim != 2 || a.adjoint) return false;
+  if (a.g.ndim != 2 || a.adjoint || has_external(a.g)) return false;
   const int TX = a.tile_x > 0 ? a.tile_x : 64, TY = a.tile_y > 0 ? a.tile_y : 32;
   if (TX < 8 || TY < 1 || TX > 256 || TY > 256 || a.ksteps < 1 || a.ksteps > 8) return false;
   const int stages = std::max(1, a.s.stages);
@@ -25,7 +34,7 @@ bool direct_supported(const StepArgs& a) { return a.ksteps == 1; }
 bool march_supported(const StepArgs& a) {
   int blocks = 0, zchunk = 0;
   return a.g.ndim == 3 && !a.adjoint && a.s.kind != kUser && a.ksteps == 1 &&
-         march_geometry(a.g, &blocks, &zchunk);
+         !has_external(a.g) && march_geometry(a.g, &blocks, &zchunk);
 }
 
 cudaError_t launch_trap2d(const StepArgs& a) {

@@ -17,6 +17,13 @@ template <class T> cudaError_t dispatch_t(const StepArgs& a, int* blocks) {
       default: break;  // linear stencils: the caller passes reflected weights, no reduction
     }
   }
+  if (a.ksteps == 2) {  // two sweeps per launch: the 3D z-march with temporal blocking
+    if (!tb2_supported(a)) return cudaErrorNotSupported;
+    if (s.kind == kDiff7) return TmaRunner<OpDiff7, T, 3>::run_tb2(a, {s.prm[0]}, blocks);
+    OpStarLinear<3, 1> op;
+    for (int ax = 0; ax < 3; ++ax) for (int d = 0; d < 3; ++d) op.w[ax][d] = s.star_w[ax][d];
+    return TmaRunner<OpStarLinear<3, 1>, T, 3>::run_tb2(a, op, blocks);
+  }
   switch (s.kind) {
     case kJacobi5: return TmaRunner<OpJacobi5, T, 2>::run(a, {s.prm[0]}, blocks);
     case kStar9r2: return TmaRunner<OpStar9r2, T, 2>::run(a, {s.prm[0]}, blocks);
@@ -68,7 +75,8 @@ template <class T> cudaError_t dispatch_t(const StepArgs& a, int* blocks) {
 bool tma_supported(const StepArgs& a) {
   const Geom& g = a.g;
   const StencilDesc& s = a.s;
-  if (a.ksteps != 1 || s.radius < 1 || s.radius > 2) return false;
+  if (a.ksteps == 2 && !tb2_supported(a)) return false;
+  if (a.ksteps < 1 || a.ksteps > 2 || s.radius < 1 || s.radius > 2) return false;
   if ((s.kind == kSwe || s.kind == kSweFlux) && g.ndim != 2) return false;
   if (s.kind == kUser && (a.adjoint || !jit_tma_ok(static_cast<const JitProgram*>(s.jit)))) return false;
   if (!s.star && (g.ndim != 2 || a.adjoint)) return false;  // box stencils: 2D tiles only
@@ -79,6 +87,10 @@ bool tma_supported(const StepArgs& a) {
     if (g.n[ax] > (int64_t(1) << 30)) return false;
     for (int sd = 0; sd < 2; ++sd) {
       if (g.bc[ax][sd] == kDirichlet && g.bval[ax][sd] != 0.0 && !a.adjoint) return false;
+      // an external halo: slowest axis, one sweep per launch (the caller
+      // refreshes it between sweeps)
+      if (g.bc[ax][sd] == kExternal && (ax != 3 - g.ndim || a.ksteps != 1 || a.adjoint))
+        return false;
     }
     if (g.bc[ax][0] == kPeriodic && ax >= 3 - g.ndim && g.n[ax] < s.radius) return false;
   }

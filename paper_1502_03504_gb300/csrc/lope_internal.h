@@ -19,7 +19,11 @@ namespace lope {
 enum : int { kLinear = 0, kJacobi5 = 1, kDiff7 = 2, kStar9r2 = 3, kSwe = 4, kSweFlux = 5, kUser = 6 };
 constexpr int kUserParams = 8;  // parameters P[0..7] of a user-written local function
 enum : int { kF64 = 0, kF32 = 1, kBF16 = 2 };
-enum : int { kPeriodic = 0, kDirichlet = 1 };
+// Boundary kinds of one side of an axis.  kExternal (slowest axis only): the
+// halo is read from the input buffer beyond the grid, where the caller keeps
+// the neighbouring slab's planes (or rows) -- the destination of a halo
+// exchange between the slabs of a decomposed grid.
+enum : int { kPeriodic = 0, kDirichlet = 1, kExternal = 2 };
 enum : int { kPathAuto = 0, kPathTma = 1, kPathTrap = 2, kPathDirect = 3, kPathMarch = 4 };
 
 // Device error codes written to the error flag.
@@ -124,6 +128,7 @@ cudaError_t jit_launch(const StepArgs& a, int path);
 enum : int { kGenDirect = 0, kGenTrap = 1, kGenMarch = 2 };
 cudaError_t launch_generic_rk(const StepArgs& a, int kind, int* blocks);
 bool direct_supported(const StepArgs& a);
+bool has_external(const Geom& g);
 int tma_blocks(const StepArgs& a);
 int direct_blocks(const StepArgs& a);
 

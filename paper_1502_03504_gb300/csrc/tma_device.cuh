@@ -79,6 +79,9 @@ template <class Op, class T> struct TmaParams {
   int tiles_x, tiles_y;
   int zchunk;     // 3D: output planes per unit
   int nunits;     // number of work units
+  int soff;       // slowest-axis planes (3D) / rows (2D) the tensor maps hold
+                  // before the grid: the external halo of a slab (else 0)
+  int sext;       // external sides of the slowest axis: bit 0 low, bit 1 high
   double* partials;
   int* err;
 };
@@ -206,10 +209,11 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* m, int x,
 
 // Issue the copies of one tile/plane of every field into stage `st`.  BOX:
 // the wide box alone (box stencils patch wrapped halos themselves).
+// yoff: rows the 2D tensor maps hold before the grid (an external y halo).
 template <class T, int TX, int TY, int R, int NF, int RANK, bool BOX = false>
 __device__ __forceinline__ void issue_plane(const TmaMaps<NF>& maps, unsigned char* st,
                                             uint64_t* bar, const TileInfo& t, int z, int nx,
-                                            int ny) {
+                                            int ny, int yoff = 0) {
   using L = Layout<T, TX, TY, R, NF>;
   const uint32_t per_field =
       BOX ? L::WIDE_B
@@ -220,18 +224,21 @@ __device__ __forceinline__ void issue_plane(const TmaMaps<NF>& maps, unsigned ch
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     unsigned char* w = st + f * L::FIELD_B;
-    tma_load<RANK>(w, &maps.wide[f], xw, t.y0 - R, z, bar);
+    tma_load<RANK>(w, &maps.wide[f], xw, t.y0 - R + yoff, z, bar);
     if (BOX) continue;
-    if (t.xl) tma_load<RANK>(w + L::OFF_COLL, &maps.cols[f], nx - L::CW, t.y0, z, bar);
-    if (t.xr) tma_load<RANK>(w + L::OFF_COLR, &maps.cols[f], 0, t.y0, z, bar);
+    if (t.xl) tma_load<RANK>(w + L::OFF_COLL, &maps.cols[f], nx - L::CW, t.y0 + yoff, z, bar);
+    if (t.xr) tma_load<RANK>(w + L::OFF_COLR, &maps.cols[f], 0, t.y0 + yoff, z, bar);
     if (t.yl) tma_load<RANK>(w + L::OFF_ROWLO, &maps.rows[f], xw, ny - R, z, bar);
     if (t.yh) tma_load<RANK>(w + L::OFF_ROWHI, &maps.rows[f], xw, 0, z, bar);
   }
 }
 
+// Round a shared-memory pointer up to 128 bytes.  The offset is added to the
+// pointer itself (no round trip through an integer), so the compiler still
+// knows every pointer derived from it addresses shared memory and emits
+// shared loads and stores with 32-bit addresses.
 __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
-  return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 127) &
-                                          ~uintptr_t(127));
+  return p + ((128u - (smem_u32(p) & 127u)) & 127u);
 }
 
 // Sum an FP64 value over the consumer threads (named barrier 1) and add it to
@@ -510,8 +517,10 @@ __device__ __forceinline__ void tile2d_pair(const Op& op, unsigned char* st, T* 
 // position lies outside the grid on periodic axes only: those take the value
 // at the wrapped position.  Every other ring cell already holds the right
 // value from the TMA box (in-range data, or the zero fill past a Dirichlet
-// side).  The cells are enumerated as the 2R halo columns of the warp's body
-// rows, then its halo rows over the full box width; each lane takes K cells
+// side; past an external y side the box holds the caller's rows, and only a
+// corner that also crosses a periodic x side is rewritten, from the wrapped
+// column of those rows).  The cells are enumerated as the 2R halo columns of
+// the warp's body rows, then its halo rows over the full box width; each lane takes K cells
 // per pass and issues all their loads before any store, so a warp has up to
 // K * NF loads in flight.  Adjacent warps may write the same cell with the
 // same value.  The proxy fence orders these shared-memory writes before the
@@ -519,7 +528,7 @@ __device__ __forceinline__ void tile2d_pair(const Op& op, unsigned char* st, T* 
 template <class T, int TX, int TY, int R, int NF, int RY>
 __device__ __forceinline__ void fill_ring_warp(unsigned char* st, const TileInfo& t,
                                                const T* const* in, int nx, int ny, int per_x,
-                                               int per_y, int cy0) {
+                                               int per_y, int cy0, int ext_y = 0) {
   using L = Layout<T, TX, TY, R, NF>;
   constexpr int K = 4;
   const int lane = threadIdx.x % 32;
@@ -548,9 +557,11 @@ __device__ __forceinline__ void fill_ring_warp(unsigned char* st, const TileInfo
         }
         const int gy = t.y0 + tr, gx = t.x0 + tc;
         const bool oy = gy < 0 || gy >= ny, ox = gx < 0 || gx >= nx;
-        const bool need = c < n && (oy || ox) && (!oy || per_y) && (!ox || per_x);
+        const bool ey = (gy < 0 && (ext_y & 1)) || (gy >= ny && (ext_y & 2));
+        const bool need =
+            c < n && (oy || ox) && (!oy || per_y || (ey && ox)) && (!ox || per_x);
         si[k] = need ? (R + tr) * L::W + L::CW + tc : -1;
-        gi[k] = need ? int64_t(oy ? wrap(gy, ny) : gy) * nx + (ox ? wrap(gx, nx) : gx) : 0;
+        gi[k] = need ? int64_t(oy && !ey ? wrap(gy, ny) : gy) * nx + (ox ? wrap(gx, nx) : gx) : 0;
       }
       T v[K][NF];
 #pragma unroll
@@ -610,7 +621,7 @@ __global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32)
         const TileInfo t = classify<T, TX, TY, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx,
                                               p.ny, WRAP && p.per_x, WRAP && p.per_y);
         issue_plane<T, TX, TY, R, NF, 2, !Op::STAR>(maps, smem + s * L::STAGE_B, &full[s], t, 0,
-                                                    p.nx, p.ny);
+                                                    p.nx, p.ny, p.soff);
       }
       if (abort_flag) {  // let copies already issued land before the block exits
         for (int k = max(0, i - S); k < i; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
@@ -637,7 +648,8 @@ __global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32)
       // every tap (corners included) reads the box.
       static_assert(CPR == 32, "a warp spans the tile width");
       if (WRAP && (t.xl || t.xr || t.yl || t.yh))
-        fill_ring_warp<T, TX, TY, R, NF, RY>(st, t, p.in, p.nx, p.ny, p.per_x, p.per_y, cy0);
+        fill_ring_warp<T, TX, TY, R, NF, RY>(st, t, p.in, p.nx, p.ny, p.per_x, p.per_y, cy0,
+                                             p.sext);
       if constexpr (PAIR)
         tile2d_pair<false, false, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
       else
@@ -895,7 +907,8 @@ __global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32, 2)
         if (abort_flag) break;
         int z = z0 - R + j;
         if (p.per_z) z = wrap(z, p.nz);
-        issue_plane<T, TX, TY, R, NF, 3>(maps, smem + s * L::STAGE_B, &full[s], t, z, p.nx, p.ny);
+        issue_plane<T, TX, TY, R, NF, 3>(maps, smem + s * L::STAGE_B, &full[s], t, z + p.soff, p.nx,
+                                         p.ny);
       }
       if (abort_flag) {  // let copies already issued land before the block exits
         for (int k = max(0, j - S); k < j; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
@@ -932,6 +945,274 @@ __global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32, 2)
   }
 #undef LOPE_MARCH
   if (Op::REDUCES) block_accumulate<NCONS>(red, p.partials, red_scratch);
+}
+
+// ------------------------------------------------------------------ 3D z-march, two sweeps
+// Temporal blocking of depth 2 on the paired z-march: one launch applies the
+// local function twice (the fusion latitude of Sec. 3.5) while staging each
+// input plane from HBM once, so a sweep costs half the HBM bytes of the
+// one-sweep march.  For radius-1 star functions of one field on grids whose x
+// and y sides are Dirichlet 0: the TMA zero fill is then the halo of the
+// input, and the intermediate state u1 is set to the halo value 0 outside the
+// grid (a periodic z axis is staged from wrapped planes).
+//
+// Each input plane is staged with a 2-row / 16-byte-column halo.  Every
+// consumer warp owns RY rows x 64 columns of the tile (pairs of columns per
+// lane) and keeps, in a private three-plane ring of shared-memory slots, u1
+// on its rows, the row above and the row below them (computed again by the
+// neighbouring warps: no block-wide barrier) and the column pairs just left
+// and right of the tile.  Per staged plane j a warp
+//   * pushes u0(j) of its cells onto its register queue,
+//   * computes u1 at plane j-1: own cells from the queue and the staged box,
+//     the extra rows and columns from three staged planes, rounded to the
+//     storage precision as a stored sweep would be (bitwise the one-sweep
+//     result), and writes them to its slot,
+//   * computes u2 at plane j-2 from the u1 register queue and the slot of
+//     plane j-2, and stores it.
+template <bool B> struct BoolTag { static constexpr bool value = B; };
+
+template <class S_, int WS>
+struct Tb2Acc {  // x taps from a buffer of row stride WS, y taps and centre from column registers
+  const S_* b;
+  const F2* col;  // col[1 + dy]
+  F2 zm, zp;      // the planes below and above
+  __device__ __forceinline__ F2 operator()(int, int dx, int dy, int dz) const {
+    if (dz != 0) return dz < 0 ? zm : zp;
+    if (dx == 0) return col[1 + dy];
+    const F2 c = col[1];
+    if (dx == -1) return F2::make(ld_pair(b - 2).hi(), c.lo());
+    return F2::make(c.hi(), ld_pair(b + 2).lo());
+  }
+  __device__ __forceinline__ int64_t gidx() const { return 0; }
+};
+
+template <int V> struct IntTag { static constexpr int value = V; };
+
+template <class S_, int WS>
+struct Tb2SmemAcc {  // every tap from three staged planes (centre c, below lo, above hi)
+  const S_* c;
+  const S_* lo;
+  const S_* hi;
+  __device__ __forceinline__ F2 operator()(int, int dx, int dy, int dz) const {
+    if (dz == -1) return ld_pair(lo);
+    if (dz == 1) return ld_pair(hi);
+    const S_* rb = c + dy * WS;
+    if (dx == 0) return ld_pair(rb);
+    if (dx == -1) return F2::make(ld_pair(rb - 2).hi(), ld_pair(rb).lo());
+    return F2::make(ld_pair(rb).hi(), ld_pair(rb + 2).lo());
+  }
+  __device__ __forceinline__ int64_t gidx() const { return 0; }
+};
+
+__device__ __forceinline__ void st_pair_f(float* p, F2 v) { *reinterpret_cast<uint64_t*>(p) = v.v; }
+
+// The value a stored sweep would hold (identity for FP32; BF16 rounds).
+template <class T> __device__ __forceinline__ F2 stored_pair(F2 v) { return v; }
+template <> __device__ __forceinline__ F2 stored_pair<__nv_bfloat16>(F2 v) {
+  return F2::make(__bfloat162float(__float2bfloat16_rn(v.lo())),
+                  __bfloat162float(__float2bfloat16_rn(v.hi())));
+}
+
+template <int TX, int TY, int RY> struct Tb2Slots {
+  static constexpr int W1 = TX + 8;     // columns -4 .. TX+3 (floats)
+  static constexpr int SR = RY + 2;     // tile rows cy0-1 .. cy0+RY
+  static constexpr int SLOT = SR * W1;  // floats per plane slot
+  static constexpr int NW = TY / RY;    // consumer warps
+  static constexpr uint32_t BYTES = uint32_t(NW) * 3 * SLOT * sizeof(float);
+};
+
+template <class Op, class T, int TX, int TY, int RY, int S>
+__global__ void __launch_bounds__((TX / 2) * (TY / RY) + 32, 1)
+    tma3d_tb2_kernel(const __grid_constant__ TmaMaps<1> maps, const TmaParams<Op, T> p) {
+  static_assert(Op::R == 1 && Op::NF == 1 && Op::STAR && TX == 64, "radius-1 star, one field");
+  constexpr int H = 2;  // staged halo rows: two sweeps of radius 1
+  using L = Layout<T, TX, TY, H, 1>;
+  using SL = Tb2Slots<TX, TY, RY>;
+  constexpr int NCONS = 32 * SL::NW, W = L::W, CW = L::CW, W1 = SL::W1;
+  constexpr uint32_t STAGE = L::OFF_COLL;  // the wide box alone (no wrapped-halo slots)
+  static_assert(S >= 4, "ring too short for three planes and one in flight");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = align128(smem_raw);
+  float* slots = reinterpret_cast<float*>(smem + S * STAGE);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * STAGE + SL::BYTES);
+  uint64_t* empty = full + S;
+  __shared__ volatile int abort_flag;
+
+  const int tid = threadIdx.x;
+  const int ntiles = p.tiles_x * p.tiles_y;
+  const int tile = blockIdx.x % ntiles, zc = blockIdx.x / ntiles;
+  const TileInfo t = classify<T, TX, TY, H>((tile % p.tiles_x) * TX, (tile / p.tiles_x) * TY, p.nx,
+                                            p.ny, 0, 0);
+  const int z0 = zc * p.zchunk, z1 = min(p.nz, z0 + p.zchunk);
+  const int np = (z1 - z0) + 2 * H;  // planes staged by this block
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCONS / 32);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (z0 >= z1) return;
+
+  if (tid >= NCONS) {  // producer warp
+    if (tid == NCONS) {
+      tma_prefetch_desc(&maps.wide[0]);
+      int j = 0;
+      for (; j < np; ++j) {
+        const int s = j % S;
+        if (j >= S && !mbar_wait_bounded(&empty[s], ((j / S) & 1) ^ 1, p.err)) {
+          abort_flag = 1;
+          break;
+        }
+        if (abort_flag) break;
+        int z = z0 - H + j;
+        if (p.per_z) z = wrap(z, p.nz);
+        issue_plane<T, TX, TY, H, 1, 3, true>(maps, smem + s * STAGE, &full[s], t, z, p.nx, p.ny);
+      }
+      if (abort_flag) {  // let copies already issued land before the block exits
+        for (int k = max(0, j - S); k < j; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
+      }
+    }
+    return;
+  }
+
+  const int lane = tid % 32, warp = tid / 32;
+  const int cx2 = lane * 2, cy0 = warp * RY;
+  float* myslots = slots + warp * 3 * SL::SLOT;
+  const int64_t plane = int64_t(p.nx) * p.ny;
+  const bool xin = t.x0 + cx2 < p.nx;  // nx is even: a pair is all in or all out
+  auto stage = [&](int j) { return reinterpret_cast<const T*>(smem + (j % S) * STAGE); };
+  auto release = [&](int j) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[j % S]);
+  };
+  // inside the grid in x and y (tile row tr, tile column tc of a pair)
+  auto inside = [&](int tr, int tc) {
+    const int gy = t.y0 + tr, gx = t.x0 + tc;
+    return gy >= 0 && gy < p.ny && gx >= 0 && gx < p.nx;
+  };
+  // A warp whose cells, extra rows or side columns leave the grid in x or y
+  // masks them to the Dirichlet value 0; the others compile without masks.
+  const bool edge = t.x0 == 0 || t.y0 + cy0 == 0 || t.x0 + TX + 2 > p.nx ||
+                    t.y0 + cy0 + RY + 1 > p.ny;
+  T* outp = p.out[0] + int64_t(z0) * plane + int64_t(t.y0 + cy0) * p.nx + t.x0 + cx2;
+
+  // Register queues, rotated by renaming: the plane loop is unrolled by 3, so
+  // plane j's u0 sits in q0[j % 3] and u1 of plane j in q1[j % 3].
+  F2 q0[3][RY];
+  F2 q1[3][RY];
+  bool ok = true;
+  auto step = [&](auto ph_tag, auto edge_tag, int j) {
+    constexpr int PH = decltype(ph_tag)::value;  // j % 3
+    constexpr bool EDGE = decltype(edge_tag)::value;
+    constexpr int P1 = (PH + 2) % 3, P2 = (PH + 1) % 3;  // (j-1) % 3, (j-2) % 3
+    if (!mbar_wait_bounded(&full[j % S], (j / S) & 1, p.err) || abort_flag) {
+      abort_flag = 1;
+      ok = false;
+      return;
+    }
+    const T* bj = stage(j);
+#pragma unroll
+    for (int r = 0; r < RY; ++r) q0[PH][r] = ld_pair(bj + (H + cy0 + r) * W + CW + cx2);
+    if (j < 2) return;
+    // ---- u1 at plane j-1
+    const int zg = z0 - H + (j - 1);
+    const bool zout = !p.per_z && (zg < 0 || zg >= p.nz);  // Dirichlet-0 plane: u1 = 0
+    const T* bc = stage(j - 1);
+    const T* blo = stage(j - 2);
+    float* s1 = myslots + P1 * SL::SLOT;
+    if (zout) {
+#pragma unroll
+      for (int r = 0; r < RY; ++r) {
+        q1[P1][r] = F2(0.f);
+        st_pair_f(s1 + (1 + r) * W1 + 4 + cx2, F2(0.f));
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) st_pair_f(s1 + (e ? RY + 1 : 0) * W1 + 4 + cx2, F2(0.f));
+      if (lane < 2 * SL::SR)
+        st_pair_f(s1 + (lane >> 1) * W1 + 4 + ((lane & 1) ? TX : -2), F2(0.f));
+    } else {
+      F2 col[RY + 2];
+      col[0] = ld_pair(bc + (H + cy0 - 1) * W + CW + cx2);
+      col[RY + 1] = ld_pair(bc + (H + cy0 + RY) * W + CW + cx2);
+#pragma unroll
+      for (int r = 0; r < RY; ++r) col[1 + r] = q0[P1][r];
+#pragma unroll
+      for (int r = 0; r < RY; ++r) {
+        Tb2Acc<T, W> acc{bc + (H + cy0 + r) * W + CW + cx2, col + r, q0[P2][r], q0[PH][r]};
+        F2 o[1];
+        F2 unused(0.f);
+        p.op(acc, o, unused);
+        F2 v = stored_pair<T>(o[0]);
+        if constexpr (EDGE)
+          if (!(xin && t.y0 + cy0 + r < p.ny)) v = F2(0.f);
+        q1[P1][r] = v;
+        st_pair_f(s1 + (1 + r) * W1 + 4 + cx2, v);
+      }
+      // the rows above and below the warp's rows, and the column pairs beside
+      // the tile on all of them, from the three staged planes
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int tr = e ? cy0 + RY : cy0 - 1;
+        const int off = (H + tr) * W + CW + cx2;
+        Tb2SmemAcc<T, W> acc{bc + off, blo + off, bj + off};
+        F2 o[1];
+        F2 unused(0.f);
+        p.op(acc, o, unused);
+        F2 v = stored_pair<T>(o[0]);
+        if constexpr (EDGE)
+          if (!inside(tr, cx2)) v = F2(0.f);
+        st_pair_f(s1 + (e ? RY + 1 : 0) * W1 + 4 + cx2, v);
+      }
+      if (lane < 2 * SL::SR) {
+        const int row = lane >> 1, tc = (lane & 1) ? TX : -2;
+        const int tr = cy0 - 1 + row;
+        const int off = (H + tr) * W + CW + tc;
+        Tb2SmemAcc<T, W> acc{bc + off, blo + off, bj + off};
+        F2 o[1];
+        F2 unused(0.f);
+        p.op(acc, o, unused);
+        F2 v = stored_pair<T>(o[0]);
+        if constexpr (EDGE)
+          if (!inside(tr, tc)) v = F2(0.f);
+        st_pair_f(s1 + row * W1 + 4 + tc, v);
+      }
+    }
+    release(j - 2);  // u0 plane j-2 is no longer read (the __syncwarp also publishes s1)
+    if (j < 4) return;
+    // ---- u2 at plane j-2 (output plane z0 + j - 4)
+    const float* s2 = myslots + P2 * SL::SLOT;
+    F2 col[RY + 2];
+    col[0] = ld_pair(s2 + 4 + cx2);
+    col[RY + 1] = ld_pair(s2 + (RY + 1) * W1 + 4 + cx2);
+#pragma unroll
+    for (int r = 0; r < RY; ++r) col[1 + r] = q1[P2][r];
+    T* o_plane = outp + int64_t(j - 4) * plane;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      Tb2Acc<float, W1> acc{s2 + (1 + r) * W1 + 4 + cx2, col + r, q1[PH][r], q1[P1][r]};
+      F2 o[1];
+      F2 unused(0.f);
+      p.op(acc, o, unused);
+      if (!EDGE || (xin && t.y0 + cy0 + r < p.ny)) st_pair(o_plane + int64_t(r) * p.nx, o[0]);
+    }
+  };
+  auto march = [&](auto edge_tag) {
+    for (int j0 = 0; j0 < np && ok; j0 += 3) {
+      step(IntTag<0>(), edge_tag, j0);
+      if (ok && j0 + 1 < np) step(IntTag<1>(), edge_tag, j0 + 1);
+      if (ok && j0 + 2 < np) step(IntTag<2>(), edge_tag, j0 + 2);
+    }
+  };
+  if (edge) march(BoolTag<true>());
+  else march(BoolTag<false>());
+  if (ok) {
+    release(np - 2);
+    release(np - 1);
+  }
 }
 
 }  // namespace

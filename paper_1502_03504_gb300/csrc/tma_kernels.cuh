@@ -64,6 +64,32 @@ int sm_count() {
 constexpr int kZWaves = 3;
 constexpr int kMinChunk = 48;
 
+// Work split of the 3D z-march kernels: TX x TY tiles times z-chunks.  About
+// kZWaves waves of blocks keep every resident slot busy (later blocks take the
+// slots of blocks that finish early; edge tiles of periodic grids cost more
+// per plane), but chunks stay at least kMinChunk planes long (each chunk
+// stages its halo planes again); short grids get at most one wave (a few
+// blocks past a full wave would double the time).
+template <class P>
+void zmarch_geometry(const Geom& g, P& p, int* blocks, int TX, int TY, int slots) {
+  p.nx = int(g.n[2]);
+  p.ny = int(g.n[1]);
+  p.nz = int(g.n[0]);
+  p.per_x = g.bc[2][0] == kPeriodic;
+  p.per_y = g.bc[1][0] == kPeriodic;
+  p.per_z = g.bc[0][0] == kPeriodic;
+  p.tiles_x = (p.nx + TX - 1) / TX;
+  p.tiles_y = (p.ny + TY - 1) / TY;
+  const int ntiles = p.tiles_x * p.tiles_y;
+  const int one_wave = std::max(1, slots / ntiles);
+  int nzc = std::max(one_wave, std::min((kZWaves * slots) / ntiles, p.nz / kMinChunk));
+  nzc = std::min(nzc, p.nz);
+  p.zchunk = (p.nz + nzc - 1) / nzc;
+  nzc = (p.nz + p.zchunk - 1) / p.zchunk;
+  p.nunits = ntiles * nzc;
+  *blocks = p.nunits;
+}
+
 // Tile shape, launch geometry and tensor maps of the TMA kernels for storage
 // type T, rank RANK, halo radius R and NF fields; shared by the builtin
 // runner below and by run-time compiled local functions (jit.cu).  PAIR:
@@ -94,6 +120,12 @@ struct TmaShape {
   template <class P, class Occ>
   static void geometry(const StepArgs& a, P& p, int* blocks, Occ&& occ) {
     const Geom& g = a.g;
+    const bool wrap = g.bc[2][0] == kPeriodic || g.bc[1][0] == kPeriodic;
+    const int slots = occ(wrap) * sm_count();
+    if (RANK == 3) {
+      zmarch_geometry(g, p, blocks, TX, TY, slots);
+      return;
+    }
     p.nx = int(g.n[2]);
     p.ny = int(g.n[1]);
     p.nz = int(g.n[0]);
@@ -102,30 +134,15 @@ struct TmaShape {
     p.per_z = g.bc[0][0] == kPeriodic;
     p.tiles_x = (p.nx + TX - 1) / TX;
     p.tiles_y = (p.ny + TY - 1) / TY;
-    const int ntiles = p.tiles_x * p.tiles_y;
-    const int slots = occ(p.per_x || p.per_y) * sm_count();
-    if (RANK == 2) {
-      p.nunits = ntiles;
-      p.zchunk = 1;
-      *blocks = std::min(ntiles, slots);
-    } else {
-      // Split z into chunks.  About kZWaves waves of blocks keep every
-      // resident slot busy (later blocks take the slots of blocks that finish
-      // early; edge tiles of periodic grids cost more per plane), but chunks
-      // stay at least kMinChunk planes long (each chunk stages 2R extra
-      // planes); short grids get at most one wave (a few blocks past a full
-      // wave would double the time).
-      const int one_wave = std::max(1, slots / ntiles);
-      int nzc = std::max(one_wave, std::min((kZWaves * slots) / ntiles, p.nz / kMinChunk));
-      nzc = std::min(nzc, p.nz);
-      p.zchunk = (p.nz + nzc - 1) / nzc;
-      nzc = (p.nz + p.zchunk - 1) / p.zchunk;
-      p.nunits = ntiles * nzc;
-      *blocks = p.nunits;
-    }
+    p.nunits = p.tiles_x * p.tiles_y;
+    p.zchunk = 1;
+    *blocks = std::min(p.nunits, slots);
   }
 
   // Parameters common to every kernel instance (fields, flags) and the maps.
+  // An external side of the slowest axis (z in 3D, y in 2D) extends the
+  // tensor maps by R planes / rows of the caller's buffer beyond the grid:
+  // there the halo is data, not the zero fill.
   template <class P>
   static cudaError_t prepare(const StepArgs& a, P& p, TmaMaps<NF>& maps) {
     for (int f = 0; f < NF; ++f) {
@@ -134,17 +151,68 @@ struct TmaShape {
     }
     p.partials = a.partials;
     p.err = a.err;
-    const int64_t n[3] = {a.g.n[2], a.g.n[1], a.g.n[0]};
+    const int sax = 3 - RANK;  // the slowest axis of the grid, in Geom order
+    const int lo = a.g.bc[sax][0] == kExternal ? R : 0;
+    const int hi = a.g.bc[sax][1] == kExternal ? R : 0;
+    p.soff = lo;
+    p.sext = (lo ? 1 : 0) | (hi ? 2 : 0);
+    int64_t n[3] = {a.g.n[2], a.g.n[1], a.g.n[0]};
+    n[RANK - 1] += lo + hi;
+    const int64_t before = int64_t(lo) * (RANK == 3 ? a.g.n[2] * a.g.n[1] : a.g.n[2]);
     for (int f = 0; f < NF; ++f) {
+      const T* base = static_cast<const T*>(a.in[f]) - before;
       cudaError_t e;
-      if ((e = encode<T>(&maps.wide[f], a.in[f], RANK, n, L::W, TY + 2 * R)) ||
-          (e = encode<T>(&maps.rows[f], a.in[f], RANK, n, L::W, R)) ||
-          (e = encode<T>(&maps.cols[f], a.in[f], RANK, n, L::CW, TY)))
+      if ((e = encode<T>(&maps.wide[f], base, RANK, n, L::W, TY + 2 * R)) ||
+          (e = encode<T>(&maps.rows[f], base, RANK, n, L::W, R)) ||
+          (e = encode<T>(&maps.cols[f], base, RANK, n, L::CW, TY)))
         return e;
     }
     return cudaSuccess;
   }
 };
+
+// The two-sweep z-march (tma3d_tb2_kernel): 64 x TY tiles of paired
+// consumers, RY = 8 rows per warp, an S-stage ring of input planes staged
+// with a 2-row halo, and three u1 slots per warp.
+template <class T, int TY_, int S_>
+struct Tb2Shape {
+  static constexpr int TX = 64, TY = TY_, RY = 8, S = S_, H = 2;
+  using L = Layout<T, TX, TY, H, 1>;
+  using SL = Tb2Slots<TX, TY, RY>;
+  static constexpr int THREADS = 32 * SL::NW + 32;
+  static constexpr size_t SMEM = size_t(S) * L::OFF_COLL + SL::BYTES + 2 * S * sizeof(uint64_t) + 128;
+  static_assert(SMEM <= 227 * 1024, "two-sweep ring exceeds the shared memory of a block");
+
+  template <class P>
+  static cudaError_t prepare(const StepArgs& a, P& p, TmaMaps<1>& maps) {
+    p.in[0] = static_cast<const T*>(a.in[0]);
+    p.out[0] = static_cast<T*>(a.out[0]);
+    p.partials = nullptr;
+    p.err = a.err;
+    p.soff = 0;
+    p.sext = 0;
+    const int64_t n[3] = {a.g.n[2], a.g.n[1], a.g.n[0]};
+    return encode<T>(&maps.wide[0], a.in[0], 3, n, L::W, TY + 2 * H);
+  }
+};
+
+// Whether the two-sweep z-march runs this launch: a 3D radius-1 star function
+// of one field (diffusion builtin or linear table), FP32 or BF16 storage,
+// every x and y side Dirichlet 0, no adjoint, no multi-stage combination.
+inline bool tb2_supported(const StepArgs& a) {
+  const Geom& g = a.g;
+  const StencilDesc& s = a.s;
+  if (g.ndim != 3 || g.nf != 1 || s.radius != 1 || !s.star || a.adjoint || a.stage >= 2) return false;
+  if (s.kind != kDiff7 && s.kind != kLinear) return false;
+  if (g.dtype != kF32 && g.dtype != kBF16) return false;
+  for (int ax = 1; ax < 3; ++ax)
+    for (int sd = 0; sd < 2; ++sd)
+      if (g.bc[ax][sd] != kDirichlet || g.bval[ax][sd] != 0.0) return false;
+  for (int sd = 0; sd < 2; ++sd)
+    if (g.bc[0][sd] == kExternal || (g.bc[0][sd] == kDirichlet && g.bval[0][sd] != 0.0))
+      return false;
+  return true;
+}
 
 // Paired consumers for FP32/BF16 storage (radius <= 2), adjoint functors
 // included: their per-point reduction is summed per lane (tile2d_pair /
@@ -213,6 +281,46 @@ struct TmaRunner {
 
   static cudaError_t run(const StepArgs& a, const Op& op, int* blocks_out) {
     return tma_tall(a) ? run_t<true>(a, op, blocks_out) : run_t<false>(a, op, blocks_out);
+  }
+
+  // Two sweeps in one launch (3D radius-1 star functions of one field; see
+  // tb2_supported).  lope_launch.tile_y 1 / 2 forces 32- / 64-row tiles.
+  template <int TY, int S>
+  static cudaError_t run_tb2_t(const StepArgs& a, const Op& op, int* blocks_out) {
+    if constexpr (RANK == 3 && Op::R == 1 && Op::NF == 1 && Op::STAR && PAIR && !Op::REDUCES) {
+      using Sh2 = Tb2Shape<T, TY, S>;
+      auto kern = &tma3d_tb2_kernel<Op, T, Sh2::TX, Sh2::TY, Sh2::RY, Sh2::S>;
+      static int occ = -1;
+      if (occ < 0) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh2::SMEM));
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, Sh2::THREADS, Sh2::SMEM) !=
+            cudaSuccess)
+          o = 1;
+        occ = o > 0 ? o : 1;
+      }
+      TmaParams<Op, T> p;
+      p.op = op;
+      int blocks = 0;
+      zmarch_geometry(a.g, p, &blocks, Sh2::TX, Sh2::TY, occ * sm_count());
+      if (blocks_out) *blocks_out = blocks;
+      TmaMaps<1> maps;
+      cudaError_t e = Sh2::prepare(a, p, maps);
+      if (e != cudaSuccess) return e;
+      kern<<<blocks, Sh2::THREADS, Sh2::SMEM, a.stream>>>(maps, p);
+      count_launches(1);
+      return cudaGetLastError();
+    } else {
+      (void)a;
+      (void)op;
+      (void)blocks_out;
+      return cudaErrorNotSupported;
+    }
+  }
+
+  static cudaError_t run_tb2(const StepArgs& a, const Op& op, int* blocks_out) {
+    if (a.tile_y == 1) return run_tb2_t<32, 6>(a, op, blocks_out);
+    return run_tb2_t<64, 6>(a, op, blocks_out);
   }
 };
 

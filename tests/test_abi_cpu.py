@@ -199,7 +199,8 @@ def test_tune_cache_file_round_trip_and_planning(lope, tmp_path, capfd, fake_add
 
 
 PLAN_CASES = [  # shape, dtype, builtin, params, halo, scheme, bc, expected plan-log fragment
-    ((512, 512, 512), "f32", "diff7", [0.1], 1, "euler", [1, 1, 1], "path=tma"),
+    ((512, 512, 512), "f32", "diff7", [0.1], 1, "euler", [1, 1, 1], "path=tma tile=0x0 k=2"),
+    ((256, 256, 256), "f32", "diff7", [0.1], 1, "euler", [0, 0, 0], "path=tma tile=0x0 k=1"),
     ((8192, 8192), "f32", "star9r2", [0.1], 2, "euler", [0, 0], "path=tma"),
     ((256, 256), "f64", "jacobi5", [0.2], 1, "euler", [0, 0], "path=trapezoid tile=64x16 k=4"),
     ((7094, 7094), "f32", "jacobi5", [0.2], 1, "euler", [0, 1], "path=trapezoid tile=128x32 k=4"),
@@ -238,7 +239,7 @@ def test_planner_default_choices(lope, capfd, case, fake_addresses):
     plan, launches = lope.lope_plan(g.handle, st.handle, ins, outs, works, 10)
     names = {1: "tma", 2: "trapezoid", 3: "direct", 4: "march"}
     assert f"path={names[plan.path]}" in want
-    if plan.path == 2:
+    if plan.path == 2 or "k=" in want:
         assert f"tile={plan.tile_x}x{plan.tile_y} k={plan.tsteps}" in want
     assert f"launches={launches}" in err
 
@@ -310,3 +311,28 @@ def test_forced_allocation_failure_is_reported_before_cuda(lope):
             lope.lope_apply(g.handle, s.handle, [base], [base + field], None, 1, None)
     finally:
         lope.lope_set_option("fail_alloc", 0)
+
+
+def test_external_boundary_is_checked_on_the_host(lope, fake_addresses):
+    """LOPE_BC_EXTERNAL: slowest axis only, one sweep per call, the TMA or
+    direct kernels (planned without any CUDA call; fake device addresses)."""
+    g = lope.Grid((64, 64), halo=1)
+    with pytest.raises(lope.LopeError, match="slowest axis"):
+        g.set_boundary(axis=1, side=0, kind="external")
+    g.set_boundaries([(2, 2), 0])
+    s = lope.Stencil.builtin("jacobi5", 0.2)
+    base, field = 1 << 40, 64 * 64 * 4
+    ins, outs, works = [base + 256], [base + 3 * field], [base + 5 * field]
+    with pytest.raises(lope.LopeError, match="one sweep per call"):
+        lope.lope_plan(g.handle, s.handle, ins, outs, works, 3)
+    plan, launches = lope.lope_plan(g.handle, s.handle, ins, outs, None, 1)
+    assert (plan.path, launches) == (1, 1)
+    with pytest.raises(lope.LopeError, match="UNSUPPORTED"):
+        lope.lope_plan(g.handle, s.handle, ins, outs, None, 1, lope.Launch(2, 64, 16, 1, -1))
+    # the input's external halo rows count for aliasing: out may not start in them
+    with pytest.raises(lope.LopeError, match="aliases"):
+        lope.lope_plan(g.handle, s.handle, ins, [base + 256 + field], None, 1)
+    # one external side and a Dirichlet value on the other: the direct kernel
+    g.set_boundary(axis=0, side=1, kind="dirichlet", value=0.5)
+    plan, _ = lope.lope_plan(g.handle, s.handle, ins, outs, None, 1)
+    assert plan.path == 3
