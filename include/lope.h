@@ -113,9 +113,14 @@ void lope_stencil_destroy(lope_stencil* stencil);
  *   C             the compute type (float for FP32/BF16 storage, double for
  *                 FP64; on the paired TMA path a packed pair of floats);
  *   U(f, dx, dy)  (2D) or U(f, dx, dy, dz) (3D): field f at the local offset,
- *                 dx along the fastest axis (the paper's U(dx,dy)); offsets
- *                 beyond `radius` are clamped to it, so the declared halo is the
- *                 contract of Sec. 3.5 (no out-of-bounds reads);
+ *                 dx along the fastest axis (the paper's U(dx,dy)).  The
+ *                 declared halo is the contract of Sec. 3.5 (no out-of-bounds
+ *                 indexing): a tap whose arguments are integer literals and
+ *                 that reads beyond `radius`, reads a field >= nfields, or (box
+ *                 = 0) reads a corner makes this call fail with
+ *                 LOPE_ERR_INVALID; a computed tap that does so at run time is
+ *                 clamped into the halo and lope_sync_status then reports
+ *                 LOPE_ERR_INVALID;
  *   P[0..7]       the parameters, in C;
  *   out[f]        must be assigned for every field f < nfields;
  *   add, sub, mul, fma_, C(x), and + - * on C values.
@@ -368,8 +373,9 @@ lope_status lope_set_option(const char* name, int64_t value);
 lope_status lope_reduce_noalloc(int op, lope_dtype dtype, const void* x, const void* y, int64_t n,
                                 double* result_dev, void* cuda_stream);
 
-/* Synchronise the stream, then report (and clear) a device-side error flag set
- * by a bounded wait that gave up: LOPE_ERR_TIMEOUT, else LOPE_OK. */
+/* Synchronise the stream, then report (and clear) the device-side error flag:
+ * LOPE_ERR_TIMEOUT if a bounded wait gave up, LOPE_ERR_INVALID if a run-time
+ * compiled local function read outside its declared halo, else LOPE_OK. */
 lope_status lope_sync_status(void* cuda_stream);
 
 /* Number of kernels this library has launched in this process (graph

@@ -7,6 +7,7 @@
 // its grid declares.  There is no host fallback: every computation runs in
 // the kernels of this library.
 #include <algorithm>
+#include <cctype>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -994,6 +995,71 @@ void lope_stencil_destroy(lope_stencil* stencil) {
   delete stencil;
 }
 
+// The taps U(f, dx, dy[, dz]) of a local-function body whose arguments are all
+// integer literals must lie inside the declared halo (Sec. 3.5: no
+// out-of-bounds indexing), read an existing field and, for a function
+// declared star-shaped, lie on an axis.  Taps with computed arguments are
+// checked on the device when they run.  Returns an empty string or the reason.
+std::string check_literal_taps(const std::string& text, int ndim, int radius, int nf, bool star) {
+  auto ident = [](char c) { return std::isalnum(static_cast<unsigned char>(c)) || c == '_'; };
+  std::string body;  // the text without comments
+  for (size_t i = 0; i < text.size(); ++i) {
+    if (text.compare(i, 2, "//") == 0) {
+      while (i < text.size() && text[i] != '\n') ++i;
+    } else if (text.compare(i, 2, "/*") == 0) {
+      const size_t e = text.find("*/", i + 2);
+      i = e == std::string::npos ? text.size() : e + 1;
+      body += ' ';
+      continue;
+    }
+    if (i < text.size()) body += text[i];
+  }
+  for (size_t i = 0; (i = body.find('U', i)) != std::string::npos; ++i) {
+    if (i > 0 && ident(body[i - 1])) continue;
+    size_t j = i + 1;
+    while (j < body.size() && std::isspace(static_cast<unsigned char>(body[j]))) ++j;
+    if (j >= body.size() || body[j] != '(') continue;
+    // the argument list up to the matching parenthesis, split at top-level commas
+    std::vector<std::string> args(1);
+    int depth = 0;
+    size_t k = j + 1;
+    for (; k < body.size(); ++k) {
+      const char c = body[k];
+      if (c == '(') ++depth;
+      if (c == ')' && depth-- == 0) break;
+      if (c == ',' && depth == 0) args.emplace_back();
+      else args.back() += c;
+    }
+    std::vector<long> v;
+    for (auto& a : args) {
+      std::string t;
+      for (char c : a)
+        if (!std::isspace(static_cast<unsigned char>(c))) t += c;
+      size_t q = (!t.empty() && (t[0] == '-' || t[0] == '+')) ? 1 : 0;
+      if (q >= t.size() || t.find_first_not_of("0123456789", q) != std::string::npos) {
+        v.clear();
+        break;
+      }
+      v.push_back(std::strtol(t.c_str(), nullptr, 10));
+    }
+    if (v.empty()) continue;  // computed arguments: checked when the kernel runs
+    const std::string tap = body.substr(i, k + 1 - i);
+    if (int(v.size()) != ndim + 1 && !(ndim == 3 && v.size() == 3))
+      return "tap " + tap + " has the wrong number of arguments";
+    if (v[0] < 0 || v[0] >= nf) return "tap " + tap + " reads a field the function does not have";
+    int nonzero = 0;
+    for (size_t a = 1; a < v.size(); ++a) {
+      if (v[a] < -radius || v[a] > radius)
+        return "tap " + tap + " reads beyond the declared halo of radius " + std::to_string(radius) +
+               " (Sec. 3.5: no out-of-bounds indexing)";
+      nonzero += v[a] != 0;
+    }
+    if (star && nonzero > 1)
+      return "tap " + tap + " reads a corner of a function declared star-shaped (box = 0)";
+  }
+  return "";
+}
+
 lope_status lope_stencil_create_source(lope_stencil** stencil, int ndim, int radius, int nfields,
                                        int box, const char* body, const double* params,
                                        int nparams) {
@@ -1005,6 +1071,8 @@ lope_status lope_stencil_create_source(lope_stencil** stencil, int ndim, int rad
     return fail(LOPE_ERR_INVALID, "at most 8 parameters");
   for (int i = 0; i < nparams; ++i)
     if (!std::isfinite(params[i])) return fail(LOPE_ERR_INVALID, "non-finite parameter");
+  const std::string bad = check_literal_taps(body, ndim, radius, nfields, box == 0);
+  if (!bad.empty()) return fail(LOPE_ERR_INVALID, bad);
   auto* h = new (std::nothrow) lope_stencil;
   if (!h) return fail(LOPE_ERR_ALLOC, "out of host memory");
   std::memset(h, 0, sizeof(*h));
@@ -1505,6 +1573,10 @@ lope_status lope_sync_status(void* cuda_stream) {
   if (e != cudaSuccess) return cuda_fail(e, "reading the device error flag");
   if (flag) {
     cudaMemset(d->err, 0, sizeof(int));
+    if (flag == kErrHalo)
+      return fail(LOPE_ERR_INVALID,
+                  "a run-time compiled local function read outside its declared halo (the read "
+                  "was clamped; Sec. 3.5 allows no out-of-bounds indexing)");
     return fail(LOPE_ERR_TIMEOUT, "a bounded in-kernel wait gave up");
   }
   return LOPE_OK;

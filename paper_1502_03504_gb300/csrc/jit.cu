@@ -148,6 +148,7 @@ struct UserOpHost {
   static constexpr int NDIM = ND, R = RR, NF = NFF;
   static constexpr bool REDUCES = false, STAR = ST;
   Coef p[kUserParams];
+  int* err;
 };
 
 enum : int { kDirectPlain = 0, kDirectStage = 1, kTrapPlain = 2, kTrapRk = 3, kNumKernels = 4 };
@@ -202,15 +203,27 @@ struct JitProgram {
          ", NF = " + std::to_string(nf) + ";\n";
     s += std::string("  static constexpr bool REDUCES = false, STAR = ") + (star ? "true" : "false") + ";\n";
     s += "  Coef p[" + std::to_string(kUserParams) + "];\n";
+    s += "  int* err;\n";
     s += "  template <class C, class A>\n";
     s += "  __device__ __forceinline__ void operator()(const A& lope_acc, C (&out)[NF], C&) const {\n";
-    // Offsets outside the declared halo are clamped into it, so a kernel never
-    // reads outside its staged tile whatever the body does.
+    // A read outside the declared halo (or a corner read by a function
+    // declared star-shaped) breaks the no-out-of-bounds rule of Sec. 3.5:
+    // literal offsets are refused when the stencil is created; a computed one
+    // records kErrHalo in the device error flag (reported by lope_sync_status)
+    // and is clamped, so no kernel reads outside its staged tile.  With literal
+    // offsets the check folds away at compile time.
     s += "    auto U = [&](int f, int dx, int dy, int dz = 0) -> C {\n";
-    s += "      f = f < 0 ? 0 : (f >= NF ? NF - 1 : f);\n";
-    s += "      dx = dx < -R ? -R : (dx > R ? R : dx);\n";
-    s += "      dy = dy < -R ? -R : (dy > R ? R : dy);\n";
-    s += "      dz = NDIM == 2 ? 0 : (dz < -R ? -R : (dz > R ? R : dz));\n";
+    s += "      const bool bad = f < 0 || f >= NF || dx < -R || dx > R || dy < -R || dy > R ||\n";
+    s += "                       (NDIM == 2 ? dz != 0 : (dz < -R || dz > R)) ||\n";
+    s += "                       (STAR && ((dx != 0) + (dy != 0) + (dz != 0) > 1));\n";
+    s += "      if (bad) {\n";
+    s += "        raise_error(err, kErrHalo);\n";
+    s += "        f = f < 0 ? 0 : (f >= NF ? NF - 1 : f);\n";
+    s += "        dx = dx < -R ? -R : (dx > R ? R : dx);\n";
+    s += "        dy = dy < -R ? -R : (dy > R ? R : dy);\n";
+    s += "        dz = NDIM == 2 ? 0 : (dz < -R ? -R : (dz > R ? R : dz));\n";
+    s += "        if (STAR && (dx != 0) + (dy != 0) + (dz != 0) > 1) dx = dy = dz = 0;\n";
+    s += "      }\n";
     s += "      return lope_acc(f, dx, dy, dz);\n    };\n";
     s += "    C P[" + std::to_string(kUserParams) + "];\n";
     s += "    for (int i = 0; i < " + std::to_string(kUserParams) + "; ++i) P[i] = p[i].get(C());\n";
@@ -412,6 +425,7 @@ cudaError_t run_tma_t(JitProgram& jp, const StepArgs& a, int dtype) {
   const bool stage = a.stage >= 2;
   Host op;
   for (int i = 0; i < kUserParams; ++i) op.p[i] = jp.prm[i];
+  op.err = a.err;
   auto occ = [&](bool wrap) {
     CUfunction f = nullptr;
     int o = 1;
@@ -455,6 +469,7 @@ cudaError_t run_direct(JitProgram& jp, const StepArgs& a, int dtype) {
   using Host = UserOpHost<RANK, R, NF, true>;
   Host op;
   for (int i = 0; i < kUserParams; ++i) op.p[i] = jp.prm[i];
+  op.err = a.err;
   const T* in[3] = {nullptr, nullptr, nullptr};
   T* out[3] = {nullptr, nullptr, nullptr};
   for (int f = 0; f < NF; ++f) {
@@ -485,6 +500,7 @@ cudaError_t run_trap(JitProgram& jp, const StepArgs& a, int dtype) {
   using Host = UserOpHost<RANK, R, NF, true>;
   Host op;
   for (int i = 0; i < kUserParams; ++i) op.p[i] = jp.prm[i];
+  op.err = a.err;
   int TX = a.tile_x > 0 ? a.tile_x : 64, TY = a.tile_y > 0 ? a.tile_y : 32;
   int k = std::max(1, a.ksteps);
   int stages = std::max(1, a.s.stages);

@@ -28,6 +28,7 @@ enum : int { kPathAuto = 0, kPathTma = 1, kPathTrap = 2, kPathDirect = 3, kPathM
 
 // Device error codes written to the error flag.
 constexpr int kErrTimeout = 1;
+constexpr int kErrHalo = 2;  // a run-time compiled function read beyond its declared halo
 // Upper bound of any single in-kernel wait (ns).  Normal waits last
 // microseconds; this only ends a wait that can no longer succeed.
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;

@@ -245,3 +245,21 @@ def test_user_trapezoid_with_large_shared_memory(lope, orc):
         outs = _run(lope, g, st, list(dev), T, launch)
         for k in range(2):
             assert torch.equal(outs[k], small[k]), (launch, k)
+
+
+def test_computed_tap_outside_the_halo_is_reported_and_clamped(lope):
+    """A tap whose offset is computed is checked when it runs: reading beyond
+    the declared halo (Sec. 3.5) is clamped into it and lope_sync_status
+    reports LOPE_ERR_INVALID; the context stays usable."""
+    body = "C s = C(0);\nfor (int d = -2; d <= 2; d += 4) s = add(s, U(0, d, 0));\nout[0] = s;"
+    st = lope.Stencil.source(body, ndim=2, radius=1)
+    g = _grid(lope, (64, 128), "f32", 1, [0, 0])
+    u = torch.rand(64, 128, device="cuda")
+    for launch in (_launch(lope, TMA), _launch(lope, DIRECT)):
+        lope.apply(g, st, u, nsteps=1, launch=launch)
+        with pytest.raises(lope.LopeError, match="outside its declared halo"):
+            lope.sync_status()
+    ok = lope.Stencil.source("out[0] = add(U(0, -1, 0), U(0, 1, 0));", ndim=2, radius=1)
+    out = lope.apply(g, ok, u, nsteps=1)
+    lope.sync_status()
+    assert torch.equal(out, torch.roll(u, 1, 1) + torch.roll(u, -1, 1))

@@ -60,3 +60,22 @@ def test_bad_arguments_are_rejected(lope):
         lope.Stencil.source(JACOBI5, params=[0.0] * 9)
     with pytest.raises(lope.LopeError, match="non-finite"):
         lope.Stencil.source(JACOBI5, params=[float("nan")])
+
+
+def test_literal_taps_outside_the_declared_halo_are_refused(lope):
+    """Sec. 3.5: a local function may not index outside its halo."""
+    with pytest.raises(lope.LopeError, match="beyond the declared halo"):
+        lope.Stencil.source("out[0] = U(0, 2, 0);", ndim=2, radius=1)
+    with pytest.raises(lope.LopeError, match="beyond the declared halo"):
+        lope.Stencil.source("out[0] = U(0, 0, 0, -3);", ndim=3, radius=2)
+    with pytest.raises(lope.LopeError, match="corner"):
+        lope.Stencil.source("out[0] = U(0, 1, 1);", ndim=2, radius=1)
+    with pytest.raises(lope.LopeError, match="field"):
+        lope.Stencil.source("out[0] = U(1, 0, 0);", ndim=2, radius=1, nfields=1)
+    with pytest.raises(lope.LopeError, match="number of arguments"):
+        lope.Stencil.source("out[0] = U(0, 1, 0, 0);", ndim=2, radius=1)
+    # within the halo, a declared box function, comments and computed taps pass
+    lope.Stencil.source("out[0] = U(0, 1, 1); // U(0, 5, 0) in a comment", ndim=2, radius=1,
+                        box=True)
+    lope.Stencil.source("C s = C(0);\nfor (int d = -1; d <= 1; ++d) s = add(s, U(0, d, 0));\n"
+                        "out[0] = s; /* U(0, 9, 9) */", ndim=2, radius=1)
