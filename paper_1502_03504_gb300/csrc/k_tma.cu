@@ -17,12 +17,24 @@ template <class T> cudaError_t dispatch_t(const StepArgs& a, int* blocks) {
       default: break;  // linear stencils: the caller passes reflected weights, no reduction
     }
   }
-  if (a.ksteps == 2) {  // two sweeps per launch: the 3D z-march with temporal blocking
+  if (a.ksteps == 2) {  // two sweeps per launch (temporal blocking)
     if (!tb2_supported(a)) return cudaErrorNotSupported;
     if (s.kind == kDiff7) return TmaRunner<OpDiff7, T, 3>::run_tb2(a, {s.prm[0]}, blocks);
-    OpStarLinear<3, 1> op;
-    for (int ax = 0; ax < 3; ++ax) for (int d = 0; d < 3; ++d) op.w[ax][d] = s.star_w[ax][d];
-    return TmaRunner<OpStarLinear<3, 1>, T, 3>::run_tb2(a, op, blocks);
+    if (s.kind == kJacobi5) return TmaRunner<OpJacobi5, T, 2>::run_tb2(a, {s.prm[0]}, blocks);
+    if (s.kind == kStar9r2) return TmaRunner<OpStar9r2, T, 2>::run_tb2(a, {s.prm[0]}, blocks);
+    if (s.ndim == 3) {
+      OpStarLinear<3, 1> op;
+      for (int ax = 0; ax < 3; ++ax) for (int d = 0; d < 3; ++d) op.w[ax][d] = s.star_w[ax][d];
+      return TmaRunner<OpStarLinear<3, 1>, T, 3>::run_tb2(a, op, blocks);
+    }
+    if (s.radius == 1) {
+      OpStarLinear<2, 1> op;
+      for (int ax = 0; ax < 3; ++ax) for (int d = 0; d < 3; ++d) op.w[ax][d] = s.star_w[ax][d];
+      return TmaRunner<OpStarLinear<2, 1>, T, 2>::run_tb2(a, op, blocks);
+    }
+    OpStarLinear<2, 2> op;
+    for (int ax = 0; ax < 3; ++ax) for (int d = 0; d < 5; ++d) op.w[ax][d] = s.star_w[ax][d];
+    return TmaRunner<OpStarLinear<2, 2>, T, 2>::run_tb2(a, op, blocks);
   }
   switch (s.kind) {
     case kJacobi5: return TmaRunner<OpJacobi5, T, 2>::run(a, {s.prm[0]}, blocks);

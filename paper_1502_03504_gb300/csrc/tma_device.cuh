@@ -1215,5 +1215,227 @@ __global__ void __launch_bounds__((TX / 2) * (TY / RY) + 32, 1)
   }
 }
 
+// ------------------------------------------------------------------ 2D tiles, two sweeps
+// Temporal blocking of depth 2 on the 2D TMA tiles (radius-1 and radius-2 star
+// functions of one field, paired consumers): each 64 x TY tile is staged once
+// with a 2R-row / 16-byte-column halo, the first sweep u1 = E(u0) is computed
+// on the tile plus an R-wide ring (the rows above and below it and the column
+// pairs beside it: every cell the second sweep reads) into a shared-memory
+// buffer, and the second sweep writes the tile.  Periodic sides: on tiles
+// whose staged halo crosses one, the consumers first rewrite the cells past
+// it from the wrapped global coordinates (the TMA box holds zeros there), so
+// the staged window is the periodic extension and u1 on the ring is the
+// periodic value.  Dirichlet sides (value 0): the zero fill is the halo of u0
+// and u1 is set to 0 past them.  u1 is rounded to the storage precision, so
+// the result is bitwise that of two one-sweep launches.
+template <class S_, int WS>
+struct Smem2Acc {  // every tap of a star function from one staged 2D buffer
+  const S_* c;
+  __device__ __forceinline__ F2 operator()(int, int dx, int dy, int) const {
+    const S_* rb = c + dy * WS;
+    if (dx == 0) return ld_pair(rb);
+    if (dx == -2) return ld_pair(rb - 2);
+    if (dx == 2) return ld_pair(rb + 2);
+    if (dx == -1) return F2::make(ld_pair(rb - 2).hi(), ld_pair(rb).lo());
+    return F2::make(ld_pair(rb).hi(), ld_pair(rb + 2).lo());
+  }
+  __device__ __forceinline__ int64_t gidx() const { return 0; }
+};
+
+// Named barrier `id` over `nthreads` threads that also ORs a predicate over
+// them: every thread gets the same answer.
+__device__ __forceinline__ bool bar_or(int id, int nthreads, bool pred) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.s32 p, %1, 0;\n\t"
+      "barrier.cta.red.or.pred q, %2, %3, p;\n\t"
+      "selp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(int(pred)), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+template <class Op, class T, int TY, int RY, int S, bool WRAP>
+__global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
+    tma2d_tb2_kernel(const __grid_constant__ TmaMaps<1> maps, const TmaParams<Op, T> p) {
+  constexpr int TX = 64, R = Op::R, H = 2 * R;
+  static_assert(Op::NF == 1 && Op::STAR && R <= 2, "radius <= 2 star function of one field");
+  using L = Layout<T, TX, TY, H, 1>;
+  constexpr int NW = TY / RY, NCONS = 32 * NW, W = L::W, CW = L::CW, NC = RY + 2 * R;
+  static_assert(CW >= H, "the staged columns cover two sweeps of the radius");
+  constexpr int W1 = TX + 8;             // u1 row: columns -4 .. TX+3 (floats)
+  constexpr int U1R = TY + 2 * R;        // u1 rows -R .. TY+R-1
+  constexpr uint32_t STAGE = L::OFF_COLL;  // the wide box alone
+  constexpr uint32_t U1B = (uint32_t(U1R) * W1 * 4 + 127) / 128 * 128;
+  constexpr int NRING = 2 * R * 32 + 2 * TY;  // ring pairs: 2R rows x 32, 2 columns x TY rows
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = align128(smem_raw);
+  float* u1s = reinterpret_cast<float*>(smem + S * STAGE);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * STAGE + 2 * U1B);
+  uint64_t* empty = full + S;
+  __shared__ volatile int abort_flag;
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCONS / 32);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (tid >= NCONS) {  // producer warp
+    if (tid == NCONS) {
+      tma_prefetch_desc(&maps.wide[0]);
+      int i = 0;
+      for (int u = blockIdx.x; u < p.nunits; u += gridDim.x, ++i) {
+        const int s = i % S;
+        if (i >= S && !mbar_wait_bounded(&empty[s], ((i / S) & 1) ^ 1, p.err)) {
+          abort_flag = 1;
+          break;
+        }
+        if (abort_flag) break;
+        const TileInfo t = classify<T, TX, TY, H>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx,
+                                                  p.ny, 0, 0);
+        issue_plane<T, TX, TY, H, 1, 2, true>(maps, smem + s * STAGE, &full[s], t, 0, p.nx, p.ny);
+      }
+      if (abort_flag) {  // let copies already issued land before the block exits
+        for (int k = max(0, i - S); k < i; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
+      }
+    }
+    return;
+  }
+
+  const int lane = tid % 32, warp = tid / 32;
+  const int cx2 = lane * 2, cy0 = warp * RY;
+  const bool per_x = WRAP && p.per_x, per_y = WRAP && p.per_y;
+  // The consumer warps meet at named barrier 1 (NCONS threads) after the
+  // periodic rewrite and after the first sweep.  A warp whose bounded wait
+  // gave up skips the work but still reaches both barriers; the second one
+  // ORs the failures, so every warp leaves the loop together (no warp is
+  // left waiting at a barrier).
+  int i = 0;
+  for (int u = blockIdx.x; u < p.nunits; u += gridDim.x, ++i) {
+    const int s = i % S;
+    const bool got = mbar_wait_bounded(&full[s], (i / S) & 1, p.err) && !abort_flag;
+    const int x0 = (u % p.tiles_x) * TX, y0 = (u / p.tiles_x) * TY;
+    T* box = reinterpret_cast<T*>(smem + s * STAGE);
+    float* u1 = u1s + (i & 1) * (U1B / 4);
+    // cells of this tile's window past a grid side; the others compute unmasked
+    const bool edge = x0 < CW || x0 + TX + CW > p.nx || y0 < H || y0 + TY + H > p.ny;
+    if (WRAP && edge && (per_x || per_y)) {
+      // the staged window past a periodic side: the wrapped values.  Only the
+      // strips past a side are visited: box columns [0, cl) and [cr, W) over
+      // all rows, box rows [0, rt) and [rb, BH) over the columns between.
+      constexpr int BH = TY + 2 * H;
+      const int cl = max(0, min(W, CW - x0)), cr = max(cl, min(W, p.nx - (x0 - CW)));
+      const int rt = max(0, min(BH, H - y0)), rb = max(rt, min(BH, p.ny - (y0 - H)));
+      auto fix = [&](int br, int bcol) {
+        const int gy = y0 - H + br, gx = x0 - CW + bcol;
+        const bool oy = gy < 0 || gy >= p.ny, ox = gx < 0 || gx >= p.nx;
+        if ((!oy || per_y) && (!ox || per_x))
+          box[br * W + bcol] =
+              p.in[0][int64_t(oy ? wrap(gy, p.ny) : gy) * p.nx + (ox ? wrap(gx, p.nx) : gx)];
+      };
+      const int xs = cl + (W - cr);  // columns past the x sides, per row
+      if (got && per_x && xs > 0)
+        for (int c = tid; c < xs * BH; c += NCONS) {
+          const int br = c / xs, k = c - br * xs;
+          fix(br, k < cl ? k : cr + k - cl);
+        }
+      const int ys = rt + (BH - rb), inner = cr - cl;  // rows past the y sides
+      if (got && per_y && ys > 0)
+        for (int c = tid; c < ys * inner; c += NCONS) {
+          const int k = c / inner, bcol = cl + (c - k * inner);
+          fix(k < rt ? k : rb + k - rt, bcol);
+        }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"r"(NCONS) : "memory");
+    }
+    // u1 is the Dirichlet value 0 past a Dirichlet side, the computed
+    // (periodic) value past a periodic one
+    auto keep = [&](int tr, int tc) {
+      const int gy = y0 + tr, gx = x0 + tc;
+      const bool oy = gy < 0 || gy >= p.ny, ox = gx < 0 || gx >= p.nx;
+      return (!oy || per_y) && (!ox || per_x);
+    };
+    auto sweep1 = [&](auto edge_tag) {
+      constexpr bool EDGE = decltype(edge_tag)::value;
+      F2 col[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) col[k] = ld_pair(box + (H - R + cy0 + k) * W + CW + cx2);
+#pragma unroll
+      for (int r = 0; r < RY; ++r) {
+        PairAcc<T, TX, TY, R, 1, NC> acc;
+        acc.b[0] = box + (H + cy0 + r) * W + CW + cx2;
+        acc.col = &col;
+        acc.r = r;
+        acc.g = 0;
+        F2 o[1];
+        F2 unused(0.f);
+        p.op(acc, o, unused);
+        F2 v = stored_pair<T>(o[0]);
+        if constexpr (EDGE)
+          if (!keep(cy0 + r, cx2)) v = F2(0.f);
+        st_pair_f(u1 + (R + cy0 + r) * W1 + 4 + cx2, v);
+      }
+      for (int c = tid; c < NRING; c += NCONS) {
+        int tr, tc;
+        if (c < 2 * R * 32) {  // the R rows above and below the tile
+          const int row = c >> 5;
+          tr = row < R ? row - R : TY + row - R;
+          tc = (c & 31) * 2;
+        } else {  // the column pairs left and right of the tile
+          const int d = c - 2 * R * 32;
+          tr = d >> 1;
+          tc = (d & 1) ? TX : -2;
+        }
+        Smem2Acc<T, W> acc{box + (H + tr) * W + CW + tc};
+        F2 o[1];
+        F2 unused(0.f);
+        p.op(acc, o, unused);
+        F2 v = stored_pair<T>(o[0]);
+        if constexpr (EDGE)
+          if (!keep(tr, tc)) v = F2(0.f);
+        st_pair_f(u1 + (R + tr) * W1 + 4 + tc, v);
+      }
+    };
+    if (got) {
+      if (edge) sweep1(BoolTag<true>());
+      else sweep1(BoolTag<false>());
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);  // the staged tile is no longer read
+    }
+    if (bar_or(1, NCONS, !got)) {  // u1 complete, or some warp gave up
+      abort_flag = 1;
+      break;
+    }
+    // ---- second sweep: the tile from u1
+    {
+      F2 col[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) col[k] = ld_pair(u1 + (cy0 + k) * W1 + 4 + cx2);
+      const bool xin = x0 + cx2 < p.nx;
+      T* o_row = p.out[0] + int64_t(y0 + cy0) * p.nx + x0 + cx2;
+#pragma unroll
+      for (int r = 0; r < RY; ++r) {
+        PairAcc<float, TX, TY, R, 1, NC> acc;
+        acc.b[0] = u1 + (R + cy0 + r) * W1 + 4 + cx2;
+        acc.col = &col;
+        acc.r = r;
+        acc.g = 0;
+        F2 o[1];
+        F2 unused(0.f);
+        p.op(acc, o, unused);
+        if (!edge || (xin && y0 + cy0 + r < p.ny)) st_pair(o_row + int64_t(r) * p.nx, o[0]);
+      }
+    }
+  }
+}
+
 }  // namespace
 }  // namespace lope

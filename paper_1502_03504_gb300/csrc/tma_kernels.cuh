@@ -196,22 +196,54 @@ struct Tb2Shape {
   }
 };
 
-// Whether the two-sweep z-march runs this launch: a 3D radius-1 star function
-// of one field (diffusion builtin or linear table), FP32 or BF16 storage,
-// every x and y side Dirichlet 0, no adjoint, no multi-stage combination.
+// The two-sweep 2D tiles (tma2d_tb2_kernel): 64 x 128 tiles of paired
+// consumers, RY = 16 rows per warp, a 3-stage ring of tiles staged with a
+// 2R-row halo, and two u1 buffers.
+template <class T, int R, int RY_ = 8>
+struct Tb2Shape2D {
+  static constexpr int TX = 64, TY = 128, RY = RY_, S = 3, H = 2 * R;
+  using L = Layout<T, TX, TY, H, 1>;
+  static constexpr int THREADS = 32 * (TY / RY) + 32;
+  static constexpr size_t U1B = (size_t(TY + 2 * R) * (TX + 8) * 4 + 127) / 128 * 128;
+  static constexpr size_t SMEM = size_t(S) * L::OFF_COLL + 2 * U1B + 2 * S * sizeof(uint64_t) + 128;
+  static_assert(SMEM <= 227 * 1024, "two-sweep tiles exceed the shared memory of a block");
+
+  template <class P>
+  static cudaError_t prepare(const StepArgs& a, P& p, TmaMaps<1>& maps) {
+    p.in[0] = static_cast<const T*>(a.in[0]);
+    p.out[0] = static_cast<T*>(a.out[0]);
+    p.partials = nullptr;
+    p.err = a.err;
+    p.soff = 0;
+    p.sext = 0;
+    const int64_t n[3] = {a.g.n[2], a.g.n[1], a.g.n[0]};
+    return encode<T>(&maps.wide[0], a.in[0], 2, n, L::W, TY + 2 * H);
+  }
+};
+
+// Whether the two-sweep kernels run this launch: a star function of one field
+// (radius 1 in 3D: diffusion builtin or linear table; radius 1 or 2 in 2D:
+// jacobi5, star9r2 or a linear table), FP32 or BF16 storage, no external
+// halo, Dirichlet sides of value 0, no adjoint, no multi-stage combination.
+// The 3D z-march also needs every x and y side Dirichlet (its ring of u1 is
+// masked, not wrapped); the 2D tiles take periodic sides too.
 inline bool tb2_supported(const StepArgs& a) {
   const Geom& g = a.g;
   const StencilDesc& s = a.s;
-  if (g.ndim != 3 || g.nf != 1 || s.radius != 1 || !s.star || a.adjoint || a.stage >= 2) return false;
-  if (s.kind != kDiff7 && s.kind != kLinear) return false;
+  if (g.nf != 1 || !s.star || a.adjoint || a.stage >= 2) return false;
   if (g.dtype != kF32 && g.dtype != kBF16) return false;
-  for (int ax = 1; ax < 3; ++ax)
+  for (int ax = 0; ax < 3; ++ax)
     for (int sd = 0; sd < 2; ++sd)
-      if (g.bc[ax][sd] != kDirichlet || g.bval[ax][sd] != 0.0) return false;
-  for (int sd = 0; sd < 2; ++sd)
-    if (g.bc[0][sd] == kExternal || (g.bc[0][sd] == kDirichlet && g.bval[0][sd] != 0.0))
-      return false;
-  return true;
+      if (g.bc[ax][sd] == kExternal || (g.bc[ax][sd] == kDirichlet && g.bval[ax][sd] != 0.0))
+        return false;
+  if (g.ndim == 3) {
+    if (s.radius != 1 || (s.kind != kDiff7 && s.kind != kLinear)) return false;
+    for (int ax = 1; ax < 3; ++ax)
+      for (int sd = 0; sd < 2; ++sd)
+        if (g.bc[ax][sd] != kDirichlet) return false;
+    return true;
+  }
+  return s.radius <= 2 && (s.kind == kJacobi5 || s.kind == kStar9r2 || s.kind == kLinear);
 }
 
 // Paired consumers for FP32/BF16 storage (radius <= 2), adjoint functors
@@ -318,7 +350,60 @@ struct TmaRunner {
     }
   }
 
+  template <bool WRAP, int RY>
+  static cudaError_t run_tb2_2d_t(const StepArgs& a, const Op& op, int* blocks_out) {
+    if constexpr (RANK == 2 && Op::R <= 2 && Op::NF == 1 && Op::STAR && PAIR && !Op::REDUCES) {
+      using Sh2 = Tb2Shape2D<T, Op::R, RY>;
+      auto kern = &tma2d_tb2_kernel<Op, T, Sh2::TY, Sh2::RY, Sh2::S, WRAP>;
+      static int occ = -1;
+      if (occ < 0) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh2::SMEM));
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, Sh2::THREADS, Sh2::SMEM) !=
+            cudaSuccess)
+          o = 1;
+        occ = o > 0 ? o : 1;
+      }
+      TmaParams<Op, T> p;
+      p.op = op;
+      const Geom& g = a.g;
+      p.nx = int(g.n[2]);
+      p.ny = int(g.n[1]);
+      p.nz = 1;
+      p.per_x = g.bc[2][0] == kPeriodic;
+      p.per_y = g.bc[1][0] == kPeriodic;
+      p.per_z = 0;
+      p.tiles_x = (p.nx + Sh2::TX - 1) / Sh2::TX;
+      p.tiles_y = (p.ny + Sh2::TY - 1) / Sh2::TY;
+      p.nunits = p.tiles_x * p.tiles_y;
+      p.zchunk = 1;
+      const int blocks = std::min(p.nunits, occ * sm_count());
+      if (blocks_out) *blocks_out = blocks;
+      TmaMaps<1> maps;
+      cudaError_t e = Sh2::prepare(a, p, maps);
+      if (e != cudaSuccess) return e;
+      kern<<<blocks, Sh2::THREADS, Sh2::SMEM, a.stream>>>(maps, p);
+      count_launches(1);
+      return cudaGetLastError();
+    } else {
+      (void)a;
+      (void)op;
+      (void)blocks_out;
+      return cudaErrorNotSupported;
+    }
+  }
+
   static cudaError_t run_tb2(const StepArgs& a, const Op& op, int* blocks_out) {
+    if constexpr (RANK == 2) {
+      // lope_launch.tile_y 1 takes 16 rows per consumer warp (8 warps), else 8
+      // rows (16 warps)
+      const bool wrap = a.g.bc[2][0] == kPeriodic || a.g.bc[1][0] == kPeriodic;
+      if (a.tile_y == 1)
+        return wrap ? run_tb2_2d_t<true, 16>(a, op, blocks_out)
+                    : run_tb2_2d_t<false, 16>(a, op, blocks_out);
+      return wrap ? run_tb2_2d_t<true, 8>(a, op, blocks_out)
+                  : run_tb2_2d_t<false, 8>(a, op, blocks_out);
+    }
     if (a.tile_y == 1) return run_tb2_t<32, 6>(a, op, blocks_out);
     return run_tb2_t<64, 6>(a, op, blocks_out);
   }

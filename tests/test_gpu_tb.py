@@ -105,3 +105,64 @@ def test_two_sweeps_write_only_their_output(lope):
         for b in bufs:
             assert bool((b[:guard] == sentinel).all()) and bool((b[guard + n:] == sentinel).all())
         assert torch.equal(u0, keep)
+
+
+SHAPES_2D = [(300, 200), (129, 64), (8, 8), (1030, 136), (64, 1032)]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("bc", [[0, 0], [1, 1], [0, 1], [1, 0]])
+@pytest.mark.parametrize("kind,prm,halo", [("jacobi5", [0.2], 1), ("star9r2", [0.1], 2)])
+@pytest.mark.parametrize("shape", SHAPES_2D, ids=lambda s: "x".join(map(str, s)))
+def test_two_sweeps_2d_bitwise_equal_one_sweep(lope, orc, dtype, bc, kind, prm, halo, shape):
+    u0, u0s = to_device(LI.uniform_field(1710, shape), dtype)
+    g = lope.Grid(shape, dtype, halo=halo)
+    g.set_boundaries(bc)
+    st = lope.Stencil.builtin(kind, *prm)
+    for T in (2, 5):
+        ref = _run(lope, g, st, u0, T, lope.Launch(TMA, 0, 0, 1, -1))
+        got = _run(lope, g, st, u0, T, lope.Launch(TMA, 0, 0, 2, -1))
+        assert torch.equal(got, ref), T
+    assert torch.equal(ref, _run(lope, g, st, u0, 5, lope.Launch(DIRECT, 0, 0, 0, -1)))
+    if dtype == "f32" and shape == (300, 200):
+        want = orc.apply(u0s, kind, prm, 5, bc=bc)
+        G = 1.0 if kind == "jacobi5" else 1.0667
+        eps = float(local_eps(kind, prm, [float(np.max(np.abs(u0s))) * G], "f32")[0])
+        assert np.max(np.abs(to_host(ref) - want)) <= 5 * G ** 5 * eps
+
+
+def test_two_sweeps_2d_linear_asymmetric_tables(lope):
+    rng = np.random.default_rng(1711)
+    shape = (200, 136)
+    u0, _ = to_device(LI.uniform_field(1712, shape), "f32")
+    for r in (1, 2):
+        w = np.zeros((2 * r + 1, 2 * r + 1))
+        for d in range(2 * r + 1):
+            if d != r:
+                w[r, d] = rng.uniform(0.01, 0.08)
+                w[d, r] = rng.uniform(0.01, 0.08)
+        w[r, r] = 1.0 - w.sum()
+        st = lope.Stencil.linear(w)
+        for bc in ([0, 0], [1, 0]):
+            g = lope.Grid(shape, "f32", halo=r)
+            g.set_boundaries(bc)
+            ref = _run(lope, g, st, u0, 6, lope.Launch(DIRECT, 0, 0, 0, -1))
+            assert torch.equal(_run(lope, g, st, u0, 6, lope.Launch(TMA, 0, 0, 2, -1)), ref), (r, bc)
+
+
+def test_two_sweeps_2d_write_only_their_output(lope):
+    shape = (300, 200)
+    n = int(np.prod(shape))
+    guard, sentinel = 4096, -7.0e30
+    u0, _ = to_device(LI.uniform_field(1713, shape), "f32")
+    keep = u0.clone()
+    st = lope.Stencil.builtin("star9r2", 0.1)
+    for bc in ([0, 0], [1, 1]):
+        g = lope.Grid(shape, "f32", halo=2)
+        g.set_boundaries(bc)
+        bufs = [torch.full((n + 2 * guard,), sentinel, device="cuda") for _ in range(2)]
+        out, work = (b[guard:guard + n].view(shape) for b in bufs)
+        _run(lope, g, st, u0, 5, lope.Launch(TMA, 0, 0, 2, -1), out=out, work=work)
+        for b in bufs:
+            assert bool((b[:guard] == sentinel).all()) and bool((b[guard + n:] == sentinel).all())
+        assert torch.equal(u0, keep)
