@@ -202,7 +202,7 @@ PLAN_CASES = [  # shape, dtype, builtin, params, halo, scheme, bc, expected plan
     ((512, 512, 512), "f32", "diff7", [0.1], 1, "euler", [1, 1, 1], "path=tma tile=0x0 k=2"),
     ((256, 256, 256), "f32", "diff7", [0.1], 1, "euler", [0, 0, 0], "path=tma tile=0x0 k=1"),
     ((8192, 8192), "f32", "star9r2", [0.1], 2, "euler", [0, 0], "path=tma tile=0x0 k=2"),
-    ((2048, 2048), "bf16", "star9r2", [0.1], 2, "euler", [0, 0], "path=tma tile=0x0 k=2"),
+    ((4096, 4096), "bf16", "star9r2", [0.1], 2, "euler", [0, 0], "path=tma tile=0x0 k=2"),
     ((1536, 2048), "f32", "star9r2", [0.1], 2, "euler", [0, 1], "path=tma tile=0x0 k=1"),
     ((256, 256), "f64", "jacobi5", [0.2], 1, "euler", [0, 0], "path=trapezoid tile=64x16 k=4"),
     ((7094, 7094), "f32", "jacobi5", [0.2], 1, "euler", [0, 1], "path=trapezoid tile=128x32 k=4"),
