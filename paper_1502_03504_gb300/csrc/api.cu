@@ -247,14 +247,14 @@ Choice default_choice(const Geom& g, const StencilDesc& s, int* err) {
     if (trap2d_supported(a)) return {kPathTrap, 64, 16, 4};
     a.ksteps = 1;
   }
-  if (s.stages == 1 && ((g.ndim == 3 && g.dtype == kF32 && npts(g) >= (int64_t(1) << 21)) ||
+  if (s.stages == 1 && ((g.ndim == 3 && npts(g) >= (int64_t(1) << 21)) ||
                          (g.ndim == 2 && npts(g) >= (int64_t(1) << 22)))) {
     // Two sweeps per launch halve the HBM bytes per sweep.  Measured on
     // GB300, 50 sweeps (one sweep per launch -> two):
-    //   3D diff7 FP32 Dirichlet 0: 512^3 8.98 -> 5.91 ms, 384^3 3.98 -> 2.79,
-    //   256^3 1.05 -> 1.02, 128^3 0.32 -> 0.27; BF16 storage was slower at
-    //   512^3 (6.67 -> 7.46 ms: its one-sweep march is far from the copy peak
-    //   already, and the two-sweep march is bound by instruction issue);
+    //   3D diff7 FP32 Dirichlet 0: 512^3 9.10 -> 5.46 ms, 384^3 3.82 -> 2.58,
+    //   256^3 1.05 -> 0.89, 128^3 0.32 -> 0.27; BF16 512^3 6.67 -> 6.22,
+    //   256^3 1.04 -> 0.94 (its one-sweep march is far from the copy peak
+    //   already and the two-sweep march is bound by instruction issue);
     //   2D star9r2 FP32 8192^2 periodic 4.26 -> 3.25 ms, Dirichlet 4.14 ->
     //   3.05; jacobi5 FP32 8192^2 4.13 -> 2.84 / 4.21 -> 2.63; BF16 8192^2
     //   star9r2 3.71 -> 3.47, jacobi5 about equal; 4096^2 FP32 1.2-1.45x.

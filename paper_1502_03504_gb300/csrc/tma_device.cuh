@@ -1215,6 +1215,211 @@ __global__ void __launch_bounds__((TX / 2) * (TY / RY) + 32, 1)
   }
 }
 
+// Named barrier `id` over `nthreads` threads that also ORs a predicate over
+// them: every thread gets the same answer.
+__device__ __forceinline__ bool bar_or(int id, int nthreads, bool pred) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.s32 p, %1, 0;\n\t"
+      "barrier.cta.red.or.pred q, %2, %3, p;\n\t"
+      "selp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(int(pred)), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+// The same two-sweep z-march with the u1 planes shared by the block: every
+// consumer warp computes u1 on its RY rows of the tile and the block shares
+// the R-wide ring around the tile (the rows above and below, the column pairs
+// beside), so no row is computed twice; the warps meet at named barrier 1 once
+// per plane, between writing u1 of plane j-1 and reading it for u2.  Three
+// plane slots rotate: slot (j-1) % 3 is written at plane j, read at plane j+1
+// and written again at plane j+3, after every warp has passed the barrier of
+// plane j+2.  The barrier ORs the warps' wait failures, so all leave together.
+template <class Op, class T, int TX, int TY, int RY, int S>
+__global__ void __launch_bounds__((TX / 2) * (TY / RY) + 32, 1)
+    tma3d_tb2s_kernel(const __grid_constant__ TmaMaps<1> maps, const TmaParams<Op, T> p) {
+  static_assert(Op::R == 1 && Op::NF == 1 && Op::STAR && TX == 64, "radius-1 star, one field");
+  constexpr int H = 2;
+  using L = Layout<T, TX, TY, H, 1>;
+  constexpr int NW = TY / RY, NCONS = 32 * NW, W = L::W, CW = L::CW;
+  constexpr int W1 = TX + 8, SR = TY + 2;  // slot: rows -1 .. TY, columns -4 .. TX+3
+  constexpr int SLOT = SR * W1;
+  constexpr uint32_t STAGE = L::OFF_COLL;
+  constexpr int NRING = 2 * 32 + 2 * SR;  // rows -1 and TY; column pairs -2 and TX on rows -1..TY
+  static_assert(S >= 4, "ring too short for three planes and one in flight");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = align128(smem_raw);
+  float* slots = reinterpret_cast<float*>(smem + S * STAGE);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * STAGE + 3 * SLOT * 4);
+  uint64_t* empty = full + S;
+  __shared__ volatile int abort_flag;
+
+  const int tid = threadIdx.x;
+  const int ntiles = p.tiles_x * p.tiles_y;
+  const int tile = blockIdx.x % ntiles, zc = blockIdx.x / ntiles;
+  const TileInfo t = classify<T, TX, TY, H>((tile % p.tiles_x) * TX, (tile / p.tiles_x) * TY, p.nx,
+                                            p.ny, 0, 0);
+  const int z0 = zc * p.zchunk, z1 = min(p.nz, z0 + p.zchunk);
+  const int np = (z1 - z0) + 2 * H;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCONS / 32);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (z0 >= z1) return;
+
+  if (tid >= NCONS) {  // producer warp
+    if (tid == NCONS) {
+      tma_prefetch_desc(&maps.wide[0]);
+      int j = 0;
+      for (; j < np; ++j) {
+        const int s = j % S;
+        if (j >= S && !mbar_wait_bounded(&empty[s], ((j / S) & 1) ^ 1, p.err)) {
+          abort_flag = 1;
+          break;
+        }
+        if (abort_flag) break;
+        int z = z0 - H + j;
+        if (p.per_z) z = wrap(z, p.nz);
+        issue_plane<T, TX, TY, H, 1, 3, true>(maps, smem + s * STAGE, &full[s], t, z, p.nx, p.ny);
+      }
+      if (abort_flag) {
+        for (int k = max(0, j - S); k < j; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
+      }
+    }
+    return;
+  }
+
+  const int lane = tid % 32, warp = tid / 32;
+  const int cx2 = lane * 2, cy0 = warp * RY;
+  const int64_t plane = int64_t(p.nx) * p.ny;
+  const bool xin = t.x0 + cx2 < p.nx;
+  auto stage = [&](int j) { return reinterpret_cast<const T*>(smem + (j % S) * STAGE); };
+  auto inside = [&](int tr, int tc) {
+    const int gy = t.y0 + tr, gx = t.x0 + tc;
+    return gy >= 0 && gy < p.ny && gx >= 0 && gx < p.nx;
+  };
+  const bool edge = t.x0 == 0 || t.y0 == 0 || t.x0 + TX + 2 > p.nx || t.y0 + TY + 1 > p.ny;
+  T* outp = p.out[0] + int64_t(z0) * plane + int64_t(t.y0 + cy0) * p.nx + t.x0 + cx2;
+
+  F2 q0[3][RY];
+  F2 q1[3][RY];
+  bool ok = true;       // changes only at a barrier: the same in every warp
+  bool failed = false;  // this warp's waits so far
+  auto step = [&](auto ph_tag, auto edge_tag, int j) {
+    constexpr int PH = decltype(ph_tag)::value;
+    constexpr bool EDGE = decltype(edge_tag)::value;
+    constexpr int P1 = (PH + 2) % 3, P2 = (PH + 1) % 3;
+    const bool got = !failed && mbar_wait_bounded(&full[j % S], (j / S) & 1, p.err) && !abort_flag;
+    failed = !got;
+    const T* bj = stage(j);
+    if (got) {
+#pragma unroll
+      for (int r = 0; r < RY; ++r) q0[PH][r] = ld_pair(bj + (H + cy0 + r) * W + CW + cx2);
+    }
+    if (j < 2) return;  // a failure here is reported at the next barrier
+    // ---- u1 at plane j-1
+    const int zg = z0 - H + (j - 1);
+    const bool zout = !p.per_z && (zg < 0 || zg >= p.nz);
+    const T* bc = stage(j - 1);
+    const T* blo = stage(j - 2);
+    float* s1 = slots + P1 * SLOT;
+    if (got) {
+      if (zout) {
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+          q1[P1][r] = F2(0.f);
+          st_pair_f(s1 + (1 + cy0 + r) * W1 + 4 + cx2, F2(0.f));
+        }
+        for (int c = tid; c < NRING; c += NCONS) {
+          const int tr = c < 64 ? ((c >> 5) ? TY : -1) : (c - 64) / 2 - 1;
+          const int tc = c < 64 ? (c & 31) * 2 : (((c - 64) & 1) ? TX : -2);
+          st_pair_f(s1 + (1 + tr) * W1 + 4 + tc, F2(0.f));
+        }
+      } else {
+        F2 col[RY + 2];
+        col[0] = ld_pair(bc + (H + cy0 - 1) * W + CW + cx2);
+        col[RY + 1] = ld_pair(bc + (H + cy0 + RY) * W + CW + cx2);
+#pragma unroll
+        for (int r = 0; r < RY; ++r) col[1 + r] = q0[P1][r];
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+          Tb2Acc<T, W> acc{bc + (H + cy0 + r) * W + CW + cx2, col + r, q0[P2][r], q0[PH][r]};
+          F2 o[1];
+          F2 unused(0.f);
+          p.op(acc, o, unused);
+          F2 v = stored_pair<T>(o[0]);
+          if constexpr (EDGE)
+            if (!(xin && t.y0 + cy0 + r < p.ny)) v = F2(0.f);
+          q1[P1][r] = v;
+          st_pair_f(s1 + (1 + cy0 + r) * W1 + 4 + cx2, v);
+        }
+        for (int c = tid; c < NRING; c += NCONS) {
+          const int tr = c < 64 ? ((c >> 5) ? TY : -1) : (c - 64) / 2 - 1;
+          const int tc = c < 64 ? (c & 31) * 2 : (((c - 64) & 1) ? TX : -2);
+          const int off = (H + tr) * W + CW + tc;
+          Tb2SmemAcc<T, W> acc{bc + off, blo + off, bj + off};
+          F2 o[1];
+          F2 unused(0.f);
+          p.op(acc, o, unused);
+          F2 v = stored_pair<T>(o[0]);
+          if constexpr (EDGE)
+            if (!inside(tr, tc)) v = F2(0.f);
+          st_pair_f(s1 + (1 + tr) * W1 + 4 + tc, v);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[(j - 2) % S]);  // u0 plane j-2 is no longer read
+    }
+    if (bar_or(1, NCONS, !got)) {  // u1 of plane j-1 complete, or some warp gave up
+      abort_flag = 1;
+      ok = false;
+      return;
+    }
+    if (j < 4) return;
+    // ---- u2 at plane j-2 (output plane z0 + j - 4)
+    const float* s2 = slots + P2 * SLOT;
+    F2 col[RY + 2];
+    col[0] = ld_pair(s2 + cy0 * W1 + 4 + cx2);
+    col[RY + 1] = ld_pair(s2 + (cy0 + RY + 1) * W1 + 4 + cx2);
+#pragma unroll
+    for (int r = 0; r < RY; ++r) col[1 + r] = q1[P2][r];
+    T* o_plane = outp + int64_t(j - 4) * plane;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      Tb2Acc<float, W1> acc{s2 + (1 + cy0 + r) * W1 + 4 + cx2, col + r, q1[PH][r], q1[P1][r]};
+      F2 o[1];
+      F2 unused(0.f);
+      p.op(acc, o, unused);
+      if (!EDGE || (xin && t.y0 + cy0 + r < p.ny)) st_pair(o_plane + int64_t(r) * p.nx, o[0]);
+    }
+  };
+  auto march = [&](auto edge_tag) {
+    for (int j0 = 0; j0 < np && ok; j0 += 3) {
+      step(IntTag<0>(), edge_tag, j0);
+      if (ok && j0 + 1 < np) step(IntTag<1>(), edge_tag, j0 + 1);
+      if (ok && j0 + 2 < np) step(IntTag<2>(), edge_tag, j0 + 2);
+    }
+  };
+  if (edge) march(BoolTag<true>());
+  else march(BoolTag<false>());
+  if (ok) {
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&empty[(np - 2) % S]);
+      mbar_arrive(&empty[(np - 1) % S]);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ 2D tiles, two sweeps
 // Temporal blocking of depth 2 on the 2D TMA tiles (radius-1 and radius-2 star
 // functions of one field, paired consumers): each 64 x TY tile is staged once
@@ -1241,21 +1446,6 @@ struct Smem2Acc {  // every tap of a star function from one staged 2D buffer
   }
   __device__ __forceinline__ int64_t gidx() const { return 0; }
 };
-
-// Named barrier `id` over `nthreads` threads that also ORs a predicate over
-// them: every thread gets the same answer.
-__device__ __forceinline__ bool bar_or(int id, int nthreads, bool pred) {
-  int r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.s32 p, %1, 0;\n\t"
-      "barrier.cta.red.or.pred q, %2, %3, p;\n\t"
-      "selp.s32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"(int(pred)), "r"(id), "r"(nthreads)
-      : "memory");
-  return r != 0;
-}
 
 template <class Op, class T, int TY, int RY, int S, bool WRAP>
 __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)

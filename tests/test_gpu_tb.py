@@ -49,9 +49,9 @@ def test_two_sweeps_bitwise_equal_one_sweep(lope, orc, dtype, zbc, shape):
         ref = _run(lope, g, st, u0, T, lope.Launch(TMA, 0, 0, 1, -1))
         direct = _run(lope, g, st, u0, T, lope.Launch(DIRECT, 0, 0, 0, -1))
         assert torch.equal(ref, direct)
-        for tile in (SHORT, TALL):
-            got = _run(lope, g, st, u0, T, lope.Launch(TMA, 0, tile, 2, -1))
-            assert torch.equal(got, ref), (T, tile)
+        for tx, ty in ((0, SHORT), (0, TALL), (1, 0)):  # per-warp slots; block-shared planes
+            got = _run(lope, g, st, u0, T, lope.Launch(TMA, tx, ty, 2, -1))
+            assert torch.equal(got, ref), (T, tx, ty)
         if dtype == "f32" and T == 7:
             want = orc.apply(u0s, "diff7", [0.1], T, bc=[zbc, 1, 1])
             bound = T * float(local_eps("diff7", [0.1], [float(np.max(np.abs(u0s)))], "f32")[0])
@@ -74,8 +74,8 @@ def test_two_sweeps_linear_table_asymmetric(lope):
     for zbc in (0, 1):
         g = _grid(lope, shape, "f32", zbc)
         ref = _run(lope, g, st, u0, 6, lope.Launch(DIRECT, 0, 0, 0, -1))
-        for tile in (SHORT, TALL):
-            assert torch.equal(_run(lope, g, st, u0, 6, lope.Launch(TMA, 0, tile, 2, -1)), ref)
+        for tx, ty in ((0, SHORT), (0, TALL), (1, 0)):
+            assert torch.equal(_run(lope, g, st, u0, 6, lope.Launch(TMA, tx, ty, 2, -1)), ref)
 
 
 def test_two_sweeps_refused_where_it_does_not_apply(lope):
@@ -100,8 +100,8 @@ def test_two_sweeps_write_only_their_output(lope):
     st = lope.Stencil.builtin("diff7", 0.1)
     bufs = [torch.full((n + 2 * guard,), sentinel, device="cuda") for _ in range(2)]
     out, work = (b[guard:guard + n].view(shape) for b in bufs)
-    for tile in (SHORT, TALL):
-        _run(lope, g, st, u0, 5, lope.Launch(TMA, 0, tile, 2, -1), out=out, work=work)
+    for tx, ty in ((0, SHORT), (0, TALL), (1, 0)):
+        _run(lope, g, st, u0, 5, lope.Launch(TMA, tx, ty, 2, -1), out=out, work=work)
         for b in bufs:
             assert bool((b[:guard] == sentinel).all()) and bool((b[guard + n:] == sentinel).all())
         assert torch.equal(u0, keep)
