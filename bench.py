@@ -396,7 +396,7 @@ def main():
     ach3 = alg3 / launch3_s / 1e9
     ach2 = alg2 / launch2_s / 1e9
     tr = traffic_record()
-    name3 = ("tma3d_tb2_kernel<OpDiff7, float> (512^3, two sweeps per launch)" if k3 == 2 else
+    name3 = ("tma3d_tb2s_kernel<OpDiff7, float> (512^3, two sweeps per launch)" if k3 == 2 else
              "tma3d_kernel<OpDiff7, float> (512^3, one sweep per launch)")
     roofline = {"bound": "hbm", "achieved": ach3, "peak": peak, "unit": "GB/s",
                 "frac": ach3 / peak,
@@ -413,7 +413,7 @@ def main():
                          "avg_launch_us": launch2_s * 1e6,
                          "alg_GBps": ach2, "frac_of_peak": ach2 / peak,
                          "updates_per_s": N2 ** 2 * T2 / (t2 / 1e3),
-                         "traffic": tr.get("star9r2_8192_bytes_per_launch") if tr else None},
+                         "traffic": tr.get(f"star9r2_8192_k{k2}_bytes_per_launch") if tr else None},
     }
     # the one-sweep z-march on the same grid (the k = 1 form of the roofline
     # gate), timed after the step
