@@ -267,8 +267,12 @@ lope_status lope_tune_cache_load(const char* path, const char* gpu_name, int* lo
  * hold n*nfields pointers, grid-major.  workspace is caller device memory of at
  * least lope_batch_workspace_size bytes; it holds the work list and the
  * inter-block barrier and must stay untouched between calls that reuse it.
- * cfg may be NULL (tile and temporal depth from the batch autotuner cache,
- * see lope_autotune_batch, else 64 x 32 tiles and depth 4).  Errors as
+ * cfg may be NULL: the choice of the batch autotuner for this batch (see
+ * lope_autotune_batch), else, for FP32 star functions of radius 1-2 (jacobi5,
+ * star9r2, linear star tables), the two-sweep register tiles (cfg->path 1:
+ * 64 x 128 tiles staged by plain loads, any row pitch, two sweeps per pass),
+ * and the trapezoid tiles otherwise (cfg->path 2: 64 x 32 tiles, depth 4;
+ * tile_x, tile_y and tsteps choose another shape and depth).  Errors as
  * lope_apply; LOPE_ERR_TIMEOUT is reported by lope_sync_status if a bounded
  * barrier wait gave up. */
 lope_status lope_batch_workspace_size(int n, const lope_grid* const* grids,
@@ -279,8 +283,9 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
                              int64_t nsteps, const lope_launch* cfg, void* workspace,
                              size_t workspace_bytes, void* cuda_stream);
 
-/* Batch autotuner: times the batched launch over tile shapes {128, 64} x {32,
- * 16} and temporal depths {1, 2, 4, 5} on the caller's buffers (out and work
+/* Batch autotuner: times the batched launch over the two-sweep register tiles
+ * (where they apply) and the trapezoid tiles of shapes {128, 64} x {32, 16}
+ * and temporal depths {1, 2, 4, 5} on the caller's buffers (out and work
  * are overwritten), stores the fastest for this batch (grid extents and
  * boundaries, dtype, stencil) and returns it in *best (*best_ms its time for
  * nsteps).  Later lope_apply_batch calls with cfg NULL (or zero tile/depth) on

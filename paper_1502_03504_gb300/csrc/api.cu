@@ -842,7 +842,10 @@ bool parse_tune_line(const std::string& line, const std::string& gpu, bool* batc
   }
   if (!(is >> colon >> c->path >> c->tile_x >> c->tile_y >> c->k) || colon != ":") return false;
   if (!choice_in_range(*c)) return false;
-  if (*batch && (c->path != kPathTrap || c->tile_x < 8 || c->tile_y < 1)) return false;
+  if (*batch && !((c->path == kPathTrap && c->tile_x >= 8 && c->tile_y >= 1) ||
+                  (c->path == kPathTma && c->tile_x == kBatchTb2X && c->tile_y == kBatchTb2Y &&
+                   c->k == 2)))
+    return false;
   return true;
 }
 
@@ -1271,26 +1274,39 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
     void* work1[1] = {work ? work[i] : nullptr};
     if ((rs = check_fields(grids[i]->g, in1, out1, work1, true)) != LOPE_OK) return rs;
   }
-  Choice tuned = {kPathTrap, 64, 32, 4};  // defaults, or the autotuner's choice for this batch
-  if (!cfg || cfg->tile_x <= 0 || cfg->tile_y <= 0 || cfg->tsteps <= 0) {
+  // The two-sweep register tiles (path 1: 64 x 128 tiles, two sweeps per
+  // pass) serve FP32 star functions of radius 1-2 (jacobi5, star9r2, linear
+  // star tables) and are the default there; other batches take the trapezoid
+  // tiles (path 2, 64 x 32, four sweeps per pass).  A choice remembered by the
+  // batch autotuner comes first; cfg overrides either.
+  const bool tb2_ok = dtype == kF32 && s.star && s.radius <= 2 &&
+                      (s.kind == kJacobi5 || s.kind == kStar9r2 || s.kind == kLinear);
+  Choice tuned = tb2_ok ? Choice{kPathTma, kBatchTb2X, kBatchTb2Y, 2} : Choice{kPathTrap, 64, 32, 4};
+  if (!cfg || cfg->path == kPathAuto || cfg->tile_x <= 0 || cfg->tile_y <= 0 || cfg->tsteps <= 0) {
     std::lock_guard<std::mutex> lk(g_btune_mu);
     auto it = g_btune.find(batch_sig(n, grids, s));
     if (it != g_btune.end()) tuned = it->second;
   }
-  const int tx = cfg && cfg->tile_x > 0 ? cfg->tile_x : tuned.tile_x;
-  const int ty = cfg && cfg->tile_y > 0 ? cfg->tile_y : tuned.tile_y;
-  const int k = cfg && cfg->tsteps > 0 ? cfg->tsteps : tuned.k;
+  const int path = cfg && cfg->path != kPathAuto ? cfg->path : tuned.path;
+  if (path != kPathTma && path != kPathTrap)
+    return fail(LOPE_ERR_UNSUPPORTED, "the batched launch runs trapezoid (2) or two-sweep (1) tiles");
+  const int mode = path == kPathTma ? 1 : 0;
+  const int tx = mode ? kBatchTb2X : cfg && cfg->tile_x > 0 ? cfg->tile_x : tuned.tile_x;
+  const int ty = mode ? kBatchTb2Y : cfg && cfg->tile_y > 0 ? cfg->tile_y : tuned.tile_y;
+  const int k = mode ? 2 : cfg && cfg->tsteps > 0 ? cfg->tsteps : tuned.k;
   if (tx < 8 || tx > 256 || ty < 1 || ty > 256 || k < 1 || k > 8)
     return fail(LOPE_ERR_INVALID, "bad batch tile or depth");
+  if (mode && cfg && cfg->tsteps > 0 && cfg->tsteps != 2)
+    return fail(LOPE_ERR_UNSUPPORTED, "the two-sweep batched tiles run two sweeps per pass");
   DevState* d = nullptr;
   lope_status rs = dev_state(&d);
   if (rs != LOPE_OK) return rs;
-  const int maxb = batch_max_blocks(s, dtype, tx, ty, k);
+  const int maxb = batch_max_blocks(s, dtype, tx, ty, k, mode);
   if (maxb <= 0) return fail(LOPE_ERR_UNSUPPORTED, "batched kernel does not support this stencil/tile");
 
   const int64_t wait_ms = g_wait_limit_ms.load(), skip = g_skip_arrive.load();
   std::vector<int64_t> key = {int64_t(n), int64_t(dtype), s.kind, tx, ty, k, nsteps,
-                              int64_t(reinterpret_cast<uintptr_t>(workspace)), wait_ms, skip};
+                              int64_t(reinterpret_cast<uintptr_t>(workspace)), wait_ms, skip, mode};
   const int64_t* sw = reinterpret_cast<const int64_t*>(&s);
   key.insert(key.end(), sw, sw + sizeof(StencilDesc) / 8);
   for (int i = 0; i < n; ++i) {
@@ -1350,6 +1366,7 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
     plan->dev.err = d->err;
     plan->dev.wait_ns = (unsigned long long)wait_ms * 1000000ull;
     plan->dev.skip_block = int(skip);
+    plan->dev.mode = mode;
     plan->blocks = std::min(items, maxb);
     // Capture: descriptor upload, barrier reset, persistent kernel.
     cudaGraph_t graph = nullptr;
@@ -1394,32 +1411,33 @@ lope_status lope_autotune_batch(int n, const lope_grid* const* grids, const lope
   double bms = 1e300;
   lope_launch bl = {0, 0, 0, 0, 0};
   lope_status last = LOPE_OK;
+  std::vector<lope_launch> cands = {{kPathTma, kBatchTb2X, kBatchTb2Y, 2, -1}};
   for (const auto& t : tiles)
-    for (int k : {1, 2, 4, 5}) {
-      const lope_launch c = {kPathTrap, t[0], t[1], k, -1};
-      // first call builds and caches the plan's graph; the second is timed
-      if ((last = lope_apply_batch(n, grids, stencil, in, out, work, nsteps, &c, workspace,
-                                   workspace_bytes, cuda_stream)) != LOPE_OK)
-        continue;
-      cudaEventRecord(e0, st);
-      last = lope_apply_batch(n, grids, stencil, in, out, work, nsteps, &c, workspace,
-                              workspace_bytes, cuda_stream);
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess || last != LOPE_OK) continue;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < bms) {
-        bms = ms;
-        bl = c;
-      }
+    for (int k : {1, 2, 4, 5}) cands.push_back({kPathTrap, t[0], t[1], k, -1});
+  for (const auto& c : cands) {
+    // first call builds and caches the plan's graph; the second is timed
+    if ((last = lope_apply_batch(n, grids, stencil, in, out, work, nsteps, &c, workspace,
+                                 workspace_bytes, cuda_stream)) != LOPE_OK)
+      continue;
+    cudaEventRecord(e0, st);
+    last = lope_apply_batch(n, grids, stencil, in, out, work, nsteps, &c, workspace,
+                            workspace_bytes, cuda_stream);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || last != LOPE_OK) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < bms) {
+      bms = ms;
+      bl = c;
     }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (bl.path == 0) return last != LOPE_OK ? last : fail(LOPE_ERR_UNSUPPORTED, "no batched plan ran");
   g_last_error = "no error";
   {
     std::lock_guard<std::mutex> lk(g_btune_mu);
-    g_btune[batch_sig(n, grids, stencil->s)] = {kPathTrap, bl.tile_x, bl.tile_y, bl.tsteps};
+    g_btune[batch_sig(n, grids, stencil->s)] = {bl.path, bl.tile_x, bl.tile_y, bl.tsteps};
   }
   if (best) *best = bl;
   if (best_ms) *best_ms = bms;

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "tma_device.cuh"
 #include "trap.cuh"
 
 namespace lope {
@@ -115,6 +116,234 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(Op op, BatchPlanDe
   }
 }
 
+// ------------------------------------------------------------------ two sweeps per pass
+// The batched form of the two-sweep 2D tiles (tma2d_tb2_kernel), for FP32 grids
+// of any row pitch: a 64 x TY tile is staged into shared memory with a 2R-row
+// / 4-column halo by 4-byte asynchronous copies (cp.async; the grids' rows need
+// not be 16-byte aligned, as TMA would require), the boundary rule applied as
+// each cell is staged (rows first: the Dirichlet value, stored directly, or
+// the wrapped row; then columns likewise); the first sweep u1 is computed on
+// the tile and its R-wide ring and held at the side's Dirichlet value past a
+// Dirichlet side; the second sweep writes the tile.  The box is free once the
+// first sweep is done, so the next tile's copies are issued before the second
+// sweep and land while it runs.  A pass (two sweeps, or one for the last of an
+// odd count) covers every tile of every grid; passes are separated by the
+// bounded grid-wide barrier, whose acquire orders the next pass's copies
+// after every block's stores.  All threads of a block run the same control
+// flow, so its barriers cannot strand a thread.
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global.L2::128B [%0], [%1], 4;" ::"r"(dst), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+template <class Op, int TY, int RY>
+__global__ void __launch_bounds__(32 * (TY / RY), 2) batch_tb2_kernel(Op op, BatchPlanDev p) {
+  constexpr int TX = 64, R = Op::R, H = 2 * R, CW = 4, W = TX + 2 * CW;  // box columns -4..TX+3
+  static_assert(Op::NF == 1 && Op::STAR && R <= 2, "radius <= 2 star function of one field");
+  constexpr int BH = TY + 2 * H, NW = TY / RY, NT = 32 * NW;
+  constexpr int W1 = TX + 8, NC = RY + 2 * R;
+  constexpr int NRING = 2 * R * 32 + 2 * TY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* box = reinterpret_cast<float*>(smem_raw);
+  float* u1 = box + BH * W;
+  const uint32_t sbox = smem_u32(box);
+  __shared__ volatile int s_abort;
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  const int cx2 = lane * 2, cy0 = warp * RY;
+  if (tid == 0) s_abort = 0;
+  __syncthreads();
+
+  const int64_t passes = (p.nsteps + 1) / 2;
+  for (int64_t pass = 0; pass < passes; ++pass) {
+    const int kp = (pass == passes - 1 && (p.nsteps & 1)) ? 1 : 2;
+    const bool to_out = ((passes - 1 - pass) & 1) == 0;
+    // The tile of an item, its grid's extents and sides in registers.
+    const float* src = nullptr;
+    float* dst = nullptr;
+    int nx = 0, ny = 0, x0 = 0, y0 = 0;
+    int bcy0 = 0, bcy1 = 0, bcx0 = 0, bcx1 = 0;
+    float vy0 = 0.f, vy1 = 0.f, vx0 = 0.f, vx1 = 0.f;
+    auto locate = [&](int item) {
+      const BatchGrid& g = p.grids[find_grid(p.grids, p.ngrids, item)];
+      src = static_cast<const float*>(pass == 0 ? g.in : (to_out ? g.work : g.out));
+      dst = static_cast<float*>(to_out ? g.out : g.work);
+      nx = g.nx;
+      ny = g.ny;
+      bcy0 = g.bc[0][0];
+      bcy1 = g.bc[0][1];
+      bcx0 = g.bc[1][0];
+      bcx1 = g.bc[1][1];
+      vy0 = float(g.bval[0][0]);
+      vy1 = float(g.bval[0][1]);
+      vx0 = float(g.bval[1][0]);
+      vx1 = float(g.bval[1][1]);
+      const int t = item - g.first_item;
+      x0 = (t % g.tiles_x) * TX;
+      y0 = (t / g.tiles_x) * TY;
+    };
+    // Stage the box: warp w takes box rows w, w + NW, ...; lane l the box
+    // columns l, l + 32, l + 64.  The row rule is decided once per row, the
+    // column rule once per column; rows (the slower axis) decide first.
+    auto load = [&]() {
+      int gcol[3];
+      float cval[3];
+      bool cfix[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        int gx = x0 - CW + lane + 32 * k;
+        cfix[k] = false;
+        cval[k] = 0.f;
+        if (gx < 0 || gx >= nx) {
+          const bool lo = gx < 0;
+          if ((lo ? bcx0 : bcx1) == kDirichlet) {
+            cfix[k] = true;
+            cval[k] = lo ? vx0 : vx1;
+          }
+          gx = wrap(gx, nx);
+        }
+        gcol[k] = gx;
+      }
+#pragma unroll 4
+      for (int br = warp; br < BH; br += NW) {
+        int gy = y0 - H + br;
+        bool rfix = false;
+        float rval = 0.f;
+        if (gy < 0 || gy >= ny) {
+          const bool lo = gy < 0;
+          if ((lo ? bcy0 : bcy1) == kDirichlet) {
+            rfix = true;
+            rval = lo ? vy0 : vy1;
+          }
+          gy = wrap(gy, ny);
+        }
+        const float* row = src + int64_t(gy) * nx;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if (lane + 32 * k >= W) break;
+          const int at = br * W + lane + 32 * k;
+          if (rfix) box[at] = rval;
+          else if (cfix[k]) box[at] = cval[k];
+          else cp_async4(sbox + 4u * unsigned(at), row + gcol[k]);
+        }
+      }
+    };
+    if (int(blockIdx.x) < p.nitems) {
+      locate(blockIdx.x);
+      load();
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int item = blockIdx.x; item < p.nitems; item += gridDim.x) {
+      const bool edge = x0 < CW || x0 + TX + CW > nx || y0 < H || y0 + TY + H > ny;
+      // the value past a Dirichlet side, or false where the cell is computed
+      auto held = [&](int tr, int tc, float* v) {
+        const int gy = y0 + tr, gx = x0 + tc;
+        if (gy < 0 && bcy0 == kDirichlet) { *v = vy0; return true; }
+        if (gy >= ny && bcy1 == kDirichlet) { *v = vy1; return true; }
+        if (gx < 0 && bcx0 == kDirichlet) { *v = vx0; return true; }
+        if (gx >= nx && bcx1 == kDirichlet) { *v = vx1; return true; }
+        return false;
+      };
+      auto mask = [&](F2 v, int tr, int tc) {
+        float a = v.lo(), b = v.hi(), h;
+        if (held(tr, tc, &h)) a = h;
+        if (held(tr, tc + 1, &h)) b = h;
+        return F2::make(a, b);
+      };
+      auto sweep1 = [&](auto edge_tag) {
+        constexpr bool EDGE = decltype(edge_tag)::value;
+        F2 col[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) col[k] = ld_pair(box + (H - R + cy0 + k) * W + CW + cx2);
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+          PairAcc<float, TX, TY, R, 1, NC> acc;
+          acc.b[0] = box + (H + cy0 + r) * W + CW + cx2;
+          acc.col = &col;
+          acc.r = r;
+          acc.g = 0;
+          F2 o[1];
+          F2 unused(0.f);
+          op(acc, o, unused);
+          F2 v = o[0];
+          if constexpr (EDGE) v = mask(v, cy0 + r, cx2);
+          st_pair_f(u1 + (R + cy0 + r) * W1 + 4 + cx2, v);
+        }
+        for (int c = tid; c < NRING; c += NT) {
+          int tr, tc;
+          if (c < 2 * R * 32) {
+            const int row = c >> 5;
+            tr = row < R ? row - R : TY + row - R;
+            tc = (c & 31) * 2;
+          } else {
+            const int d = c - 2 * R * 32;
+            tr = d >> 1;
+            tc = (d & 1) ? TX : -2;
+          }
+          Smem2Acc<float, W> acc{box + (H + tr) * W + CW + tc};
+          F2 o[1];
+          F2 unused(0.f);
+          op(acc, o, unused);
+          F2 v = o[0];
+          if constexpr (EDGE) v = mask(v, tr, tc);
+          st_pair_f(u1 + (R + tr) * W1 + 4 + tc, v);
+        }
+      };
+      if (edge) sweep1(BoolTag<true>());
+      else sweep1(BoolTag<false>());
+      __syncthreads();  // u1 complete; the box is free
+      // the tile's output, kept while the next tile is located and its copies issued
+      float* const out = dst;
+      const int onx = nx, ony = ny, ox = x0 + cx2, oy = y0 + cy0;
+      const int next = item + gridDim.x;
+      if (next < p.nitems) {
+        locate(next);
+        load();
+      }
+      auto put = [&](int r, F2 v) {
+        const int gy = oy + r;
+        if (gy >= ony || ox >= onx) return;
+        float* d = out + int64_t(gy) * onx + ox;
+        if (ox + 1 < onx && (reinterpret_cast<uintptr_t>(d) & 7) == 0) {
+          st_pair(d, v);
+        } else {
+          d[0] = v.lo();
+          if (ox + 1 < onx) d[1] = v.hi();
+        }
+      };
+      if (kp == 1) {  // a one-sweep pass: u1 is the result
+#pragma unroll
+        for (int r = 0; r < RY; ++r) put(r, ld_pair(u1 + (R + cy0 + r) * W1 + 4 + cx2));
+      } else {
+        F2 col[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) col[k] = ld_pair(u1 + (cy0 + k) * W1 + 4 + cx2);
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+          PairAcc<float, TX, TY, R, 1, NC> acc;
+          acc.b[0] = u1 + (R + cy0 + r) * W1 + 4 + cx2;
+          acc.col = &col;
+          acc.r = r;
+          acc.g = 0;
+          F2 o[1];
+          F2 unused(0.f);
+          op(acc, o, unused);
+          put(r, o[0]);
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();  // the next box is staged; u1 may be rewritten
+    }
+    const bool arrive = !(pass == 0 && int(blockIdx.x) == p.skip_block);
+    if (pass + 1 < passes &&
+        !grid_sync(p.barrier, unsigned(pass + 1) * gridDim.x, p.err, &s_abort, p.wait_ns, arrive))
+      return;
+  }
+}
+
 template <class Op, class T, class Tile> struct BatchRunner {
   static cudaError_t prepare(size_t smem) {
     return cudaFuncSetAttribute(&batch_kernel<Op, T, Tile>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -172,6 +401,69 @@ auto with_tile(int tx, int ty, int k, F&& f) {
   return f(TileAny());
 }
 
+// Two-sweep register tiles: 8 warps of 16 rows on 64 x 128 tiles, two blocks
+// per SM (one stages while the other computes).
+constexpr int kTb2RY = 16, kTb2Threads = 32 * (kBatchTb2Y / kTb2RY);
+
+template <class Op>
+size_t tb2_smem() {
+  constexpr int R = Op::R, H = 2 * R, W = kBatchTb2X + 8;
+  return (size_t(kBatchTb2Y + 2 * H) * W + size_t(kBatchTb2Y + 2 * R) * (kBatchTb2X + 8)) * 4;
+}
+
+template <class Op>
+struct BatchTb2Runner {
+  static auto kernel() { return &batch_tb2_kernel<Op, kBatchTb2Y, kTb2RY>; }
+  static int max_blocks() {
+    if (cudaFuncSetAttribute(kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(tb2_smem<Op>())) != cudaSuccess)
+      return 0;
+    int occ = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel(), kTb2Threads, tb2_smem<Op>()) !=
+        cudaSuccess)
+      return 0;
+    return occ * sms;
+  }
+  static cudaError_t launch(const Op& op, const BatchPlanDev& p, int blocks, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(tb2_smem<Op>()));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kTb2Threads);
+    cfg.dynamicSmemBytes = tb2_smem<Op>();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kernel(), op, p);
+    count_launches(1);
+    return e;
+  }
+};
+
+// Local functions of the two-sweep batched tiles: the 5-point Jacobi, the
+// 9-point radius-2 star, and linear star tables of radius 1 or 2.
+template <class F> cudaError_t with_tb2_op(const StencilDesc& s, F&& f) {
+  if (s.kind == kJacobi5) return f(OpJacobi5{s.prm[0]});
+  if (s.kind == kStar9r2) return f(OpStar9r2{s.prm[0]});
+  if (s.kind == kLinear && s.star && s.ndim == 2 && s.radius == 1) {
+    OpStarLinear<2, 1> op;
+    for (int ax = 0; ax < 3; ++ax) for (int d = 0; d < 3; ++d) op.w[ax][d] = s.star_w[ax][d];
+    return f(op);
+  }
+  if (s.kind == kLinear && s.star && s.ndim == 2 && s.radius == 2) {
+    OpStarLinear<2, 2> op;
+    for (int ax = 0; ax < 3; ++ax) for (int d = 0; d < 5; ++d) op.w[ax][d] = s.star_w[ax][d];
+    return f(op);
+  }
+  return cudaErrorNotSupported;
+}
+
 template <class T>
 cudaError_t launch_t(const BatchPlanDev& p, const StencilDesc& s, int blocks, cudaStream_t st) {
   const size_t smem = trap_smem_bytes(sizeof(T) == 8 ? kF64 : kF32, 1, p.tile_x, p.tile_y,
@@ -196,6 +488,12 @@ template <class T> int max_blocks_t(const StencilDesc& s, int tx, int ty, int k)
 
 cudaError_t launch_batch(const BatchPlanDev& p, const StencilDesc& s, int dtype, int blocks,
                          cudaStream_t st) {
+  if (p.mode == 1) {
+    if (dtype != kF32) return cudaErrorNotSupported;
+    return with_tb2_op(s, [&](auto op) {
+      return BatchTb2Runner<decltype(op)>::launch(op, p, blocks, st);
+    });
+  }
   if (!(s.kind == kJacobi5 || (s.kind == kLinear && s.star && s.ndim == 2 && s.radius == 1)))
     return cudaErrorNotSupported;
   switch (dtype) {
@@ -206,7 +504,18 @@ cudaError_t launch_batch(const BatchPlanDev& p, const StencilDesc& s, int dtype,
   }
 }
 
-int batch_max_blocks(const StencilDesc& s, int dtype, int tile_x, int tile_y, int ksteps) {
+int batch_max_blocks(const StencilDesc& s, int dtype, int tile_x, int tile_y, int ksteps,
+                     int mode) {
+  if (mode == 1) {
+    if (dtype != kF32 || tile_x != kBatchTb2X || tile_y != kBatchTb2Y || ksteps < 1 || ksteps > 2)
+      return 0;
+    int b = 0;
+    with_tb2_op(s, [&](auto op) {
+      b = BatchTb2Runner<decltype(op)>::max_blocks();
+      return cudaSuccess;
+    });
+    return b;
+  }
   if (!(s.kind == kJacobi5 || (s.kind == kLinear && s.star && s.ndim == 2 && s.radius == 1)))
     return 0;
   switch (dtype) {

@@ -272,3 +272,45 @@ def test_batch_autotuner_choice_is_used_and_bitwise_equal(lope):
                            launch=lope.Launch(2, best.tile_x, best.tile_y, best.tsteps, -1))
         torch.cuda.synchronize()
         assert torch.equal(alone, a)
+
+
+@pytest.mark.parametrize("kind,prm,halo", [("jacobi5", [0.2], 1), ("star9r2", [0.1], 2)])
+def test_batch_two_sweep_tiles_equal_per_grid_and_oracle(lope, orc, kind, prm, halo):
+    """The two-sweep batched tiles (path 1): uneven grids of any row pitch,
+    periodic and Dirichlet sides (non-zero values included), even and odd step
+    counts (an odd count ends with a one-sweep pass): bitwise equal to each
+    grid advanced alone, and within T eps of the oracle."""
+    shapes, kinds = LI.batch_shapes(85, 12, lo=5, hi=400)
+    shapes[0], shapes[1] = (1, 7), (130, 3)  # a single row; fewer columns than the radius
+    kinds[0], kinds[1] = 1, 1
+    bvals = [((0.3, -0.2), (0.0, 0.5)) if k == 1 and i % 2 else ((0.0, 0.0), (0.0, 0.0))
+             for i, k in enumerate(kinds)]
+    grids, ins, stored = [], [], []
+    off = 0
+    for (ny, nx), k, bv in zip(shapes, kinds, bvals):
+        g = lope.Grid((ny, nx), "f32", halo=halo)
+        if k == 1:
+            g.set_boundaries([(1, 1), (1, 1)], list(bv))
+        grids.append(g)
+        u = LI.uniform(86, ny * nx, off).reshape(ny, nx)
+        off += ny * nx
+        t, st_ = to_device(u, "f32")
+        ins.append(t)
+        stored.append(st_)
+    st = lope.Stencil.builtin(kind, *prm)
+    for T in (6, 7):
+        outs = lope.apply_batch(grids, st, ins, nsteps=T, launch=lope.Launch(1, 64, 128, 2, -1))
+        torch.cuda.synchronize()
+        lope.sync_status()
+        for gi, (g, i, o) in enumerate(zip(grids, ins, outs)):
+            alone = lope.apply(g, st, i, nsteps=T, launch=lope.Launch(3, 0, 0, 0, -1))
+            torch.cuda.synchronize()
+            assert torch.equal(alone, o), (T, gi, shapes[gi])
+    for gi in (0, 1, 2, 5):
+        k = kinds[gi]
+        bc = [(k, k), (k, k)]
+        want = orc.apply(stored[gi], kind, prm, 7, bc=bc, bval=list(bvals[gi]))
+        G = 1.0 if kind == "jacobi5" else 1.0667
+        M = max(1.0, *(abs(v) for pair in bvals[gi] for v in pair))
+        eps = float(local_eps(kind, prm, [M * G ** 7], "f32")[0])
+        assert np.max(np.abs(to_host(outs[gi]) - want)) <= 7 * G ** 7 * eps, gi
