@@ -159,6 +159,23 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// Asynchronous copy of one 4- or 8-byte element from global to shared memory
+// (cp.async through L1 and L2, 128-byte L2 fetches).  Many can be in flight
+// per thread; they complete at cp_async_wait_all.
+template <int B>
+__device__ __forceinline__ void cp_async_elem(uint32_t dst, const void* src) {
+  static_assert(B == 4 || B == 8, "element copies of 4 or 8 bytes");
+  if constexpr (B == 4)
+    asm volatile("cp.async.ca.shared.global.L2::128B [%0], [%1], 4;" ::"r"(dst), "l"(src)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global.L2::128B [%0], [%1], 8;" ::"r"(dst), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }

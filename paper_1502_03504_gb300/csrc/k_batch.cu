@@ -6,9 +6,10 @@
 // barrier before the next pass reads what this one wrote — the one-GPU form
 // of "all threads finish the loop body, then the halo transfer synchronises"
 // (Sec. 3.2).  The barrier wait is bounded: after kWaitLimitNs it records a
-// timeout in the error flag and the kernel returns.  Loads in later passes go
-// through L2 (ld.global.cg), so no block reads a stale L1 line of data another
-// block wrote in the previous pass.
+// timeout in the error flag and the kernel returns.  The barrier's GPU-scope
+// acquire, passed on to the whole block by its CTA barrier, orders every read
+// of the next pass (the asynchronous window copies included) after the stores
+// every block made in this one.
 #include <algorithm>
 #include <type_traits>
 
@@ -131,14 +132,6 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(Op op, BatchPlanDe
 // bounded grid-wide barrier, whose acquire orders the next pass's copies
 // after every block's stores.  All threads of a block run the same control
 // flow, so its barriers cannot strand a thread.
-__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global.L2::128B [%0], [%1], 4;" ::"r"(dst), "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
 template <class Op, int TY, int RY>
 __global__ void __launch_bounds__(32 * (TY / RY), 2) batch_tb2_kernel(Op op, BatchPlanDev p) {
   constexpr int TX = 64, R = Op::R, H = 2 * R, CW = 4, W = TX + 2 * CW;  // box columns -4..TX+3
@@ -226,7 +219,7 @@ __global__ void __launch_bounds__(32 * (TY / RY), 2) batch_tb2_kernel(Op op, Bat
           const int at = br * W + lane + 32 * k;
           if (rfix) box[at] = rval;
           else if (cfix[k]) box[at] = cval[k];
-          else cp_async4(sbox + 4u * unsigned(at), row + gcol[k]);
+          else cp_async_elem<4>(sbox + 4u * unsigned(at), row + gcol[k]);
         }
       }
     };

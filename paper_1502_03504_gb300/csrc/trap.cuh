@@ -56,6 +56,32 @@ __device__ __forceinline__ bool outside_dirichlet(const TrapGrid& g, int gy, int
   return false;
 }
 
+// Stage the window cell at global (gy, gx) into `cell`: the Dirichlet value
+// past a Dirichlet side (stored directly), else the element at the wrapped
+// position.  Where the stored and computed types agree (FP32, FP64) the
+// element moves by an asynchronous copy, so a thread keeps every copy of the
+// window in flight at once; the caller ends the fill with cp_async_wait_all
+// and a block barrier.  BF16 is widened on the way, by a load and a store.
+template <class T>
+__device__ __forceinline__ void stage_cell(C_t<T>* cell, const T* src, const TrapGrid& g, int gy,
+                                           int gx, bool inside) {
+  using C = C_t<T>;
+  if constexpr (sizeof(T) == sizeof(C)) {
+    if (!inside) {
+      double v;
+      if (outside_dirichlet(g, gy, gx, &v)) {
+        *cell = C(v);
+        return;
+      }
+      gy = wrap(gy, g.ny);
+      gx = wrap(gx, g.nx);
+    }
+    cp_async_elem<sizeof(T)>(smem_u32(cell), src + int64_t(gy) * g.nx + gx);
+  } else {
+    *cell = inside ? to_c(__ldcg(src + int64_t(gy) * g.nx + gx)) : halo_read<T>(src, g, gy, gx);
+  }
+}
+
 // One tile: k sweeps from src to dst.  smem holds 2 * NF * H * W values of C.
 // Threads walk the window as a 2D grid (threadIdx.x along x in steps of 32,
 // the rest of the block along y), so no cell index is divided.
@@ -77,11 +103,10 @@ __device__ __forceinline__ void trap_tile(const Op& op, const T* const* src, T* 
     for (int i = tx; i < W; i += 32) {
       const int gx = x0 - h + i;
 #pragma unroll
-      for (int f = 0; f < NF; ++f)
-        b0[f * HW + j * W + i] = inside ? to_c(__ldcg(src[f] + int64_t(gy) * g.nx + gx))
-                                        : halo_read<T>(src[f], g, gy, gx);
+      for (int f = 0; f < NF; ++f) stage_cell<T>(b0 + f * HW + j * W + i, src[f], g, gy, gx, inside);
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   for (int s = 1; s <= k; ++s) {
     const C* cur = (s & 1) ? b0 : b1;
@@ -175,11 +200,11 @@ struct TrapFixed {
           const int gx = x0 - h + i;
 #pragma unroll
           for (int f = 0; f < NF; ++f)
-            b0[f * HW + j * W + i] = inside ? to_c(__ldcg(src[f] + int64_t(gy) * g.nx + gx))
-                                            : halo_read<T>(src[f], g, gy, gx);
+            stage_cell<T>(b0 + f * HW + j * W + i, src[f], g, gy, gx, inside);
         }
       }
     }
+    cp_async_wait_all();
     __syncthreads();
     for (int s = 1; s <= kp; ++s) {
       const C* cur = (s & 1) ? b0 : b1;
@@ -298,11 +323,10 @@ __device__ __forceinline__ void trap_tile_rk(const Op& op, const T* const* src, 
     for (int i = tx; i < W; i += 32) {
       const int gx = x0 - h + i;
 #pragma unroll
-      for (int f = 0; f < NF; ++f)
-        bu[f * HW + j * W + i] = inside ? to_c(__ldcg(src[f] + int64_t(gy) * g.nx + gx))
-                                        : halo_read<T>(src[f], g, gy, gx);
+      for (int f = 0; f < NF; ++f) stage_cell<T>(bu + f * HW + j * W + i, src[f], g, gy, gx, inside);
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   Coef a2, b2c, a3, b3c;
   {
