@@ -7,8 +7,8 @@
 //    from global memory through the boundary rule (2D and 3D).  This is the
 //    plainest GPU form of "call the local function for each interior index"
 //    (Sec. 2.2, Sec. 3.2) and serves shapes the TMA path cannot take;
-//  * march3d_plain_kernel — 3D planes marched along z through a shared-memory
-//    ring, for grids the TMA tiles cannot stage.
+//  * march3d_plain_kernel / march3d_async_kernel — 3D planes marched along z
+//    through a shared-memory ring, for grids the TMA tiles cannot stage.
 #pragma once
 
 #include "trap.cuh"
@@ -289,6 +289,168 @@ __global__ void __launch_bounds__(256) march3d_plain_kernel(Op op, const __grid_
       for (int f = 0; f < NF; ++f) dst[f][acc.p] = from_c<T>(o[f]);
     }
   }
+}
+
+// The plane march for FP32 and FP64 grids (stored type = compute type).  A
+// 256-thread block owns a kAsyncX x kAsyncY tile of (x, y) columns; thread
+// (tx, ty) computes the kAsyncRY consecutive rows ty * kAsyncRY + r of column
+// tx, holding that column of the current plane (its halo rows included) in
+// registers, so only the off-column taps read shared memory.  The window
+// cells move by asynchronous element copies (cp.async) straight into their
+// ring slot, PF planes ahead of the plane being computed, so a block keeps PF
+// planes of loads in flight without holding them in registers; cells given by
+// a Dirichlet side are stored directly.  One copy group per plane: before
+// computing plane z a thread waits until its copies of planes up to z + R
+// have landed (at most PF - 1 younger groups pending), then the block barrier
+// makes every thread's copies and stores visible and frees the slot of plane
+// z - R - 1, which is refilled with plane z + R + PF.  The ring holds
+// 2R + 1 + PF planes.  Every tap reads what the direct kernel reads.
+constexpr int kAsyncX = 64, kAsyncY = 16, kAsyncRY = 4;
+
+// Planes in flight, and the ring's bytes (dynamic shared memory): up to four
+// planes ahead within a 64 KB ring.
+template <class C, int NF, int R>
+__host__ __device__ constexpr int march_async_depth() {
+  constexpr int slot = NF * (kAsyncX + 2 * R) * (kAsyncY + 2 * R) * int(sizeof(C));
+  constexpr int fit = (64 * 1024) / slot - (2 * R + 1);
+  return fit < 1 ? 1 : fit > 4 ? 4 : fit;
+}
+template <class C, int NF, int R>
+__host__ __device__ constexpr int march_async_smem() {
+  return (2 * R + 1 + march_async_depth<C, NF, R>()) * NF * (kAsyncX + 2 * R) *
+         (kAsyncY + 2 * R) * int(sizeof(C));
+}
+
+template <class C, int NF, int W, int CELLS, int R, int RY>
+struct MarchColAcc {
+  const C* pl[2 * R + 1];             // plane z + dz, at this thread's first output cell
+  const C (*col)[NF][RY + 2 * R];     // plane z, this column, rows -R .. RY - 1 + R
+  int r;                              // output row within the thread's rows
+  int64_t p;                          // global index of the output
+  __device__ __forceinline__ C operator()(int f, int dx, int dy, int dz) const {
+    if (dx == 0 && dz == 0) return (*col)[f][r + R + dy];
+    return pl[dz + R][f * CELLS + (r + dy) * W + dx];
+  }
+  __device__ __forceinline__ int64_t gidx() const { return p; }
+};
+
+template <class Op, class T>
+__global__ void __launch_bounds__(256) march3d_async_kernel(Op op, const __grid_constant__ Geom g,
+                                                            const T* in0, const T* in1,
+                                                            const T* in2, T* out0, T* out1,
+                                                            T* out2, int zchunk) {
+  using C = C_t<T>;
+  static_assert(sizeof(C) == sizeof(T), "stored type copied as is");
+  constexpr int R = Op::R, NF = Op::NF, RY = kAsyncRY;
+  constexpr int W = kAsyncX + 2 * R, H = kAsyncY + 2 * R, CELLS = W * H;
+  constexpr int PER = (CELLS + 255) / 256;
+  constexpr int PF = march_async_depth<C, NF, R>(), NS = 2 * R + 1 + PF;
+  static_assert(kAsyncX * kAsyncY == 256 * RY, "RY outputs per thread and plane");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* const ring = reinterpret_cast<C*>(smem_raw);  // NS planes x NF fields x CELLS
+  const T* src[3] = {in0, in1, in2};
+  T* dst[3] = {out0, out1, out2};
+  const int nz = int(g.n[0]), ny = int(g.n[1]), nx = int(g.n[2]);
+  const int tiles_x = (nx + kAsyncX - 1) / kAsyncX, tiles_y = (ny + kAsyncY - 1) / kAsyncY;
+  const unsigned ntiles = unsigned(tiles_x) * unsigned(tiles_y);
+  const int tile = int(blockIdx.x % ntiles), chunk = int(blockIdx.x / ntiles);
+  const int x0 = (tile % tiles_x) * kAsyncX, y0 = (tile / tiles_x) * kAsyncY;
+  const int z0 = chunk * zchunk, z1 = min(nz, z0 + zchunk);
+  if (z0 >= z1) return;  // the whole block
+  const int64_t plane = int64_t(nx) * ny;
+  // This thread's window cells: the in-plane position of the source value, or
+  // which Dirichlet side gives it (1, 2: y low / high; 3, 4: x low / high),
+  // or -1 for a cell no output reads (past the tile's valid cells + R).
+  const int xend = min(x0 + kAsyncX, nx) + R, yend = min(y0 + kAsyncY, ny) + R;
+  int64_t cpos[PER];
+  int ccode[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int e = int(threadIdx.x) + 256 * j;
+    const int gy = y0 - R + e / W, gx = x0 - R + e % W;
+    cpos[j] = 0;
+    if (e >= CELLS || gx >= xend || gy >= yend) {
+      ccode[j] = -1;
+      continue;
+    }
+    const int yy = axis_index(gy, ny, g.bc[1][0], g.bc[1][1]);
+    const int xx = axis_index(gx, nx, g.bc[2][0], g.bc[2][1]);
+    if (yy < 0) ccode[j] = yy == -1 ? 1 : 2;
+    else if (xx < 0) ccode[j] = xx == -1 ? 3 : 4;
+    else {
+      ccode[j] = 0;
+      cpos[j] = int64_t(yy) * nx + xx;
+    }
+  }
+  const uint32_t sring = smem_u32(ring);
+  auto slot = [&](int v) { return (v - z0 + R) % NS; };
+  // Issue plane v into its slot and close its copy group (empty past the chunk).
+  auto issue = [&](int v) {
+    if (v < z1 + R) {
+      const int zz = axis_index(v, nz, g.bc[0][0], g.bc[0][1]);
+      const int base = slot(v) * NF * CELLS + int(threadIdx.x);
+      const T* s0 = src[0] + (zz < 0 ? 0 : int64_t(zz) * plane);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T* sf = f == 0 ? s0 : src[f] + (zz < 0 ? 0 : int64_t(zz) * plane);
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+          const int c = ccode[j];
+          if (c < 0) continue;
+          const int e = base + f * CELLS + 256 * j;
+          if (zz < 0) ring[e] = C(g.bval[0][zz == -1 ? 0 : 1]);
+          else if (c == 0)
+            cp_async_elem<int(sizeof(T))>(sring + unsigned(e) * unsigned(sizeof(C)), sf + cpos[j]);
+          else ring[e] = C(g.bval[(c + 1) / 2][(c + 1) % 2]);
+        }
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  for (int v = z0 - R; v < z0 + R + PF; ++v) issue(v);
+  const int tx = int(threadIdx.x) % kAsyncX, ty = int(threadIdx.x) / kAsyncX;
+  const int x = x0 + tx, yb = y0 + ty * RY;
+  const int cell0 = (ty * RY + R) * W + tx + R;  // window offset of the first output
+  MarchColAcc<C, NF, W, CELLS, R, RY> acc;
+  C col[NF][RY + 2 * R];
+  acc.col = &col;
+  for (int z = z0; z < z1; ++z) {
+    asm volatile("cp.async.wait_group %0;" ::"n"(PF - 1) : "memory");
+    __syncthreads();
+    issue(z + R + PF);
+    if (x < nx && yb < ny) {
+      int sl = slot(z - R);
+#pragma unroll
+      for (int d = 0; d < 2 * R + 1; ++d) {
+        acc.pl[d] = ring + sl * NF * CELLS + cell0;
+        sl = sl + 1 == NS ? 0 : sl + 1;
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int k = 0; k < RY + 2 * R; ++k) col[f][k] = acc.pl[R][f * CELLS + (k - R) * W];
+      const int64_t p0 = (int64_t(z) * ny + yb) * nx + x;
+      auto row = [&](int r) {
+        acc.r = r;
+        acc.p = p0 + int64_t(r) * nx;
+        C o[NF];
+        C r1 = C(0);
+        op(acc, o, r1);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) dst[f][acc.p] = from_c<T>(o[f]);
+      };
+      if constexpr (Op::STAR || R == 1) {
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+          if (yb + r < ny) row(r);
+      } else {  // 125-tap boxes: one row at a time keeps the weights in registers
+#pragma unroll 1
+        for (int r = 0; r < RY; ++r)
+          if (yb + r < ny) row(r);
+      }
+    }
+  }
+  cp_async_wait_all();
 }
 
 }  // namespace

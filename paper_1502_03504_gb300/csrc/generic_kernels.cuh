@@ -106,12 +106,12 @@ cudaError_t run_direct(const StepArgs& a, const Op& op, int* blocks_out) {
   return cudaGetLastError();
 }
 
-// Plane march geometry: kMarchX x kMarchY column tiles; z cut into chunks of
-// at least 16 planes so that about two waves of 256-thread blocks (eight per
-// SM) are in flight (each chunk stages 2R extra planes).
-inline bool march_geometry(const Geom& g, int* blocks, int* zchunk) {
-  const int64_t tiles = ((g.n[2] + kMarchX - 1) / kMarchX) * ((g.n[1] + kMarchY - 1) / kMarchY);
-  const int64_t slots = 2 * 8 * 152;
+// Plane march geometry: tx x ty column tiles; z cut into chunks of at least
+// 16 planes so that about two waves of 256-thread blocks (per_sm per SM) are
+// in flight (each chunk stages 2R extra planes).
+inline bool march_geometry_t(const Geom& g, int tx, int ty, int per_sm, int* blocks, int* zchunk) {
+  const int64_t tiles = ((g.n[2] + tx - 1) / tx) * ((g.n[1] + ty - 1) / ty);
+  const int64_t slots = 2 * int64_t(per_sm) * 152;
   int64_t nzc = std::max<int64_t>(1, std::min<int64_t>(g.n[0] / 16, (slots + tiles - 1) / tiles));
   const int64_t zc = (g.n[0] + nzc - 1) / nzc;
   nzc = (g.n[0] + zc - 1) / zc;
@@ -120,19 +120,70 @@ inline bool march_geometry(const Geom& g, int* blocks, int* zchunk) {
   *zchunk = int(zc);
   return true;
 }
+// The same cut for the asynchronous march, counted in whole waves: among the
+// chunk counts that keep 16 planes or more per chunk, the one that maximises
+// the busy fraction of the last wave times the share of planes that are not
+// halo (each chunk stages 2R planes twice).
+inline bool march_chunks(const Geom& g, int tx, int ty, int R, int per_sm, int* blocks,
+                         int* zchunk) {
+  const int64_t tiles = ((g.n[2] + tx - 1) / tx) * ((g.n[1] + ty - 1) / ty);
+  const int64_t conc = int64_t(per_sm) * 152;
+  const int64_t most = std::max<int64_t>(1, std::min<int64_t>(g.n[0] / 16, 4 * conc / tiles + 1));
+  double best = -1.0;
+  int64_t bzc = g.n[0], bn = 1;
+  for (int64_t n = 1; n <= most; ++n) {
+    const int64_t zc = (g.n[0] + n - 1) / n, nzc = (g.n[0] + zc - 1) / zc;
+    const int64_t b = tiles * nzc, waves = (b + conc - 1) / conc;
+    const double score = double(b) / double(waves * conc) * double(zc) / double(zc + 2 * R);
+    if (score > best + 1e-9) {
+      best = score;
+      bzc = zc;
+      bn = nzc;
+    }
+  }
+  if (tiles * bn > int64_t(0x7fffffff)) return false;
+  *blocks = int(tiles * bn);
+  *zchunk = int(bzc);
+  return true;
+}
+inline bool march_geometry(const Geom& g, int* blocks, int* zchunk) {
+  return march_geometry_t(g, kMarchX, kMarchY, 8, blocks, zchunk);
+}
 
+// FP32 / FP64 grids take the asynchronous-copy march (64 x 16 tiles, four
+// rows per thread), BF16 grids the register-staged one (widened on load).
 template <class Op, class T>
 cudaError_t run_march(const StepArgs& a, const Op& op) {
-  int blocks = 0, zchunk = 0;
-  if (!march_geometry(a.g, &blocks, &zchunk)) return cudaErrorInvalidConfiguration;
   const T* in[3] = {nullptr, nullptr, nullptr};
   T* out[3] = {nullptr, nullptr, nullptr};
   for (int f = 0; f < Op::NF; ++f) {
     in[f] = static_cast<const T*>(a.in[f]);
     out[f] = static_cast<T*>(a.out[f]);
   }
-  march3d_plain_kernel<Op, T><<<blocks, 256, 0, a.stream>>>(op, a.g, in[0], in[1], in[2], out[0],
-                                                             out[1], out[2], zchunk);
+  int blocks = 0, zchunk = 0;
+  if constexpr (sizeof(T) == sizeof(C_t<T>)) {
+    constexpr int smem = march_async_smem<C_t<T>, Op::NF, Op::R>();
+    auto kern = &march3d_async_kernel<Op, T>;
+    static int per_sm = 0;  // resident blocks per SM, measured once per instance
+    if (per_sm == 0) {
+      if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+      }
+      int n = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 256, smem);
+      if (e != cudaSuccess) return e;
+      per_sm = std::max(1, n);
+    }
+    if (!march_chunks(a.g, kAsyncX, kAsyncY, Op::R, per_sm, &blocks, &zchunk))
+      return cudaErrorInvalidConfiguration;
+    kern<<<blocks, 256, smem, a.stream>>>(op, a.g, in[0], in[1], in[2], out[0], out[1], out[2],
+                                          zchunk);
+  } else {
+    if (!march_geometry(a.g, &blocks, &zchunk)) return cudaErrorInvalidConfiguration;
+    march3d_plain_kernel<Op, T><<<blocks, 256, 0, a.stream>>>(op, a.g, in[0], in[1], in[2],
+                                                               out[0], out[1], out[2], zchunk);
+  }
   count_launches(1);
   return cudaGetLastError();
 }

@@ -100,10 +100,14 @@ def test_direct_wide_and_narrow_rows(lope, orc):
 MARCH, DIRECT = 4, 3
 
 
+# 45 and 131 points per row: no TMA staging for any storage type.  The second
+# shape spans several column tiles with ragged tails and four z chunks, each
+# refilling its plane ring from its own first planes.
+@pytest.mark.parametrize("shape", [(21, 19, 45), (70, 37, 131)], ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f64"])
 @pytest.mark.parametrize("bc", [[0, 0, 0], [1, 1, 1], [0, 1, 0], [1, 0, 1]])
-def test_3d_march_equals_direct(lope, dtype, bc):
-    shape, T = (21, 19, 45), 5  # 45 points per row: no TMA staging for any storage type
+def test_3d_march_equals_direct(lope, dtype, bc, shape):
+    T = 5
     u, _ = to_device(LI.uniform_field(1440, shape), dtype)
     rng = np.random.default_rng(1441)
     box = rng.uniform(-0.1, 0.1, (3, 3, 3))
