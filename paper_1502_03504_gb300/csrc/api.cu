@@ -1363,6 +1363,7 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
     plan->dev.ksteps = k;
     plan->dev.nsteps = nsteps;
     plan->dev.barrier = reinterpret_cast<unsigned int*>(ws);
+    plan->dev.claim = reinterpret_cast<unsigned long long*>(ws + 128);
     plan->dev.err = d->err;
     plan->dev.wait_ns = (unsigned long long)wait_ms * 1000000ull;
     plan->dev.skip_block = int(skip);

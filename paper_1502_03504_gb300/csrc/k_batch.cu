@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(32 * (TY / RY), 2) batch_tb2_kernel(Op op, Bat
   float* u1 = box + BH * W;
   const uint32_t sbox = smem_u32(box);
   __shared__ volatile int s_abort;
+  __shared__ int s_claim;
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   const int cx2 = lane * 2, cy0 = warp * RY;
   if (tid == 0) s_abort = 0;
@@ -153,6 +154,17 @@ __global__ void __launch_bounds__(32 * (TY / RY), 2) batch_tb2_kernel(Op op, Bat
   for (int64_t pass = 0; pass < passes; ++pass) {
     const int kp = (pass == passes - 1 && (p.nsteps & 1)) ? 1 : 2;
     const bool to_out = ((passes - 1 - pass) & 1) == 0;
+    // Tiles are claimed one at a time from a counter (the next one while the
+    // current one is swept), so blocks finish a pass together whatever their
+    // tiles cost.  A block stops at its first claim past the list, so each
+    // pass takes exactly nitems + gridDim.x claims and pass `pass` starts
+    // from pass * (nitems + gridDim.x).
+    const unsigned long long pbase =
+        (unsigned long long)pass * (unsigned long long)(p.nitems + int(gridDim.x));
+    auto claim = [&]() {
+      const unsigned long long v = atomicAdd(p.claim, 1ull) - pbase;
+      return v < (unsigned long long)p.nitems ? int(v) : -1;
+    };
     // The tile of an item, its grid's extents and sides in registers.
     const float* src = nullptr;
     float* dst = nullptr;
@@ -223,28 +235,31 @@ __global__ void __launch_bounds__(32 * (TY / RY), 2) batch_tb2_kernel(Op op, Bat
         }
       }
     };
-    if (int(blockIdx.x) < p.nitems) {
-      locate(blockIdx.x);
+    if (tid == 0) s_claim = claim();
+    __syncthreads();
+    int item = s_claim;
+    if (item >= 0) {
+      locate(item);
       load();
     }
     cp_async_wait_all();
     __syncthreads();
-    for (int item = blockIdx.x; item < p.nitems; item += gridDim.x) {
+    while (item >= 0) {
+      if (tid == 0) s_claim = claim();  // published by the barrier after the first sweep
       const bool edge = x0 < CW || x0 + TX + CW > nx || y0 < H || y0 + TY + H > ny;
-      // the value past a Dirichlet side, or false where the cell is computed
-      auto held = [&](int tr, int tc, float* v) {
-        const int gy = y0 + tr, gx = x0 + tc;
-        if (gy < 0 && bcy0 == kDirichlet) { *v = vy0; return true; }
-        if (gy >= ny && bcy1 == kDirichlet) { *v = vy1; return true; }
-        if (gx < 0 && bcx0 == kDirichlet) { *v = vx0; return true; }
-        if (gx >= nx && bcx1 == kDirichlet) { *v = vx1; return true; }
-        return false;
-      };
+      // Cells past a Dirichlet side keep its value: tile rows outside
+      // [row_lo, row_hi) and columns outside [col_lo, col_hi) (rows first,
+      // then columns, the order of the boundary rule).
+      constexpr int kFar = 1 << 30;
+      const int row_lo = bcy0 == kDirichlet ? -y0 : -kFar;
+      const int row_hi = bcy1 == kDirichlet ? ny - y0 : kFar;
+      const int col_lo = bcx0 == kDirichlet ? -x0 : -kFar;
+      const int col_hi = bcx1 == kDirichlet ? nx - x0 : kFar;
+      auto cell = [&](float v, int tc) { return tc < col_lo ? vx0 : tc >= col_hi ? vx1 : v; };
       auto mask = [&](F2 v, int tr, int tc) {
-        float a = v.lo(), b = v.hi(), h;
-        if (held(tr, tc, &h)) a = h;
-        if (held(tr, tc + 1, &h)) b = h;
-        return F2::make(a, b);
+        if (tr < row_lo) return F2::make(vy0, vy0);
+        if (tr >= row_hi) return F2::make(vy1, vy1);
+        return F2::make(cell(v.lo(), tc), cell(v.hi(), tc + 1));
       };
       auto sweep1 = [&](auto edge_tag) {
         constexpr bool EDGE = decltype(edge_tag)::value;
@@ -291,8 +306,8 @@ __global__ void __launch_bounds__(32 * (TY / RY), 2) batch_tb2_kernel(Op op, Bat
       // the tile's output, kept while the next tile is located and its copies issued
       float* const out = dst;
       const int onx = nx, ony = ny, ox = x0 + cx2, oy = y0 + cy0;
-      const int next = item + gridDim.x;
-      if (next < p.nitems) {
+      const int next = s_claim;
+      if (next >= 0) {
         locate(next);
         load();
       }
@@ -329,6 +344,7 @@ __global__ void __launch_bounds__(32 * (TY / RY), 2) batch_tb2_kernel(Op op, Bat
       }
       cp_async_wait_all();
       __syncthreads();  // the next box is staged; u1 may be rewritten
+      item = next;
     }
     const bool arrive = !(pass == 0 && int(blockIdx.x) == p.skip_block);
     if (pass + 1 < passes &&

@@ -161,6 +161,7 @@ struct BatchPlanDev {
   int ksteps;
   int64_t nsteps;
   unsigned int* barrier;   // device counter, zeroed before each launch
+  unsigned long long* claim;  // device tile-claim counter, zeroed before each launch
   int* err;
   unsigned long long wait_ns;  // limit of each barrier wait
   int skip_block;              // test hook: this block skips its first arrival (-1: none)
