@@ -247,9 +247,11 @@ def main():
                     help="keep the nvidia-smi clock samples of the timed region in this folder")
     ap.add_argument("--profile", default=None,
                     help="run one kernel workload for --steps launches and exit (for ncu): "
-                         "diff7:N, diff7p:N, star9r2:N, jacobi5:N, swe:N, swebf16:N, with an "
-                         "optional boundary spec per axis, slowest first, e.g. diff7:512:DDP "
-                         "(D Dirichlet 0, P periodic), and :k2 for two sweeps per launch")
+                         "diff7:N, diff7p:N, star9r2:N, jacobi5:N, swe:N, swebf16:N, sweflux:N, "
+                         "swefluxbf16:N, with an optional boundary spec per axis, slowest first, "
+                         "e.g. diff7:512:DDP (D Dirichlet 0, P periodic), and :k2 for two sweeps "
+                         "per launch; batch:NGRIDS[:trap] for the first NGRIDS grids of the "
+                         "batched workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -498,7 +500,7 @@ def run_profile(args):
         kind, nf = "periodic", 3
         dtype, bpp = ("f32", 24) if name == "swe" else ("bf16", 12)
     elif name == "batch":
-        return run_profile_batch(args, n)
+        return run_profile_batch(args, n, trap="trap" in parts[2:])
     elif name in ("sweflux", "swefluxbf16"):
         shape, halo, pts = (n, n), 1, n * n
         st = L.Stencil.builtin("swe_flux", 0.02, 1.0, 0.5, 1.0)
@@ -532,9 +534,10 @@ def run_profile(args):
                       "alg_GBps": bpp * pts / (us * 1e-6) / 1e9}), flush=True)
 
 
-def run_profile_batch(args, ngrids):
+def run_profile_batch(args, ngrids, trap=False):
     """The first `ngrids` grids of the batched workload: one batched launch per
-    step (tile 128 x 32, 4 sweeps per pass, 4 sweeps = one pass)."""
+    step of 4 sweeps; the planner's default (two-sweep tiles, two passes) or,
+    with `trap`, the trapezoid tiles (128 x 32, 4 sweeps = one pass)."""
     import torch
 
     import lope_inputs as LI
@@ -552,7 +555,7 @@ def run_profile_batch(args, ngrids):
     outs = [torch.empty_like(x) for x in ins]
     works = [torch.empty_like(x) for x in ins]
     s = L.Stencil.builtin("jacobi5", 0.2)
-    cfg = L.Launch(2, 128, 32, 4, -1)
+    cfg = L.Launch(2, 128, 32, 4, -1) if trap else None
     wsb = torch.empty(L.batch_workspace_size(grids, s), dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         L.apply_batch(grids, s, ins, outs, works, 4, cfg, wsb)

@@ -737,6 +737,7 @@ struct BatchPlan {
   BatchPlanDev dev;
   cudaGraphExec_t exec = nullptr;
   int blocks = 0;
+  int64_t kernels = 1;  // kernel launches per replay
   ~BatchPlan() {
     if (exec) cudaGraphExecDestroy(exec);
     if (pinned) cudaFreeHost(pinned);
@@ -745,7 +746,20 @@ struct BatchPlan {
 std::mutex g_batch_mu;
 std::map<std::vector<int64_t>, std::shared_ptr<BatchPlan>> g_batch;
 
-size_t batch_ws_bytes(int n) { return 256 + (size_t(n) * sizeof(BatchGrid) + 255) / 256 * 256; }
+// Batch workspace: the barrier and claim counters (256 B), the grid list, and
+// one record per tile of the two-sweep batched tiles (64 x 128 tiles).
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+int64_t batch_tb2_items(int n, const lope_grid* const* grids) {
+  int64_t items = 0;
+  for (int i = 0; i < n; ++i)
+    items += ((grids[i]->g.n[2] + kBatchTb2X - 1) / kBatchTb2X) *
+             ((grids[i]->g.n[1] + kBatchTb2Y - 1) / kBatchTb2Y);
+  return items;
+}
+size_t batch_ws_bytes(int n, const lope_grid* const* grids) {
+  return 256 + round256(size_t(n) * sizeof(BatchGrid)) +
+         round256(size_t(batch_tb2_items(n, grids)) * sizeof(BatchItem));
+}
 
 // Batch autotuner cache: the fastest (tile, depth) per batch signature (grid
 // shapes and boundaries, dtype, stencil), filled by lope_autotune_batch.
@@ -1245,7 +1259,9 @@ lope_status lope_batch_workspace_size(int n, const lope_grid* const* grids,
                                       size_t* bytes) {
   (void)cfg;
   if (n < 1 || !grids || !stencil || !bytes) return fail(LOPE_ERR_INVALID, "bad argument");
-  *bytes = batch_ws_bytes(n);
+  for (int i = 0; i < n; ++i)
+    if (!grids[i]) return fail(LOPE_ERR_INVALID, "NULL grid");
+  *bytes = batch_ws_bytes(n, grids);
   return LOPE_OK;
 }
 
@@ -1256,7 +1272,10 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
   if (n < 1 || !grids || !stencil || !in || !out || !workspace)
     return fail(LOPE_ERR_INVALID, "NULL argument");
   if (nsteps < 1) return fail(LOPE_ERR_INVALID, "nsteps must be >= 1");
-  if (workspace_bytes < batch_ws_bytes(n)) return fail(LOPE_ERR_ALLOC, "batch workspace too small");
+  for (int i = 0; i < n; ++i)
+    if (!grids[i]) return fail(LOPE_ERR_INVALID, "NULL grid");
+  if (workspace_bytes < batch_ws_bytes(n, grids))
+    return fail(LOPE_ERR_ALLOC, "batch workspace too small");
   if (!aligned16(workspace)) return fail(LOPE_ERR_INVALID, "workspace not 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const StencilDesc& s = stencil->s;
@@ -1356,6 +1375,9 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
     std::memcpy(plan->pinned, plan->host.data(), sizeof(BatchGrid) * n);
     char* ws = static_cast<char*>(workspace);
     plan->dev.grids = reinterpret_cast<const BatchGrid*>(ws + 256);
+    plan->dev.items = reinterpret_cast<BatchItem*>(ws + 256 + round256(sizeof(BatchGrid) * n));
+    if (mode == 1 && items != batch_tb2_items(n, grids))
+      return fail(LOPE_ERR_INVALID, "batch tile count mismatch");
     plan->dev.ngrids = n;
     plan->dev.nitems = items;
     plan->dev.tile_x = tx;
@@ -1374,6 +1396,7 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
     e = cudaStreamBeginCapture(d->capture, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     g_capturing = true;
+    g_captured = 0;
     cudaError_t e1 = cudaMemcpyAsync(ws + 256, plan->pinned, sizeof(BatchGrid) * n,
                                      cudaMemcpyHostToDevice, d->capture);
     cudaError_t e2 = cudaMemsetAsync(ws, 0, 256, d->capture);
@@ -1388,13 +1411,14 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
     e = cudaGraphInstantiate(&plan->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(batch)");
+    plan->kernels = g_captured;
     std::lock_guard<std::mutex> lk(g_batch_mu);
     if (g_batch.size() > 64) g_batch.clear();
     g_batch[key] = plan;
   }
   cudaError_t e = cudaGraphLaunch(plan->exec, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch(batch)");
-  count_launches(1);
+  count_launches(plan->kernels);
   return LOPE_OK;
 }
 

@@ -125,144 +125,209 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(Op op, BatchPlanDe
 // each cell is staged (rows first: the Dirichlet value, stored directly, or
 // the wrapped row; then columns likewise); the first sweep u1 is computed on
 // the tile and its R-wide ring and held at the side's Dirichlet value past a
-// Dirichlet side; the second sweep writes the tile.  The box is free once the
-// first sweep is done, so the next tile's copies are issued before the second
-// sweep and land while it runs.  A pass (two sweeps, or one for the last of an
-// odd count) covers every tile of every grid; passes are separated by the
-// bounded grid-wide barrier, whose acquire orders the next pass's copies
-// after every block's stores.  All threads of a block run the same control
-// flow, so its barriers cannot strand a thread.
+// Dirichlet side; the second sweep writes the tile.
+//
+// Two staging boxes alternate: the copies of the next tile are issued before
+// the first sweep of the current one, so they have a whole tile's sweeps to
+// land.  Tiles are claimed one at a time from a counter, two ahead of the
+// tile being swept, and each claimed tile's 64-byte record (BatchItem) is
+// read while the current tile's second sweep runs.  A pass (two sweeps, or
+// one for the last of an odd count) covers every tile of every grid; passes
+// are separated by the bounded grid-wide barrier, whose acquire orders the
+// next pass's copies after every block's stores.  All threads of a block run
+// the same control flow, so its barriers cannot strand a thread.
+template <int R>
+struct BatchTb2Geom {
+  static constexpr int TX = 64, H = 2 * R, CW = 4, W = TX + 2 * CW;  // box columns -4..TX+3
+  static constexpr int W1 = TX + 4;                                   // u1 columns -2..TX+1
+  static constexpr __host__ __device__ int box_floats(int ty) { return (ty + 2 * H) * W; }
+  static constexpr __host__ __device__ int u1_floats(int ty) { return (ty + 2 * R) * W1; }
+};
+
+// Fill the tile records of the two-sweep batched tiles from the grid list.
+__global__ void batch_items_kernel(const BatchGrid* grids, int ngrids, int nitems, int tx, int ty,
+                                   BatchItem* items) {
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < nitems; it += gridDim.x * blockDim.x) {
+    const BatchGrid& g = grids[find_grid(grids, ngrids, it)];
+    const int t = it - g.first_item;
+    BatchItem b;
+    b.in = static_cast<const float*>(g.in);
+    b.out = static_cast<float*>(g.out);
+    b.work = static_cast<float*>(g.work);
+    b.nx = g.nx;
+    b.ny = g.ny;
+    b.x0 = (t % g.tiles_x) * tx;
+    b.y0 = (t / g.tiles_x) * ty;
+    b.bc = (g.bc[0][0] & 255) | (g.bc[0][1] & 255) << 8 | (g.bc[1][0] & 255) << 16 |
+           (g.bc[1][1] & 255) << 24;
+    b.vy0 = float(g.bval[0][0]);
+    b.vy1 = float(g.bval[0][1]);
+    b.vx0 = float(g.bval[1][0]);
+    b.vx1 = float(g.bval[1][1]);
+    b.pad = 0;
+    items[it] = b;
+  }
+}
+
 template <class Op, int TY, int RY>
 __global__ void __launch_bounds__(32 * (TY / RY), 2) batch_tb2_kernel(Op op, BatchPlanDev p) {
-  constexpr int TX = 64, R = Op::R, H = 2 * R, CW = 4, W = TX + 2 * CW;  // box columns -4..TX+3
+  using G = BatchTb2Geom<Op::R>;
+  constexpr int TX = G::TX, R = Op::R, H = G::H, CW = G::CW, W = G::W, W1 = G::W1;
   static_assert(Op::NF == 1 && Op::STAR && R <= 2, "radius <= 2 star function of one field");
   constexpr int BH = TY + 2 * H, NW = TY / RY, NT = 32 * NW;
-  constexpr int W1 = TX + 8, NC = RY + 2 * R;
+  constexpr int NC = RY + 2 * R, BOXN = G::box_floats(TY);
   constexpr int NRING = 2 * R * 32 + 2 * TY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* box = reinterpret_cast<float*>(smem_raw);
-  float* u1 = box + BH * W;
-  const uint32_t sbox = smem_u32(box);
+  float* const boxes = reinterpret_cast<float*>(smem_raw);  // two staging boxes
+  float* const u1 = boxes + 2 * BOXN;
+  // Tile records: the tile being swept, the next one (staged during this
+  // tile's sweeps) and the one after (fetched during the second sweep).
+  __shared__ __align__(16) BatchItem s_rec[3];
   __shared__ volatile int s_abort;
   __shared__ int s_claim;
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   const int cx2 = lane * 2, cy0 = warp * RY;
   if (tid == 0) s_abort = 0;
   __syncthreads();
+  // Threads 0-3 copy the four 16-byte quarters of a record into slot `sl`
+  // (asynchronously; the copy lands by the next wait).
+  auto fetch_rec = [&](int item, int sl) {
+    if (item >= 0 && tid < 4) {
+      const uint32_t d = smem_u32(&s_rec[sl]) + 16u * unsigned(tid);
+      const char* src = reinterpret_cast<const char*>(p.items + item) + 16 * tid;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
 
   const int64_t passes = (p.nsteps + 1) / 2;
   for (int64_t pass = 0; pass < passes; ++pass) {
     const int kp = (pass == passes - 1 && (p.nsteps & 1)) ? 1 : 2;
     const bool to_out = ((passes - 1 - pass) & 1) == 0;
-    // Tiles are claimed one at a time from a counter (the next one while the
-    // current one is swept), so blocks finish a pass together whatever their
-    // tiles cost.  A block stops at its first claim past the list, so each
-    // pass takes exactly nitems + gridDim.x claims and pass `pass` starts
-    // from pass * (nitems + gridDim.x).
+    // Each block claims until its first claim past the list and then once
+    // more (the claims run two tiles ahead), so each pass takes exactly
+    // nitems + 2 * gridDim.x claims and pass `pass` starts from
+    // pass * (nitems + 2 * gridDim.x).
     const unsigned long long pbase =
-        (unsigned long long)pass * (unsigned long long)(p.nitems + int(gridDim.x));
-    auto claim = [&]() {
-      const unsigned long long v = atomicAdd(p.claim, 1ull) - pbase;
-      return v < (unsigned long long)p.nitems ? int(v) : -1;
-    };
-    // The tile of an item, its grid's extents and sides in registers.
-    const float* src = nullptr;
-    float* dst = nullptr;
-    int nx = 0, ny = 0, x0 = 0, y0 = 0;
-    int bcy0 = 0, bcy1 = 0, bcx0 = 0, bcx1 = 0;
-    float vy0 = 0.f, vy1 = 0.f, vx0 = 0.f, vx1 = 0.f;
-    auto locate = [&](int item) {
-      const BatchGrid& g = p.grids[find_grid(p.grids, p.ngrids, item)];
-      src = static_cast<const float*>(pass == 0 ? g.in : (to_out ? g.work : g.out));
-      dst = static_cast<float*>(to_out ? g.out : g.work);
-      nx = g.nx;
-      ny = g.ny;
-      bcy0 = g.bc[0][0];
-      bcy1 = g.bc[0][1];
-      bcx0 = g.bc[1][0];
-      bcx1 = g.bc[1][1];
-      vy0 = float(g.bval[0][0]);
-      vy1 = float(g.bval[0][1]);
-      vx0 = float(g.bval[1][0]);
-      vx1 = float(g.bval[1][1]);
-      const int t = item - g.first_item;
-      x0 = (t % g.tiles_x) * TX;
-      y0 = (t / g.tiles_x) * TY;
-    };
-    // Stage the box: warp w takes box rows w, w + NW, ...; lane l the box
-    // columns l, l + 32, l + 64.  The row rule is decided once per row, the
-    // column rule once per column; rows (the slower axis) decide first.
-    auto load = [&]() {
-      int gcol[3];
-      float cval[3];
-      bool cfix[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        int gx = x0 - CW + lane + 32 * k;
-        cfix[k] = false;
-        cval[k] = 0.f;
-        if (gx < 0 || gx >= nx) {
-          const bool lo = gx < 0;
-          if ((lo ? bcx0 : bcx1) == kDirichlet) {
-            cfix[k] = true;
-            cval[k] = lo ? vx0 : vx1;
-          }
-          gx = wrap(gx, nx);
-        }
-        gcol[k] = gx;
-      }
+        (unsigned long long)pass * (unsigned long long)(p.nitems + 2 * int(gridDim.x));
+    auto claim_raw = [&]() { return atomicAdd(p.claim, 1ull) - pbase; };
+    auto valid = [&](unsigned long long v) { return v < (unsigned long long)p.nitems ? int(v) : -1; };
+    // Stage the tile of record `t` into `box`: warp w takes box rows w,
+    // w + NW, ...; lane l the box columns l, l + 32, l + 64.  A tile whose box
+    // lies inside its grid copies every cell; elsewhere the row rule is
+    // decided once per row and the column rule once per column, rows (the
+    // slower axis) first.  Ends with a commit, so each tile's copies form
+    // one group.
+    auto load = [&](const BatchItem& t, float* box) {
+      const uint32_t sbox = smem_u32(box);
+      const float* src = pass == 0 ? t.in : (to_out ? t.work : t.out);
+      const int nx = t.nx, ny = t.ny, x0 = t.x0, y0 = t.y0;
+      if (x0 >= CW && x0 + TX + CW <= nx && y0 >= H && y0 + TY + H <= ny) {
+        const float* rp = src + int64_t(y0 - H + warp) * nx + (x0 - CW + lane);
+        const int64_t step = int64_t(NW) * nx;
+        uint32_t d = sbox + 4u * unsigned(warp * W + lane);
 #pragma unroll 4
-      for (int br = warp; br < BH; br += NW) {
-        int gy = y0 - H + br;
-        bool rfix = false;
-        float rval = 0.f;
-        if (gy < 0 || gy >= ny) {
-          const bool lo = gy < 0;
-          if ((lo ? bcy0 : bcy1) == kDirichlet) {
-            rfix = true;
-            rval = lo ? vy0 : vy1;
-          }
-          gy = wrap(gy, ny);
+        for (int br = warp; br < BH; br += NW, rp += step, d += 4u * NW * W) {
+          cp_async_elem<4>(d, rp);
+          cp_async_elem<4>(d + 128u, rp + 32);
+          if (lane < W - 64) cp_async_elem<4>(d + 256u, rp + 64);
         }
-        const float* row = src + int64_t(gy) * nx;
+      } else {
+        const int bcy0 = t.bc & 255, bcy1 = (t.bc >> 8) & 255;
+        const int bcx0 = (t.bc >> 16) & 255, bcx1 = (t.bc >> 24) & 255;
+        int gcol[3];
+        float cval[3];
+        bool cfix[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          if (lane + 32 * k >= W) break;
-          const int at = br * W + lane + 32 * k;
-          if (rfix) box[at] = rval;
-          else if (cfix[k]) box[at] = cval[k];
-          else cp_async_elem<4>(sbox + 4u * unsigned(at), row + gcol[k]);
+          int gx = x0 - CW + lane + 32 * k;
+          cfix[k] = false;
+          cval[k] = 0.f;
+          if (gx < 0 || gx >= nx) {
+            const bool lo = gx < 0;
+            if ((lo ? bcx0 : bcx1) == kDirichlet) {
+              cfix[k] = true;
+              cval[k] = lo ? t.vx0 : t.vx1;
+            }
+            gx = wrap(gx, nx);
+          }
+          gcol[k] = gx;
+        }
+        for (int br = warp; br < BH; br += NW) {
+          int gy = y0 - H + br;
+          bool rfix = false;
+          float rval = 0.f;
+          if (gy < 0 || gy >= ny) {
+            const bool lo = gy < 0;
+            if ((lo ? bcy0 : bcy1) == kDirichlet) {
+              rfix = true;
+              rval = lo ? t.vy0 : t.vy1;
+            }
+            gy = wrap(gy, ny);
+          }
+          const float* row = src + int64_t(gy) * nx;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            if (lane + 32 * k >= W) break;
+            const int at = br * W + lane + 32 * k;
+            if (rfix) box[at] = rval;
+            else if (cfix[k]) box[at] = cval[k];
+            else cp_async_elem<4>(sbox + 4u * unsigned(at), row + gcol[k]);
+          }
         }
       }
+      asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    if (tid == 0) s_claim = claim();
+    // Prologue: the first tile claimed, its record read and its box staged;
+    // the second claimed and its record fetched.
+    if (tid == 0) s_claim = valid(claim_raw());
     __syncthreads();
-    int item = s_claim;
-    if (item >= 0) {
-      locate(item);
-      load();
-    }
+    int cur = s_claim;
+    fetch_rec(cur, 0);
     cp_async_wait_all();
+    __syncthreads();  // the record is visible; every thread has read s_claim
+    if (tid == 0) s_claim = valid(claim_raw());
+    if (cur >= 0) load(s_rec[0], boxes);
     __syncthreads();
-    while (item >= 0) {
-      if (tid == 0) s_claim = claim();  // published by the barrier after the first sweep
+    int nxt = s_claim;
+    fetch_rec(nxt, 1);
+    int a = 0, b = 1, c = 2, buf = 0;
+    while (cur >= 0) {
+      cp_async_wait_all();
+      __syncthreads();  // this tile's box and the next record have landed; u1 is free
+      // the next tile's copies go to the other box, free since the barrier
+      // after the previous tile's first sweep
+      if (nxt >= 0) load(s_rec[b], boxes + (buf ^ 1) * BOXN);
+      unsigned long long v = 0;
+      if (tid == 0) v = claim_raw();  // the tile after next; published after the first sweep
+      const BatchItem& t = s_rec[a];
+      const float* box = boxes + buf * BOXN;
+      const int nx = t.nx, ny = t.ny, x0 = t.x0, y0 = t.y0;
       const bool edge = x0 < CW || x0 + TX + CW > nx || y0 < H || y0 + TY + H > ny;
-      // Cells past a Dirichlet side keep its value: tile rows outside
-      // [row_lo, row_hi) and columns outside [col_lo, col_hi) (rows first,
-      // then columns, the order of the boundary rule).
-      constexpr int kFar = 1 << 30;
-      const int row_lo = bcy0 == kDirichlet ? -y0 : -kFar;
-      const int row_hi = bcy1 == kDirichlet ? ny - y0 : kFar;
-      const int col_lo = bcx0 == kDirichlet ? -x0 : -kFar;
-      const int col_hi = bcx1 == kDirichlet ? nx - x0 : kFar;
-      auto cell = [&](float v, int tc) { return tc < col_lo ? vx0 : tc >= col_hi ? vx1 : v; };
-      auto mask = [&](F2 v, int tr, int tc) {
-        if (tr < row_lo) return F2::make(vy0, vy0);
-        if (tr >= row_hi) return F2::make(vy1, vy1);
-        return F2::make(cell(v.lo(), tc), cell(v.hi(), tc + 1));
-      };
       auto sweep1 = [&](auto edge_tag) {
         constexpr bool EDGE = decltype(edge_tag)::value;
+        // Cells past a Dirichlet side keep its value: tile rows outside
+        // [row_lo, row_hi) and columns outside [col_lo, col_hi) (rows first,
+        // then columns, the order of the boundary rule).
+        constexpr int kFar = 1 << 30;
+        int row_lo = -kFar, row_hi = kFar, col_lo = -kFar, col_hi = kFar;
+        float vy0 = 0.f, vy1 = 0.f, vx0 = 0.f, vx1 = 0.f;
+        if constexpr (EDGE) {
+          if ((t.bc & 255) == kDirichlet) row_lo = -y0;
+          if (((t.bc >> 8) & 255) == kDirichlet) row_hi = ny - y0;
+          if (((t.bc >> 16) & 255) == kDirichlet) col_lo = -x0;
+          if (((t.bc >> 24) & 255) == kDirichlet) col_hi = nx - x0;
+          vy0 = t.vy0;
+          vy1 = t.vy1;
+          vx0 = t.vx0;
+          vx1 = t.vx1;
+        }
+        auto cell = [&](float v, int tc) { return tc < col_lo ? vx0 : tc >= col_hi ? vx1 : v; };
+        auto mask = [&](F2 v, int tr, int tc) {
+          if (tr < row_lo) return F2::make(vy0, vy0);
+          if (tr >= row_hi) return F2::make(vy1, vy1);
+          return F2::make(cell(v.lo(), tc), cell(v.hi(), tc + 1));
+        };
         F2 col[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) col[k] = ld_pair(box + (H - R + cy0 + k) * W + CW + cx2);
@@ -278,16 +343,16 @@ __global__ void __launch_bounds__(32 * (TY / RY), 2) batch_tb2_kernel(Op op, Bat
           op(acc, o, unused);
           F2 v = o[0];
           if constexpr (EDGE) v = mask(v, cy0 + r, cx2);
-          st_pair_f(u1 + (R + cy0 + r) * W1 + 4 + cx2, v);
+          st_pair_f(u1 + (R + cy0 + r) * W1 + 2 + cx2, v);
         }
-        for (int c = tid; c < NRING; c += NT) {
+        for (int q = tid; q < NRING; q += NT) {
           int tr, tc;
-          if (c < 2 * R * 32) {
-            const int row = c >> 5;
+          if (q < 2 * R * 32) {
+            const int row = q >> 5;
             tr = row < R ? row - R : TY + row - R;
-            tc = (c & 31) * 2;
+            tc = (q & 31) * 2;
           } else {
-            const int d = c - 2 * R * 32;
+            const int d = q - 2 * R * 32;
             tr = d >> 1;
             tc = (d & 1) ? TX : -2;
           }
@@ -297,42 +362,39 @@ __global__ void __launch_bounds__(32 * (TY / RY), 2) batch_tb2_kernel(Op op, Bat
           op(acc, o, unused);
           F2 v = o[0];
           if constexpr (EDGE) v = mask(v, tr, tc);
-          st_pair_f(u1 + (R + tr) * W1 + 4 + tc, v);
+          st_pair_f(u1 + (R + tr) * W1 + 2 + tc, v);
         }
       };
       if (edge) sweep1(BoolTag<true>());
       else sweep1(BoolTag<false>());
-      __syncthreads();  // u1 complete; the box is free
-      // the tile's output, kept while the next tile is located and its copies issued
-      float* const out = dst;
-      const int onx = nx, ony = ny, ox = x0 + cx2, oy = y0 + cy0;
-      const int next = s_claim;
-      if (next >= 0) {
-        locate(next);
-        load();
-      }
+      if (tid == 0) s_claim = valid(v);
+      __syncthreads();  // u1 complete; s_claim published; this box is free
+      const int nn = s_claim;
+      fetch_rec(nn, c);  // the record slot of the previous tile, read before the barrier above
+      float* const out = to_out ? t.out : t.work;
+      const int ox = x0 + cx2, oy = y0 + cy0;
       auto put = [&](int r, F2 v) {
         const int gy = oy + r;
-        if (gy >= ony || ox >= onx) return;
-        float* d = out + int64_t(gy) * onx + ox;
-        if (ox + 1 < onx && (reinterpret_cast<uintptr_t>(d) & 7) == 0) {
+        if (gy >= ny || ox >= nx) return;
+        float* d = out + int64_t(gy) * nx + ox;
+        if (ox + 1 < nx && (reinterpret_cast<uintptr_t>(d) & 7) == 0) {
           st_pair(d, v);
         } else {
           d[0] = v.lo();
-          if (ox + 1 < onx) d[1] = v.hi();
+          if (ox + 1 < nx) d[1] = v.hi();
         }
       };
       if (kp == 1) {  // a one-sweep pass: u1 is the result
 #pragma unroll
-        for (int r = 0; r < RY; ++r) put(r, ld_pair(u1 + (R + cy0 + r) * W1 + 4 + cx2));
+        for (int r = 0; r < RY; ++r) put(r, ld_pair(u1 + (R + cy0 + r) * W1 + 2 + cx2));
       } else {
         F2 col[NC];
 #pragma unroll
-        for (int k = 0; k < NC; ++k) col[k] = ld_pair(u1 + (cy0 + k) * W1 + 4 + cx2);
+        for (int k = 0; k < NC; ++k) col[k] = ld_pair(u1 + (cy0 + k) * W1 + 2 + cx2);
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           PairAcc<float, TX, TY, R, 1, NC> acc;
-          acc.b[0] = u1 + (R + cy0 + r) * W1 + 4 + cx2;
+          acc.b[0] = u1 + (R + cy0 + r) * W1 + 2 + cx2;
           acc.col = &col;
           acc.r = r;
           acc.g = 0;
@@ -342,10 +404,15 @@ __global__ void __launch_bounds__(32 * (TY / RY), 2) batch_tb2_kernel(Op op, Bat
           put(r, o[0]);
         }
       }
-      cp_async_wait_all();
-      __syncthreads();  // the next box is staged; u1 may be rewritten
-      item = next;
+      cur = nxt;
+      nxt = nn;
+      const int a0 = a;
+      a = b;
+      b = c;
+      c = a0;
+      buf ^= 1;
     }
+    cp_async_wait_all();
     const bool arrive = !(pass == 0 && int(blockIdx.x) == p.skip_block);
     if (pass + 1 < passes &&
         !grid_sync(p.barrier, unsigned(pass + 1) * gridDim.x, p.err, &s_abort, p.wait_ns, arrive))
@@ -411,13 +478,13 @@ auto with_tile(int tx, int ty, int k, F&& f) {
 }
 
 // Two-sweep register tiles: 8 warps of 16 rows on 64 x 128 tiles, two blocks
-// per SM (one stages while the other computes).
+// per SM, each with two staging boxes.
 constexpr int kTb2RY = 16, kTb2Threads = 32 * (kBatchTb2Y / kTb2RY);
 
 template <class Op>
 size_t tb2_smem() {
-  constexpr int R = Op::R, H = 2 * R, W = kBatchTb2X + 8;
-  return (size_t(kBatchTb2Y + 2 * H) * W + size_t(kBatchTb2Y + 2 * R) * (kBatchTb2X + 8)) * 4;
+  using G = BatchTb2Geom<Op::R>;
+  return size_t(2 * G::box_floats(kBatchTb2Y) + G::u1_floats(kBatchTb2Y)) * 4;
 }
 
 template <class Op>
@@ -449,8 +516,13 @@ struct BatchTb2Runner {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    // the tile records first (one thread per tile), then the persistent kernel
+    batch_items_kernel<<<(p.nitems + 255) / 256, 256, 0, st>>>(p.grids, p.ngrids, p.nitems,
+                                                               kBatchTb2X, kBatchTb2Y, p.items);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     e = cudaLaunchKernelEx(&cfg, kernel(), op, p);
-    count_launches(1);
+    count_launches(2);
     return e;
   }
 };

@@ -153,8 +153,21 @@ struct BatchGrid {
   int tiles_x;
   int first_item;     // index of this grid's first tile in the global item list
 };
+// One tile of the two-sweep batched tiles (mode 1), 64 bytes: everything a
+// block needs to stage and sweep it, read with four 16-byte loads.  Filled
+// on the device from the grid list at the start of each batched launch.
+struct __align__(16) BatchItem {
+  const float* in;
+  float* out;
+  float* work;
+  int nx, ny, x0, y0;
+  int bc;             // side kinds, 8 bits each: y low, y high, x low, x high
+  float vy0, vy1, vx0, vx1;
+  int pad;
+};
 struct BatchPlanDev {
   const BatchGrid* grids;  // device
+  BatchItem* items;        // device, one per tile (mode 1 only)
   int ngrids;
   int nitems;
   int tile_x, tile_y;

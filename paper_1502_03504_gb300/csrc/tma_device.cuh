@@ -50,24 +50,25 @@ template <> struct TmaTx<double> { static constexpr int TX = 32; };
 // 3D, where a radius-2 register queue of 8 rows would spill).  FP32
 // multi-field 2D tiles are 64 rows with 4 rows per thread (17-warp blocks:
 // nonlinear shallow water 0.44 -> 0.53, Gray-Scott 0.75 -> 0.86; the linear
-// shallow water unchanged).  Three-field 3D rings take 6 stages to stay
-// within 227 KB of shared memory.
+// shallow water unchanged).  Three-field 3D rings take 6 stages (5 at radius
+// 2) to stay within 227 KB of shared memory.
 // TALL = false gives the shorter tiles (2D single-field 64 rows, others 32),
 // which keep more blocks in flight on small grids; the runner picks per grid.
 template <class T, int RANK, int R, int NF, bool PAIR, bool TALL = true> struct TmaCfg {
   static constexpr int TX = TmaTx<T>::TX;
   static constexpr bool TALL2 = TALL && RANK == 2 && NF == 1 && PAIR;
   static constexpr bool TALL3 = TALL && RANK == 3 && NF == 1 && PAIR && R == 1;
-  static constexpr bool MULTI32 = TALL && RANK == 2 && NF > 1 && PAIR && sizeof(T) == 4;
-  static constexpr int TY = TALL2 ? 128 : (RANK == 2 && NF == 1) ? 64 : (TALL3 || MULTI32) ? 64 : 32;
+  static constexpr bool MULTI = TALL && RANK == 2 && NF > 1 && PAIR;
+  static constexpr int TY = TALL2 ? 128 : (RANK == 2 && NF == 1) ? 64 : (TALL3 || MULTI) ? 64 : 32;
   static constexpr int RY = PAIR ? (((RANK == 2 && NF == 1) || TALL3) ? 8 : 4) : (RANK == 2 ? 16 : 8);
-  static constexpr int S = RANK == 3 ? (NF == 3 ? 6 : 8) : 3;
+  static constexpr int S = RANK == 3 ? (NF == 3 ? (R == 2 ? 5 : 6) : 8) : 3;
 };
 
 template <int NF> struct TmaMaps {
   CUtensorMap wide[NF];  // box {W, TY+2R}: tile, CW halo columns each side, R halo rows each side
   CUtensorMap rows[NF];  // box {W, R}: R consecutive halo rows
-  CUtensorMap cols[NF];  // box {CW, TY}: one 16-byte column block of the body rows
+  CUtensorMap cols[NF];  // box {CW, TY} (star functions: the body rows) or {CW, TY+2R} (box
+                         // functions: the halo rows too): one 16-byte column block
 };
 
 template <class Op, class T> struct TmaParams {
@@ -90,7 +91,8 @@ template <class Op, class T> struct TmaParams {
 //   wide   (TY+2R) x W box, W = TX + 2 CW, loaded at (x0-CW, y0-R): the tile,
 //          CW halo columns on each side and R halo rows above and below.
 //          Out-of-range cells arrive as zeros (the Dirichlet-0 halo).
-//   colL, colR   TY x CW slots: wrapped halo columns (periodic x edge tiles)
+//   colL, colR   (TY+2R) x CW slots: wrapped halo columns (periodic x edge
+//                tiles; TY rows for star functions, TY+2R for box functions)
 //   rowLo, rowHi R x W slots: wrapped halo rows (periodic y edge tiles)
 // Consumers read every tap at a compile-time offset from the local element in
 // the wide box.  Where the periodic halo wraps (BC=CYCLIC of Sec. 3.2), the
@@ -101,12 +103,13 @@ template <class T, int TX, int TY, int R, int NF> struct Layout {
   static constexpr int CW = 16 / int(sizeof(T));
   static constexpr int W = TX + 2 * CW;
   static constexpr uint32_t WIDE_B = (TY + 2 * R) * W * sizeof(T);
-  static constexpr uint32_t COL_B = TY * CW * sizeof(T);
+  static constexpr uint32_t COL_B = TY * CW * sizeof(T);             // star functions
+  static constexpr uint32_t COLX_B = (TY + 2 * R) * CW * sizeof(T);  // box functions
   static constexpr uint32_t ROW_B = R * W * sizeof(T);
   static constexpr uint32_t A(uint32_t b) { return (b + 127) / 128 * 128; }
   static constexpr uint32_t OFF_COLL = A(WIDE_B);
-  static constexpr uint32_t OFF_COLR = OFF_COLL + A(COL_B);
-  static constexpr uint32_t OFF_ROWLO = OFF_COLR + A(COL_B);
+  static constexpr uint32_t OFF_COLR = OFF_COLL + A(COLX_B);
+  static constexpr uint32_t OFF_ROWLO = OFF_COLR + A(COLX_B);
   static constexpr uint32_t OFF_ROWHI = OFF_ROWLO + A(ROW_B);
   static constexpr uint32_t FIELD_B = OFF_ROWHI + A(ROW_B);
   static constexpr uint32_t STAGE_B = NF * FIELD_B;
@@ -207,27 +210,45 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* m, int x,
   else tma_load_3d(dst, m, x, y, z, bar);
 }
 
-// Issue the copies of one tile/plane of every field into stage `st`.  BOX:
-// the wide box alone (box stencils patch wrapped halos themselves).
+// Box functions on a tile whose halo wraps on one axis only take the wrapped
+// halo from slots (fill_ring_slots); tiles at a corner of the grid, where it
+// wraps on both axes, read the wrapped cells from global memory instead
+// (fill_ring_warp).
+__device__ __forceinline__ bool box_corner(const TileInfo& t) {
+  return (t.xl || t.xr) && (t.yl || t.yh);
+}
+
+// What a stage holds besides the wide box (issue_plane's MODE).
+enum : int {
+  kStageStar = 0,  // star functions: wrapped halo columns (body rows) and rows in slots
+  kStageBox = 1,   // box functions: wrapped halo columns (halo rows too) and rows in slots,
+                   // none on corner tiles of the grid
+  kStageWide = 2   // the wide box alone (the two-sweep kernels)
+};
+
+// Issue the copies of one tile/plane of every field into stage `st`.
 // yoff: rows the 2D tensor maps hold before the grid (an external y halo).
-template <class T, int TX, int TY, int R, int NF, int RANK, bool BOX = false>
+template <class T, int TX, int TY, int R, int NF, int RANK, int MODE = kStageStar>
 __device__ __forceinline__ void issue_plane(const TmaMaps<NF>& maps, unsigned char* st,
                                             uint64_t* bar, const TileInfo& t, int z, int nx,
                                             int ny, int yoff = 0) {
   using L = Layout<T, TX, TY, R, NF>;
+  constexpr bool BOX = MODE == kStageBox;
+  const bool slots = MODE == kStageStar || (BOX && !box_corner(t));
   const uint32_t per_field =
-      BOX ? L::WIDE_B
-          : L::WIDE_B + (uint32_t(t.xl) + uint32_t(t.xr)) * L::COL_B +
-                (uint32_t(t.yl) + uint32_t(t.yh)) * L::ROW_B;
+      L::WIDE_B + (slots ? (uint32_t(t.xl) + uint32_t(t.xr)) * (BOX ? L::COLX_B : L::COL_B) +
+                               (uint32_t(t.yl) + uint32_t(t.yh)) * L::ROW_B
+                         : 0u);
   mbar_arrive_expect_tx(bar, NF * per_field);
   const int xw = t.x0 - L::CW;
+  const int cy = t.y0 + yoff - (BOX ? R : 0);
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     unsigned char* w = st + f * L::FIELD_B;
     tma_load<RANK>(w, &maps.wide[f], xw, t.y0 - R + yoff, z, bar);
-    if (BOX) continue;
-    if (t.xl) tma_load<RANK>(w + L::OFF_COLL, &maps.cols[f], nx - L::CW, t.y0 + yoff, z, bar);
-    if (t.xr) tma_load<RANK>(w + L::OFF_COLR, &maps.cols[f], 0, t.y0 + yoff, z, bar);
+    if (!slots) continue;
+    if (t.xl) tma_load<RANK>(w + L::OFF_COLL, &maps.cols[f], nx - L::CW, cy, z, bar);
+    if (t.xr) tma_load<RANK>(w + L::OFF_COLR, &maps.cols[f], 0, cy, z, bar);
     if (t.yl) tma_load<RANK>(w + L::OFF_ROWLO, &maps.rows[f], xw, ny - R, z, bar);
     if (t.yh) tma_load<RANK>(w + L::OFF_ROWHI, &maps.rows[f], xw, 0, z, bar);
   }
@@ -373,16 +394,26 @@ __device__ __forceinline__ F2 ld_pair(const float* p) {
   r.v = *reinterpret_cast<const uint64_t*>(p);
   return r;
 }
+// A BF16 value is the upper half of the FP32 value it widens to, so a pair
+// widens exactly with one shift (low element) and one mask (high element).
 __device__ __forceinline__ F2 ld_pair(const __nv_bfloat16* p) {
-  const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
-  return F2::make(f.x, f.y);
+  const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
+  return F2::make(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+// One element of an aligned pair: p[0] (lo) or p[1] (hi); a BF16 element
+// widens from the pair's word with one instruction.
+__device__ __forceinline__ float ld_pair_lo(const float* p) { return ld_pair(p).lo(); }
+__device__ __forceinline__ float ld_pair_hi(const float* p) { return ld_pair(p).hi(); }
+__device__ __forceinline__ float ld_pair_lo(const __nv_bfloat16* p) {
+  return __uint_as_float(*reinterpret_cast<const uint32_t*>(p) << 16);
+}
+__device__ __forceinline__ float ld_pair_hi(const __nv_bfloat16* p) {
+  return __uint_as_float(*reinterpret_cast<const uint32_t*>(p) & 0xffff0000u);
 }
 __device__ __forceinline__ void st_pair(float* p, F2 v) { *reinterpret_cast<uint64_t*>(p) = v.v; }
+// Both elements rounded to nearest even and packed by one conversion.
 __device__ __forceinline__ void st_pair(__nv_bfloat16* p, F2 v) {
-  __nv_bfloat162 b;
-  b.x = __float2bfloat16_rn(v.lo());
-  b.y = __float2bfloat16_rn(v.hi());
-  *reinterpret_cast<__nv_bfloat162*>(p) = b;
+  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.lo(), v.hi());
 }
 
 template <class T, int TX, int TY, int R, int NF, int NC>
@@ -398,8 +429,8 @@ struct PairAcc {
     if (dx == -2) return ld_pair(rb - 2);
     if (dx == 2) return ld_pair(rb + 2);
     const F2 c = col[f][r + R + dy];
-    if (dx == -1) return F2::make(ld_pair(rb - 2).hi(), c.lo());
-    return F2::make(c.hi(), ld_pair(rb + 2).lo());
+    if (dx == -1) return F2::make(ld_pair_hi(rb - 2), c.lo());
+    return F2::make(c.hi(), ld_pair_lo(rb + 2));
   }
   __device__ __forceinline__ int64_t gidx() const { return g; }
 };
@@ -418,8 +449,8 @@ struct PairAcc3 {
     if (dx == -2) return ld_pair(b[f] - 2);
     if (dx == 2) return ld_pair(b[f] + 2);
     const F2 c = col[f][r + R];
-    if (dx == -1) return F2::make(ld_pair(b[f] - 2).hi(), c.lo());
-    return F2::make(c.hi(), ld_pair(b[f] + 2).lo());
+    if (dx == -1) return F2::make(ld_pair_hi(b[f] - 2), c.lo());
+    return F2::make(c.hi(), ld_pair_lo(b[f] + 2));
   }
   __device__ __forceinline__ int64_t gidx() const { return g; }
 };
@@ -580,6 +611,64 @@ __device__ __forceinline__ void fill_ring_warp(unsigned char* st, const TileInfo
   __syncwarp();
 }
 
+// Box stencils on a tile whose halo wraps on one axis only: each consumer
+// warp copies the halo-ring cells its own rows read (tile rows cy0-R ..
+// min(cy0+RY, nvy)+R-1) that lie past a periodic side from the slots the
+// producer staged beside the box: the wrapped halo columns of the tile's rows
+// and halo rows (colL / colR), or the wrapped halo rows (rowLo / rowHi).
+// Every cell of a slot already holds what the boundary rule gives there
+// (in-range data, the zero fill past a Dirichlet side, the caller's rows past
+// an external y side), so the copy needs no further test and no global load.
+template <class T, int TX, int TY, int R, int NF, int RY>
+__device__ __forceinline__ void fill_ring_slots(unsigned char* st, const TileInfo& t, int ny,
+                                                int cy0) {
+  using L = Layout<T, TX, TY, R, NF>;
+  const int lane = threadIdx.x % 32;
+  if (cy0 < t.nvy) {
+    const int r0 = cy0 - R, r1 = min(cy0 + RY, t.nvy) + R;  // rows [r0, r1)
+    if (t.xl || t.xr) {
+      // R cells on each side of every row; colL holds global columns
+      // nx-CW .. nx-1, colR columns 0 .. CW-1, both for tile rows -R .. TY+R-1
+      const int n = (r1 - r0) * 2 * R;
+      for (int c = lane; c < n; c += 32) {
+        const int tr = r0 + c / (2 * R), j = c % (2 * R);
+        const bool left = j < R;
+        if (left ? !t.xl : !t.xr) continue;
+        const int tc = left ? j - R : t.nvx + j - R;
+        const int sc = left ? L::CW + tc : tc - t.nvx;
+        const int bo = (R + tr) * L::W + L::CW + tc, so = (R + tr) * L::CW + sc;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          unsigned char* fb = st + f * L::FIELD_B;
+          reinterpret_cast<T*>(fb)[bo] =
+              reinterpret_cast<const T*>(fb + (left ? L::OFF_COLL : L::OFF_COLR))[so];
+        }
+      }
+    } else {
+      // the halo rows among [r0, r1) past a periodic y side, columns -R .. nvx+R-1;
+      // rowLo holds global rows ny-R .. ny-1, rowHi rows 0 .. R-1
+      const int wr = t.nvx + 2 * R;
+      for (int tr = r0; tr < r1; ++tr) {
+        const int gy = t.y0 + tr;
+        if (gy >= 0 && gy < ny) continue;
+        const int off = gy < 0 ? L::OFF_ROWLO : L::OFF_ROWHI;
+        const int sr = gy < 0 ? gy + R : gy - ny;
+        for (int c = lane; c < wr; c += 32) {
+          const int tc = c - R;
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            unsigned char* fb = st + f * L::FIELD_B;
+            reinterpret_cast<T*>(fb)[(R + tr) * L::W + L::CW + tc] =
+                reinterpret_cast<const T*>(fb + off)[sr * L::W + L::CW + tc];
+          }
+        }
+      }
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+}
+
 // ------------------------------------------------------------------ 2D tiles
 template <class Op, class T, int TX, int TY, int RY, int S, bool WRAP, bool PAIR>
 __global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32)
@@ -620,8 +709,9 @@ __global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32)
         if (abort_flag) break;
         const TileInfo t = classify<T, TX, TY, R>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx,
                                               p.ny, WRAP && p.per_x, WRAP && p.per_y);
-        issue_plane<T, TX, TY, R, NF, 2, !Op::STAR>(maps, smem + s * L::STAGE_B, &full[s], t, 0,
-                                                    p.nx, p.ny, p.soff);
+        constexpr int MODE = Op::STAR ? kStageStar : kStageBox;
+        issue_plane<T, TX, TY, R, NF, 2, MODE>(maps, smem + s * L::STAGE_B, &full[s], t, 0, p.nx,
+                                               p.ny, p.soff);
       }
       if (abort_flag) {  // let copies already issued land before the block exits
         for (int k = max(0, i - S); k < i; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
@@ -647,9 +737,13 @@ __global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32)
       // Box stencil: complete the halo ring of wrapped tiles in the box, then
       // every tap (corners included) reads the box.
       static_assert(CPR == 32, "a warp spans the tile width");
-      if (WRAP && (t.xl || t.xr || t.yl || t.yh))
-        fill_ring_warp<T, TX, TY, R, NF, RY>(st, t, p.in, p.nx, p.ny, p.per_x, p.per_y, cy0,
-                                             p.sext);
+      if (WRAP && (t.xl || t.xr || t.yl || t.yh)) {
+        if (box_corner(t))
+          fill_ring_warp<T, TX, TY, R, NF, RY>(st, t, p.in, p.nx, p.ny, p.per_x, p.per_y, cy0,
+                                               p.sext);
+        else
+          fill_ring_slots<T, TX, TY, R, NF, RY>(st, t, p.ny, cy0);
+      }
       if constexpr (PAIR)
         tile2d_pair<false, false, Op, T, TX, TY, RY>(p.op, st, p.out, p.nx, p.ny, t, cx, cy0, red);
       else
@@ -1070,7 +1164,7 @@ __global__ void __launch_bounds__((TX / 2) * (TY / RY) + 32, 1)
         if (abort_flag) break;
         int z = z0 - H + j;
         if (p.per_z) z = wrap(z, p.nz);
-        issue_plane<T, TX, TY, H, 1, 3, true>(maps, smem + s * STAGE, &full[s], t, z, p.nx, p.ny);
+        issue_plane<T, TX, TY, H, 1, 3, kStageWide>(maps, smem + s * STAGE, &full[s], t, z, p.nx, p.ny);
       }
       if (abort_flag) {  // let copies already issued land before the block exits
         for (int k = max(0, j - S); k < j; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
@@ -1289,7 +1383,7 @@ __global__ void __launch_bounds__((TX / 2) * (TY / RY) + 32, 1)
         if (abort_flag) break;
         int z = z0 - H + j;
         if (p.per_z) z = wrap(z, p.nz);
-        issue_plane<T, TX, TY, H, 1, 3, true>(maps, smem + s * STAGE, &full[s], t, z, p.nx, p.ny);
+        issue_plane<T, TX, TY, H, 1, 3, kStageWide>(maps, smem + s * STAGE, &full[s], t, z, p.nx, p.ny);
       }
       if (abort_flag) {
         for (int k = max(0, j - S); k < j; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
@@ -1491,7 +1585,7 @@ __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
         if (abort_flag) break;
         const TileInfo t = classify<T, TX, TY, H>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx,
                                                   p.ny, 0, 0);
-        issue_plane<T, TX, TY, H, 1, 2, true>(maps, smem + s * STAGE, &full[s], t, 0, p.nx, p.ny);
+        issue_plane<T, TX, TY, H, 1, 2, kStageWide>(maps, smem + s * STAGE, &full[s], t, 0, p.nx, p.ny);
       }
       if (abort_flag) {  // let copies already issued land before the block exits
         for (int k = max(0, i - S); k < i; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);

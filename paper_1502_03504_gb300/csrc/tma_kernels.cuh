@@ -159,12 +159,14 @@ struct TmaShape {
     int64_t n[3] = {a.g.n[2], a.g.n[1], a.g.n[0]};
     n[RANK - 1] += lo + hi;
     const int64_t before = int64_t(lo) * (RANK == 3 ? a.g.n[2] * a.g.n[1] : a.g.n[2]);
+    // box functions stage the wrapped halo columns of the halo rows too
+    const uint32_t colh = a.s.star ? TY : TY + 2 * R;
     for (int f = 0; f < NF; ++f) {
       const T* base = static_cast<const T*>(a.in[f]) - before;
       cudaError_t e;
       if ((e = encode<T>(&maps.wide[f], base, RANK, n, L::W, TY + 2 * R)) ||
           (e = encode<T>(&maps.rows[f], base, RANK, n, L::W, R)) ||
-          (e = encode<T>(&maps.cols[f], base, RANK, n, L::CW, TY)))
+          (e = encode<T>(&maps.cols[f], base, RANK, n, L::CW, colh)))
         return e;
     }
     return cudaSuccess;
