@@ -172,6 +172,10 @@ __device__ __forceinline__ void cp_async_elem(uint32_t dst, const void* src) {
     asm volatile("cp.async.ca.shared.global.L2::128B [%0], [%1], 8;" ::"r"(dst), "l"(src)
                  : "memory");
 }
+// One 16-byte asynchronous copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async_16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global.L2::128B [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -264,6 +268,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* m, int
 __device__ __forceinline__ int wrap(int q, int n) {
   q %= n;
   return q < 0 ? q + n : q;
+}
+
+// Index of coordinate v (within one extent of the axis, -n <= v < 2n) on an
+// axis of extent n: itself when inside, wrapped on a periodic side, or -1 / -2
+// past a low / high Dirichlet side.
+__device__ __forceinline__ int axis_index(int v, int n, int bc_lo, int bc_hi) {
+  if (v < 0) return bc_lo == kDirichlet ? -1 : v + n;
+  if (v >= n) return bc_hi == kDirichlet ? -2 : v - n;
+  return v;
 }
 
 // A coefficient kept in both precisions, converted once on the host (round

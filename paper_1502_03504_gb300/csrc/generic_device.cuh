@@ -178,14 +178,6 @@ struct PlaneAcc {
   __device__ __forceinline__ int64_t gidx() const { return p; }
 };
 
-// Index of coordinate v on an axis of extent n: itself when inside, wrapped on
-// a periodic side, or -1 / -2 past a low / high Dirichlet side.
-__device__ __forceinline__ int axis_index(int v, int n, int bc_lo, int bc_hi) {
-  if (v < 0) return bc_lo == kDirichlet ? -1 : v + n;
-  if (v >= n) return bc_hi == kDirichlet ? -2 : v - n;
-  return v;
-}
-
 template <class Op, class T>
 __global__ void __launch_bounds__(256) march3d_plain_kernel(Op op, const __grid_constant__ Geom g,
                                                             const T* in0, const T* in1,

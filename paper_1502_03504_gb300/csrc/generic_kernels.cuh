@@ -11,8 +11,10 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "generic_device.cuh"
+#include "tma_kernels.cuh"
 
 namespace lope {
 
@@ -150,8 +152,17 @@ inline bool march_geometry(const Geom& g, int* blocks, int* zchunk) {
   return march_geometry_t(g, kMarchX, kMarchY, 8, blocks, zchunk);
 }
 
-// FP32 / FP64 grids take the asynchronous-copy march (64 x 16 tiles, four
-// rows per thread), BF16 grids the register-staged one (widened on load).
+// Whether Op is a combining stage of a multi-stage step (it reads its base
+// state at the output element, which the copied-plane march's pairs would
+// read unaligned).
+template <class Op> struct IsStage : std::false_type {};
+template <class Op, class T> struct IsStage<OpStage<Op, T>> : std::true_type {};
+
+// FP32 / FP64 grids: plain sweeps of star functions take the z-march with
+// copied planes (ca3d_kernel: paired consumers, z register queues); box
+// functions and combining stages the asynchronous-copy plane march (64 x 16
+// tiles, four rows per thread).  BF16 grids take the register-staged plane
+// march (widened on load).
 template <class Op, class T>
 cudaError_t run_march(const StepArgs& a, const Op& op) {
   const T* in[3] = {nullptr, nullptr, nullptr};
@@ -161,7 +172,11 @@ cudaError_t run_march(const StepArgs& a, const Op& op) {
     out[f] = static_cast<T*>(a.out[f]);
   }
   int blocks = 0, zchunk = 0;
-  if constexpr (sizeof(T) == sizeof(C_t<T>)) {
+  if constexpr (sizeof(T) == sizeof(C_t<T>) && Op::STAR && !IsStage<Op>::value) {
+    return CaRunner<Op, T>::run(a, op, [&](int tx, int ty, int per_sm, int* b, int* zc) {
+      return march_chunks(a.g, tx, ty, Op::R, per_sm, b, zc);
+    });
+  } else if constexpr (sizeof(T) == sizeof(C_t<T>)) {
     constexpr int smem = march_async_smem<C_t<T>, Op::NF, Op::R>();
     auto kern = &march3d_async_kernel<Op, T>;
     static int per_sm = 0;  // resident blocks per SM, measured once per instance

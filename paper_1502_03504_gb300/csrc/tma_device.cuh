@@ -851,8 +851,11 @@ __device__ __forceinline__ void march3d(const TmaParams<Op, T>& p, unsigned char
 // Paired consumer side of the z-march (FP32/BF16 storage): each thread owns
 // two adjacent columns and RY rows; the z queue and the column registers
 // hold packed pairs.  A warp spans the tile width (TX = 64), so it patches
-// both wrapped halo column blocks of its own rows.
-template <bool YW, bool XF, bool SIMPLE, class Op, class T, int TX, int TY, int RY, int S>
+// both wrapped halo column blocks of its own rows.  ANYX: rows of any pitch
+// (an odd width leaves a last column without its pair, and a pair's address
+// may not be 8-byte aligned): such pairs are stored element by element.
+template <bool YW, bool XF, bool SIMPLE, class Op, class T, int TX, int TY, int RY, int S,
+          bool ANYX = false>
 __device__ __forceinline__ void march3d_pair(const TmaParams<Op, T>& p, unsigned char* smem,
                                              uint64_t* full, uint64_t* empty,
                                              volatile int* abort_flag, const TileInfo& t, int z0,
@@ -940,7 +943,20 @@ __device__ __forceinline__ void march3d_pair(const TmaParams<Op, T>& p, unsigned
       p.op(acc, o, r1);
       if (xvalid && cy0 + r < t.nvy) {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) st_pair(p.out[f] + base + int64_t(r) * p.nx, o[f]);
+        for (int f = 0; f < NF; ++f) {
+          T* d = p.out[f] + base + int64_t(r) * p.nx;
+          if constexpr (ANYX) {
+            static_assert(sizeof(T) == 4, "element stores of FP32 pairs");
+            if (cx2 + 1 < t.nvx && (reinterpret_cast<uintptr_t>(d) & 7) == 0) {
+              st_pair(d, o[f]);
+            } else {
+              d[0] = o[f].lo();
+              if (cx2 + 1 < t.nvx) d[1] = o[f].hi();
+            }
+          } else {
+            st_pair(d, o[f]);
+          }
+        }
         if (Op::REDUCES) rsum = add(rsum, r1);
       }
     }
@@ -1038,6 +1054,190 @@ __global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32, 2)
     LOPE_MARCH(false, false, true);
   }
 #undef LOPE_MARCH
+  if (Op::REDUCES) block_accumulate<NCONS>(red, p.partials, red_scratch);
+}
+
+// ------------------------------------------------------------------ 3D z-march, copied planes
+// The z-march for FP32 / FP64 grids whose rows TMA cannot stage (a row pitch
+// that is not a multiple of 16 bytes): the stage ring, mbarriers and consumer
+// warps of tma3d_kernel (its form without periodic-halo handling), with the
+// wide box of every plane filled by NPW producer warps through 4- or 8-byte
+// asynchronous copies (cp.async), which need no alignment beyond the
+// element's.  Warp w stages box rows w, w + NPW, ...; lane l the box columns
+// l, l + 32, l + 64, in 16- or 8-byte copies where a row's first cell is so
+// aligned.  The boundary rule is applied per cell as it is staged, slowest axis first (z, then y, then x, as the direct kernel
+// reads): a cell inside the grid is copied, a position past a periodic side
+// is copied from the wrapped position, a cell past a Dirichlet side is stored
+// with that side's value; cells no valid output reads (further than R beyond
+// the tile's valid cells, outside the grid) are stored as 0.  The consumers
+// then read a box that holds every halo value.  A stage's full barrier counts
+// two arrivals per producer thread: one when the thread's copies into the
+// stage have landed (cp.async.mbarrier.arrive.noinc) and one, with release
+// semantics, after its direct stores.
+template <class Op, class T, int TX, int TY, int RY, int S, bool PAIR, int NPW>
+__global__ void __launch_bounds__((PAIR ? TX / 2 : TX) * (TY / RY) + 32 * NPW)
+    ca3d_kernel(const __grid_constant__ Geom g, const TmaParams<Op, T> p) {
+  static_assert(Op::STAR && !Op::REDUCES, "plain sweeps of star functions");
+  constexpr int R = Op::R, NF = Op::NF;
+  using L = Layout<T, TX, TY, R, NF>;
+  constexpr int NCONS = (PAIR ? TX / 2 : TX) * (TY / RY), NP = 32 * NPW;
+  constexpr int BH = TY + 2 * R, W = L::W, CW = L::CW, NK = (W + 31) / 32;
+  static_assert(S >= R + 2, "ring too short for the z window");
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element copies of 4 or 8 bytes");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = align128(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * L::STAGE_B);
+  uint64_t* empty = full + S;
+  __shared__ volatile int abort_flag;
+  __shared__ double red_scratch[NCONS / 32];
+
+  const int tid = threadIdx.x;
+  const int ntiles = p.tiles_x * p.tiles_y;
+  const int tile = blockIdx.x % ntiles, zc = blockIdx.x / ntiles;
+  const TileInfo t = classify<T, TX, TY, R>((tile % p.tiles_x) * TX, (tile / p.tiles_x) * TY, p.nx,
+                                            p.ny, 0, 0);
+  const int z0 = zc * p.zchunk, z1 = min(p.nz, z0 + p.zchunk);
+  const int np = (z1 - z0) + 2 * R;  // planes staged by this block
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 2 * NP);
+      mbar_init(&empty[s], NCONS / 32);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (z0 >= z1) return;
+
+  if (tid >= NCONS) {  // producer warps
+    constexpr int NRW = (BH + NPW - 1) / NPW;  // box rows per producer warp
+    const int pw = (tid - NCONS) / 32, lane = tid % 32;
+    const int64_t plane = int64_t(p.nx) * p.ny;
+    // This lane's columns (the same on every row and plane): 0 copy from
+    // gcol, 1 / 2 the low / high x side's Dirichlet value, -1 unused (0).
+    int gcol[NK], ccode[NK];
+    // every box column inside the grid: rows are copied as runs of consecutive cells
+    const bool all_copy = t.x0 - CW >= 0 && t.x0 - CW + W <= p.nx;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+      const int tc = lane + 32 * k - CW, gx = t.x0 + tc;
+      gcol[k] = 0;
+      if (lane + 32 * k >= W) {
+        ccode[k] = -1;
+        continue;
+      }
+      if (gx >= 0 && gx < p.nx) {
+        ccode[k] = 0;
+        gcol[k] = gx;
+      } else if (tc >= -R && tc < t.nvx + R) {
+        const int xx = axis_index(gx, p.nx, g.bc[2][0], g.bc[2][1]);
+        ccode[k] = xx < 0 ? -xx : 0;
+        gcol[k] = xx < 0 ? 0 : xx;
+      } else {
+        ccode[k] = -1;
+      }
+    }
+    // This warp's rows (the same on every plane): the element offset of the
+    // source row in its plane, or -1 / -2 past the low / high y Dirichlet
+    // side, or -3 for a row no output reads.
+    int64_t yrow[NRW];
+#pragma unroll
+    for (int i = 0; i < NRW; ++i) {
+      const int br = pw + NPW * i, tr = br - R, gy = t.y0 + tr;
+      int yy = -3;
+      if (br < BH) {
+        if (gy >= 0 && gy < p.ny) yy = gy;
+        else if (tr >= -R && tr < t.nvy + R) yy = axis_index(gy, p.ny, g.bc[1][0], g.bc[1][1]);
+      }
+      yrow[i] = yy >= 0 ? int64_t(yy) * p.nx : int64_t(yy);
+    }
+    const T vx0 = T(g.bval[2][0]), vx1 = T(g.bval[2][1]);
+    const T vy0 = T(g.bval[1][0]), vy1 = T(g.bval[1][1]);
+    // a row of one value: every cell the outputs read, 0 elsewhere
+    auto fill_row = [&](T* brow, T v) {
+#pragma unroll
+      for (int k = 0; k < NK; ++k)
+        if (lane + 32 * k < W) brow[lane + 32 * k] = ccode[k] < 0 ? T(0) : v;
+    };
+    for (int j = 0; j < np; ++j) {
+      const int s = j % S;
+      if (j >= S && !mbar_wait_bounded(&empty[s], ((j / S) & 1) ^ 1, p.err)) {
+        abort_flag = 1;
+        break;
+      }
+      if (abort_flag) break;
+      const int zz = axis_index(z0 - R + j, p.nz, g.bc[0][0], g.bc[0][1]);
+      unsigned char* st = smem + s * L::STAGE_B;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        T* box = reinterpret_cast<T*>(st + f * L::FIELD_B);
+        const uint32_t sbox = smem_u32(box);
+        if (zz < 0) {  // a plane past a Dirichlet z side: its value (z decides first)
+          const T v = T(g.bval[0][-zz - 1]);
+#pragma unroll
+          for (int i = 0; i < NRW; ++i)
+            if (pw + NPW * i < BH) fill_row(box + (pw + NPW * i) * W, v);
+          continue;
+        }
+        const T* src = p.in[f] + int64_t(zz) * plane;
+#pragma unroll
+        for (int i = 0; i < NRW; ++i) {
+          const int br = pw + NPW * i;
+          if (br >= BH) break;
+          T* brow = box + br * W;
+          const int64_t yo = yrow[i];
+          if (yo < 0) {  // a y Dirichlet side decides before x
+            fill_row(brow, yo == -3 ? T(0) : yo == -1 ? vy0 : vy1);
+            continue;
+          }
+          const T* row = src + yo;
+          const uint32_t d = sbox + uint32_t(br * W + lane) * uint32_t(sizeof(T));
+          if (all_copy) {
+            // the row's cells are consecutive in memory: 16- or 8-byte copies
+            // where the row's first cell is so aligned (the box row is)
+            const T* r0 = row + (t.x0 - CW);
+            const uint32_t drow = sbox + uint32_t(br * W) * uint32_t(sizeof(T));
+            const unsigned mis = unsigned(reinterpret_cast<uintptr_t>(r0)) & 15u;
+            if (mis == 0) {
+              constexpr int E = 16 / int(sizeof(T)), NV = W / E;
+              static_assert(W % E == 0 && NV <= 32, "a box row in 16-byte copies");
+              if (lane < NV) cp_async_16(drow + 16u * lane, r0 + E * lane);
+            } else if (sizeof(T) == 4 && (mis & 7u) == 0) {
+              constexpr int NV = W / 2;
+#pragma unroll
+              for (int k = 0; k * 32 < NV; ++k)
+                if (lane + 32 * k < NV) cp_async_elem<8>(drow + 8u * (lane + 32 * k), r0 + 2 * (lane + 32 * k));
+            } else {
+#pragma unroll
+              for (int k = 0; k < NK; ++k)
+                if (lane + 32 * k < W) cp_async_elem<int(sizeof(T))>(d + 32u * k * sizeof(T), r0 + lane + 32 * k);
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+              if (lane + 32 * k >= W) continue;
+              if (ccode[k] == 0) cp_async_elem<int(sizeof(T))>(d + 32u * k * sizeof(T), row + gcol[k]);
+              else brow[lane + 32 * k] = ccode[k] < 0 ? T(0) : ccode[k] == 1 ? vx0 : vx1;
+            }
+          }
+        }
+      }
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[s]))
+                   : "memory");
+      mbar_arrive(&full[s]);
+    }
+    cp_async_wait_all();  // this thread's copies land before it leaves
+    return;
+  }
+
+  double red = 0.0;
+  if constexpr (PAIR)
+    march3d_pair<false, false, true, Op, T, TX, TY, RY, S, true>(p, smem, full, empty, &abort_flag,
+                                                                 t, z0, z1, np, red);
+  else
+    march3d<false, false, true, Op, T, TX, TY, RY, S>(p, smem, full, empty, &abort_flag, t, z0, z1,
+                                                      np, red);
   if (Op::REDUCES) block_accumulate<NCONS>(red, p.partials, red_scratch);
 }
 

@@ -462,5 +462,94 @@ struct TmaRunner {
   }
 };
 
+// The z-march with planes copied by producer warps (ca3d_kernel), for FP32 /
+// FP64 3D grids whose rows TMA cannot stage: 64 x 64 tiles (32 x 32 for FP64;
+// lope_launch.tile_y 1 forces 64 x 32 / 32 x 32), sixteen producer warps (eight
+// for FP64, whose rows take half the copies), as many planes in flight as 227
+// KB of shared memory hold (at most kCaMaxStages), and z chunks sized in whole
+// waves of the measured occupancy.
+template <class T> constexpr int ca_producer_warps() { return sizeof(T) == 8 ? 8 : 16; }
+constexpr int kCaMaxStages = 12;
+
+template <class Op, class T>
+struct CaRunner {
+  static constexpr bool PAIR = tma_pair<T, Op::R>(Op::REDUCES);
+  static constexpr int NPW = ca_producer_warps<T>();
+  template <bool TALL> using Sh = TmaShape<T, 3, Op::R, Op::NF, PAIR, TALL>;
+  template <bool TALL> using Lay = typename Sh<TALL>::L;
+  template <bool TALL> static constexpr int stages() {
+    constexpr int fit = int((227 * 1024 - 1024) / Lay<TALL>::STAGE_B);
+    return fit < kCaMaxStages ? fit : kCaMaxStages;
+  }
+  template <bool TALL> static constexpr size_t smem() {
+    return size_t(stages<TALL>()) * Lay<TALL>::STAGE_B + 2 * stages<TALL>() * sizeof(uint64_t) + 128;
+  }
+  template <bool TALL> static auto kernel() {
+    using S_ = Sh<TALL>;
+    static_assert(stages<TALL>() >= Op::R + 2 && smem<TALL>() <= 227 * 1024, "stage ring");
+    return &ca3d_kernel<Op, T, S_::TX, S_::TY, S_::RY, stages<TALL>(), PAIR, NPW>;
+  }
+  template <bool TALL> static constexpr int threads() {
+    return Sh<TALL>::THREADS - 32 + 32 * NPW;
+  }
+  template <bool TALL> static int occupancy() {
+    static int occ = -1;
+    if (occ < 0) {
+      cudaFuncSetAttribute(kernel<TALL>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(smem<TALL>()));
+      int o = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel<TALL>(), threads<TALL>(),
+                                                        smem<TALL>()) != cudaSuccess)
+        o = 1;
+      occ = o > 0 ? o : 1;
+    }
+    return occ;
+  }
+  template <bool TALL>
+  static cudaError_t run_t(const StepArgs& a, const Op& op, int zchunk, int blocks) {
+    using S_ = Sh<TALL>;
+    TmaParams<Op, T> p;
+    p.op = op;
+    p.nx = int(a.g.n[2]);
+    p.ny = int(a.g.n[1]);
+    p.nz = int(a.g.n[0]);
+    p.per_x = p.per_y = p.per_z = 0;  // the producers apply every side's rule
+    p.tiles_x = (p.nx + S_::TX - 1) / S_::TX;
+    p.tiles_y = (p.ny + S_::TY - 1) / S_::TY;
+    p.zchunk = zchunk;
+    p.nunits = blocks;
+    p.soff = 0;
+    p.sext = 0;
+    for (int f = 0; f < Op::NF; ++f) {
+      p.in[f] = static_cast<const T*>(a.in[f]);
+      p.out[f] = static_cast<T*>(a.out[f]);
+    }
+    p.partials = a.partials;
+    p.err = a.err;
+    if (Op::REDUCES && (!a.partials || blocks > a.partial_count)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(kernel<TALL>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem<TALL>()));
+    if (e != cudaSuccess) return e;
+    kernel<TALL>()<<<blocks, threads<TALL>(), smem<TALL>(), a.stream>>>(a.g, p);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  // chunks(tx, ty, per_sm, &blocks, &zchunk): the z-chunk split of the caller.
+  // Tall tiles unless lope_launch.tile_y is 1 (measured: diff7 FP32
+  // 130 x 500 x 510, 76 against 123 us per sweep; 511^3, 272 against 454 us).
+  template <class Chunks>
+  static cudaError_t run(const StepArgs& a, const Op& op, Chunks&& chunks) {
+    int blocks = 0, zchunk = 0;
+    if (a.tile_y != 1) {
+      if (!chunks(Sh<true>::TX, Sh<true>::TY, occupancy<true>(), &blocks, &zchunk))
+        return cudaErrorInvalidConfiguration;
+      return run_t<true>(a, op, zchunk, blocks);
+    }
+    if (!chunks(Sh<false>::TX, Sh<false>::TY, occupancy<false>(), &blocks, &zchunk))
+      return cudaErrorInvalidConfiguration;
+    return run_t<false>(a, op, zchunk, blocks);
+  }
+};
+
 }  // namespace
 }  // namespace lope
