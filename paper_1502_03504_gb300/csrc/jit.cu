@@ -253,21 +253,49 @@ void kernel_names(const JitProgram& jp, std::vector<std::string>* names) {
 
 // The TMA kernels come in eight instances: plain or combining stage, with or
 // without the halo-wrap code, tall or short tiles; they follow the fixed list
-// at kNumKernels + tma_index(stage, wrap, tall).
+// at kNumKernels + tma_index(stage, wrap, tall).  The two-sweep kernels
+// follow at tb2_index(wrap): the 3D march with block-shared u1 planes
+// (wrap false), or the 2D tiles without / with the halo-wrap code.
 constexpr int tma_index(bool stage, bool wrap, bool tall) {
   return kNumKernels + (stage ? 4 : 0) + (wrap ? 2 : 0) + (tall ? 1 : 0);
+}
+constexpr int tb2_index(bool wrap) { return kNumKernels + 8 + (wrap ? 1 : 0); }
+
+// Whether the two-sweep kernels are compiled for the program: star functions
+// of one field in FP32 / BF16 storage, radius 1 in 3D, 1 or 2 in 2D.
+template <class T, int RANK, int R, int NF>
+constexpr bool jit_tb2(bool star) {
+  return star && NF == 1 && !std::is_same<T, double>::value && (RANK == 3 ? R == 1 : R <= 2);
 }
 
 template <class T, int RANK, int R, int NF>
 void all_names(const JitProgram& jp, std::vector<std::string>* names) {
   kernel_names<T, RANK, R, NF>(jp, names);
-  names->resize(kNumKernels + 8);
+  names->resize(kNumKernels + 10);
   if (!jp.tma_ok()) return;
   for (int stage = 0; stage < 2; ++stage)
     for (int wrap = 0; wrap < 2; ++wrap) {
       (*names)[tma_index(stage, wrap, true)] = tma_name<T, RANK, R, NF, true>(stage, wrap);
       (*names)[tma_index(stage, wrap, false)] = tma_name<T, RANK, R, NF, false>(stage, wrap);
     }
+  if constexpr (jit_tb2<T, RANK, R, NF>(true)) {
+    if (!jp.star) return;
+    const std::string t = type_name(std::is_same<T, float>::value ? kF32 : kBF16);
+    char buf[256];
+    if constexpr (RANK == 3) {
+      using Sh = Tb2sShape<T>;
+      std::snprintf(buf, sizeof(buf), "&lope::tma3d_tb2s_kernel<lope::UserOp, %s, %d, %d, %d, %d>",
+                    t.c_str(), Sh::TX, Sh::TY, Sh::RY, Sh::S);
+      (*names)[tb2_index(false)] = buf;
+    } else {
+      using Sh = Tb2Shape2D<T, R, 8>;
+      for (int wrap = 0; wrap < 2; ++wrap) {
+        std::snprintf(buf, sizeof(buf), "&lope::tma2d_tb2_kernel<lope::UserOp, %s, %d, %d, %d, %s>",
+                      t.c_str(), Sh::TY, Sh::RY, Sh::S, wrap ? "true" : "false");
+        (*names)[tb2_index(wrap)] = buf;
+      }
+    }
+  }
 }
 
 // Dispatch a functor template over the run-time shape (storage type, rank,
@@ -458,8 +486,48 @@ cudaError_t run_tma_t(JitProgram& jp, const StepArgs& a, int dtype) {
   return go(p);
 }
 
+// Two sweeps per launch (tb2_supported decided the grid; the kernels exist
+// for the program's shape when jit_tb2 holds).
+template <class T, int RANK, int R, int NF>
+cudaError_t run_tb2(JitProgram& jp, const StepArgs& a, int dtype) {
+  if constexpr (jit_tb2<T, RANK, R, NF>(true)) {
+    if (!jp.star) return cudaErrorNotSupported;
+    using Host = UserOpHost<RANK, R, NF, true>;
+    TmaParams<Host, T> p;
+    for (int i = 0; i < kUserParams; ++i) p.op.p[i] = jp.prm[i];
+    p.op.err = a.err;
+    TmaMaps<1> maps;
+    CUfunction f = nullptr;
+    int occ = 1, blocks = 0;
+    if constexpr (RANK == 3) {
+      using Sh = Tb2sShape<T>;
+      cudaError_t e = get_kernel(jp, dtype, tb2_index(false), Sh::SMEM, Sh::THREADS, &f, &occ);
+      if (e != cudaSuccess) return e;
+      zmarch_geometry(a.g, p, &blocks, Sh::TX, Sh::TY, occ * sm_count());
+      if ((e = Sh::prepare(a, p, maps)) != cudaSuccess) return e;
+      void* args[] = {&maps, &p};
+      return launch(f, blocks, Sh::THREADS, Sh::SMEM, a.stream, args);
+    } else {
+      using Sh = Tb2Shape2D<T, R, 8>;
+      const bool wrap = a.g.bc[2][0] == kPeriodic || a.g.bc[1][0] == kPeriodic;
+      cudaError_t e = get_kernel(jp, dtype, tb2_index(wrap), Sh::SMEM, Sh::THREADS, &f, &occ);
+      if (e != cudaSuccess) return e;
+      blocks = tb2_2d_geometry<Sh>(a.g, p, occ);
+      if ((e = Sh::prepare(a, p, maps)) != cudaSuccess) return e;
+      void* args[] = {&maps, &p};
+      return launch(f, blocks, Sh::THREADS, Sh::SMEM, a.stream, args);
+    }
+  } else {
+    (void)jp;
+    (void)a;
+    (void)dtype;
+    return cudaErrorNotSupported;
+  }
+}
+
 template <class T, int RANK, int R, int NF>
 cudaError_t run_tma(JitProgram& jp, const StepArgs& a, int dtype) {
+  if (a.ksteps == 2) return run_tb2<T, RANK, R, NF>(jp, a, dtype);
   return tma_tall(a) ? run_tma_t<T, RANK, R, NF, true>(jp, a, dtype)
                      : run_tma_t<T, RANK, R, NF, false>(jp, a, dtype);
 }

@@ -223,9 +223,51 @@ struct Tb2Shape2D {
   }
 };
 
+// The two-sweep z-march with block-shared u1 planes (tma3d_tb2s_kernel): 64 x
+// 64 tiles, 16 consumer warps of 4 rows, a 6-stage ring of input planes
+// staged with a 2-row halo, three shared u1 planes.
+template <class T>
+struct Tb2sShape {
+  static constexpr int TX = 64, TY = 64, RY = 4, S = 6, H = 2;
+  using L = Layout<T, TX, TY, H, 1>;
+  static constexpr int THREADS = 32 * (TY / RY) + 32;
+  static constexpr size_t SMEM = size_t(S) * L::OFF_COLL + 3 * size_t(TY + 2) * (TX + 8) * 4 +
+                                 2 * S * sizeof(uint64_t) + 128;
+  static_assert(SMEM <= 227 * 1024, "two-sweep ring exceeds the shared memory of a block");
+
+  template <class P>
+  static cudaError_t prepare(const StepArgs& a, P& p, TmaMaps<1>& maps) {
+    p.in[0] = static_cast<const T*>(a.in[0]);
+    p.out[0] = static_cast<T*>(a.out[0]);
+    p.partials = nullptr;
+    p.err = a.err;
+    p.soff = 0;
+    p.sext = 0;
+    const int64_t n[3] = {a.g.n[2], a.g.n[1], a.g.n[0]};
+    return encode<T>(&maps.wide[0], a.in[0], 3, n, L::W, TY + 2 * H);
+  }
+};
+
+// Geometry of the two-sweep 2D tiles (persistent blocks over the tile list).
+template <class Sh2, class P>
+int tb2_2d_geometry(const Geom& g, P& p, int occ) {
+  p.nx = int(g.n[2]);
+  p.ny = int(g.n[1]);
+  p.nz = 1;
+  p.per_x = g.bc[2][0] == kPeriodic;
+  p.per_y = g.bc[1][0] == kPeriodic;
+  p.per_z = 0;
+  p.tiles_x = (p.nx + Sh2::TX - 1) / Sh2::TX;
+  p.tiles_y = (p.ny + Sh2::TY - 1) / Sh2::TY;
+  p.nunits = p.tiles_x * p.tiles_y;
+  p.zchunk = 1;
+  return std::min(p.nunits, occ * sm_count());
+}
+
 // Whether the two-sweep kernels run this launch: a star function of one field
-// (radius 1 in 3D: diffusion builtin or linear table; radius 1 or 2 in 2D:
-// jacobi5, star9r2 or a linear table), FP32 or BF16 storage, no external
+// (radius 1 in 3D: diffusion builtin, linear table or run-time compiled
+// function; radius 1 or 2 in 2D: jacobi5, star9r2, a linear table or a run-time
+// compiled function), FP32 or BF16 storage, no external
 // halo, Dirichlet sides of value 0, no adjoint, no multi-stage combination.
 // The 3D z-march also needs every x and y side Dirichlet (its ring of u1 is
 // masked, not wrapped); the 2D tiles take periodic sides too.
@@ -239,13 +281,14 @@ inline bool tb2_supported(const StepArgs& a) {
       if (g.bc[ax][sd] == kExternal || (g.bc[ax][sd] == kDirichlet && g.bval[ax][sd] != 0.0))
         return false;
   if (g.ndim == 3) {
-    if (s.radius != 1 || (s.kind != kDiff7 && s.kind != kLinear)) return false;
+    if (s.radius != 1 || (s.kind != kDiff7 && s.kind != kLinear && s.kind != kUser)) return false;
     for (int ax = 1; ax < 3; ++ax)
       for (int sd = 0; sd < 2; ++sd)
         if (g.bc[ax][sd] != kDirichlet) return false;
     return true;
   }
-  return s.radius <= 2 && (s.kind == kJacobi5 || s.kind == kStar9r2 || s.kind == kLinear);
+  return s.radius <= 2 &&
+         (s.kind == kJacobi5 || s.kind == kStar9r2 || s.kind == kLinear || s.kind == kUser);
 }
 
 // Paired consumers for FP32/BF16 storage (radius <= 2), adjoint functors
@@ -368,18 +411,7 @@ struct TmaRunner {
       }
       TmaParams<Op, T> p;
       p.op = op;
-      const Geom& g = a.g;
-      p.nx = int(g.n[2]);
-      p.ny = int(g.n[1]);
-      p.nz = 1;
-      p.per_x = g.bc[2][0] == kPeriodic;
-      p.per_y = g.bc[1][0] == kPeriodic;
-      p.per_z = 0;
-      p.tiles_x = (p.nx + Sh2::TX - 1) / Sh2::TX;
-      p.tiles_y = (p.ny + Sh2::TY - 1) / Sh2::TY;
-      p.nunits = p.tiles_x * p.tiles_y;
-      p.zchunk = 1;
-      const int blocks = std::min(p.nunits, occ * sm_count());
+      const int blocks = tb2_2d_geometry<Sh2>(a.g, p, occ);
       if (blocks_out) *blocks_out = blocks;
       TmaMaps<1> maps;
       cudaError_t e = Sh2::prepare(a, p, maps);
@@ -399,13 +431,10 @@ struct TmaRunner {
   // consumer warps of 4 rows.
   static cudaError_t run_tb2s(const StepArgs& a, const Op& op, int* blocks_out) {
     if constexpr (RANK == 3 && Op::R == 1 && Op::NF == 1 && Op::STAR && PAIR && !Op::REDUCES) {
-      constexpr int TX = 64, TY = 64, RY = 4, S = 6, H = 2;
-      using L = Layout<T, TX, TY, H, 1>;
-      constexpr int THREADS = 32 * (TY / RY) + 32;
-      constexpr size_t SMEM = size_t(S) * L::OFF_COLL + 3 * size_t(TY + 2) * (TX + 8) * 4 +
-                              2 * S * sizeof(uint64_t) + 128;
-      static_assert(SMEM <= 227 * 1024, "two-sweep ring exceeds the shared memory of a block");
-      auto kern = &tma3d_tb2s_kernel<Op, T, TX, TY, RY, S>;
+      using Sh = Tb2sShape<T>;
+      constexpr int TX = Sh::TX, TY = Sh::TY, THREADS = Sh::THREADS;
+      constexpr size_t SMEM = Sh::SMEM;
+      auto kern = &tma3d_tb2s_kernel<Op, T, TX, TY, Sh::RY, Sh::S>;
       static int occ = -1;
       if (occ < 0) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM));
@@ -419,14 +448,7 @@ struct TmaRunner {
       zmarch_geometry(a.g, p, &blocks, TX, TY, occ * sm_count());
       if (blocks_out) *blocks_out = blocks;
       TmaMaps<1> maps;
-      p.in[0] = static_cast<const T*>(a.in[0]);
-      p.out[0] = static_cast<T*>(a.out[0]);
-      p.partials = nullptr;
-      p.err = a.err;
-      p.soff = 0;
-      p.sext = 0;
-      const int64_t n[3] = {a.g.n[2], a.g.n[1], a.g.n[0]};
-      cudaError_t e = encode<T>(&maps.wide[0], a.in[0], 3, n, L::W, TY + 2 * H);
+      cudaError_t e = Sh::prepare(a, p, maps);
       if (e != cudaSuccess) return e;
       kern<<<blocks, THREADS, SMEM, a.stream>>>(maps, p);
       count_launches(1);

@@ -80,6 +80,35 @@ def test_user_diff7_bitwise_equals_builtin(lope, dtype):
                            _run(lope, g, builtin, u0, T, launch)[0]), launch
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_user_two_sweeps_per_launch_bitwise_equals_builtin(lope, dtype):
+    """Two sweeps per launch (the planner's choice on large grids) run a
+    user-written star function through the builtins' two-sweep kernels: the
+    3D march with shared u1 planes (x and y sides Dirichlet 0, z periodic or
+    not) and the 2D tiles (periodic and Dirichlet sides); bitwise equal to
+    the builtin on the same launch and to one sweep per launch."""
+    T = 7  # odd: the last launch runs one sweep
+    k2, k1 = _launch(lope, TMA, k=2), _launch(lope, TMA, k=1)
+    shape3 = (37, 50, 72)
+    u3 = to_device(LI.uniform_field(1203, shape3), dtype)[0]
+    user3 = lope.Stencil.source(DIFF7, ndim=3, radius=1, params=[0.1])
+    builtin3 = lope.Stencil.builtin("diff7", 0.1)
+    for bc in ([1, 1, 1], [0, 1, 1]):
+        g = _grid(lope, shape3, dtype, 1, bc)
+        a = _run(lope, g, user3, u3, T, k2)[0]
+        assert torch.equal(a, _run(lope, g, builtin3, u3, T, k2)[0]), bc
+        assert torch.equal(a, _run(lope, g, builtin3, u3, T, k1)[0]), bc
+    shape2 = (83, 264)
+    u2 = to_device(LI.uniform_field(1204, shape2), dtype)[0]
+    user2 = lope.Stencil.source(JACOBI5, ndim=2, radius=1, params=[0.2])
+    builtin2 = lope.Stencil.builtin("jacobi5", 0.2)
+    for bc in ([0, 0], [1, 1], [1, 0]):
+        g = _grid(lope, shape2, dtype, 1, bc)
+        a = _run(lope, g, user2, u2, T, k2)[0]
+        assert torch.equal(a, _run(lope, g, builtin2, u2, T, k2)[0]), bc
+        assert torch.equal(a, _run(lope, g, builtin2, u2, T, k1)[0]), bc
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f64"])
 def test_user_swe_flux_bitwise_equals_builtin(lope, dtype):
     shape, T = (83, 264), 5
