@@ -102,8 +102,12 @@ MARCH, DIRECT = 4, 3
 
 # 45 and 131 points per row: no TMA staging for any storage type.  The second
 # shape spans several column tiles with ragged tails and four z chunks, each
-# refilling its plane ring from its own first planes.
-@pytest.mark.parametrize("shape", [(21, 19, 45), (70, 37, 131)], ids=lambda s: "x".join(map(str, s)))
+# refilling its plane ring from its own first planes.  205 and 206 points per
+# row give the copied-plane z-march tiles whose boxes lie inside the grid, with
+# rows starting at every 4-byte (205) or 8-byte (206) offset: 16-, 8- and
+# 4-byte copies.
+@pytest.mark.parametrize("shape", [(21, 19, 45), (70, 37, 131), (12, 70, 205), (9, 67, 206)],
+                         ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f64"])
 @pytest.mark.parametrize("bc", [[0, 0, 0], [1, 1, 1], [0, 1, 0], [1, 0, 1]])
 def test_3d_march_equals_direct(lope, dtype, bc, shape):
@@ -118,9 +122,10 @@ def test_3d_march_equals_direct(lope, dtype, bc, shape):
         g = lope.Grid(shape, dtype, halo=halo)
         bval = [0.0, 0.0, 0.0] if dtype == "bf16" else [(0.5, -0.3), -0.25, (1.0, 0.2)]
         g.set_boundaries(bc, bval)
-        a = _run(lope, g, st, u, T, lope.Launch(MARCH, 0, 0, 0, -1))[0]
         b = _run(lope, g, st, u, T, lope.Launch(DIRECT, 0, 0, 0, -1))[0]
-        assert torch.equal(a, b), (st.scheme, halo)
+        for ty in (0, 1):  # the march's default tiles, and its short tiles
+            a = _run(lope, g, st, u, T, lope.Launch(MARCH, 0, ty, 0, -1))[0]
+            assert torch.equal(a, b), (st.scheme, halo, ty)
 
 
 def test_3d_odd_width_default_is_march_and_matches_oracle(lope, orc, capfd):
