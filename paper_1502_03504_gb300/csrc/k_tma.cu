@@ -22,6 +22,8 @@ template <class T> cudaError_t dispatch_t(const StepArgs& a, int* blocks) {
     if (s.kind == kDiff7) return TmaRunner<OpDiff7, T, 3>::run_tb2(a, {s.prm[0]}, blocks);
     if (s.kind == kJacobi5) return TmaRunner<OpJacobi5, T, 2>::run_tb2(a, {s.prm[0]}, blocks);
     if (s.kind == kStar9r2) return TmaRunner<OpStar9r2, T, 2>::run_tb2(a, {s.prm[0]}, blocks);
+    if (s.kind == kSwe)
+      return TmaRunner<OpSwe, T, 2>::run_tb2(a, {-s.prm[0] * s.prm[2], -s.prm[0] * s.prm[1]}, blocks);
     if (s.ndim == 3) {
       OpStarLinear<3, 1> op;
       for (int ax = 0; ax < 3; ++ax) for (int d = 0; d < 3; ++d) op.w[ax][d] = s.star_w[ax][d];

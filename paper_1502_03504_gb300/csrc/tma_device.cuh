@@ -1716,22 +1716,22 @@ __global__ void __launch_bounds__((TX / 2) * (TY / RY) + 32, 1)
 
 // ------------------------------------------------------------------ 2D tiles, two sweeps
 // Temporal blocking of depth 2 on the 2D TMA tiles (radius-1 and radius-2 star
-// functions of one field, paired consumers): each 64 x TY tile is staged once
-// with a 2R-row / 16-byte-column halo, the first sweep u1 = E(u0) is computed
-// on the tile plus an R-wide ring (the rows above and below it and the column
-// pairs beside it: every cell the second sweep reads) into a shared-memory
-// buffer, and the second sweep writes the tile.  Periodic sides: on tiles
-// whose staged halo crosses one, the consumers first rewrite the cells past
-// it from the wrapped global coordinates (the TMA box holds zeros there), so
-// the staged window is the periodic extension and u1 on the ring is the
-// periodic value.  Dirichlet sides (value 0): the zero fill is the halo of u0
-// and u1 is set to 0 past them.  u1 is rounded to the storage precision, so
-// the result is bitwise that of two one-sweep launches.
-template <class S_, int WS>
-struct Smem2Acc {  // every tap of a star function from one staged 2D buffer
+// functions of one or more fields, paired consumers): each 64 x TY tile is
+// staged once with a 2R-row / 16-byte-column halo, the first sweep u1 = E(u0)
+// is computed on the tile plus an R-wide ring (the rows above and below it and
+// the column pairs beside it: every cell the second sweep reads) into a
+// shared-memory buffer per field, and the second sweep writes the tile.
+// Periodic sides: on tiles whose staged halo crosses one, the consumers first
+// rewrite the cells past it from the wrapped global coordinates (the TMA box
+// holds zeros there), so the staged window is the periodic extension and u1 on
+// the ring is the periodic value.  Dirichlet sides (value 0): the zero fill is
+// the halo of u0 and u1 is set to 0 past them.  u1 is rounded to the storage
+// precision, so the result is bitwise that of two one-sweep launches.
+template <class S_, int WS, int FS = 0>
+struct Smem2Acc {  // every tap of a star function from staged 2D buffers (field stride FS)
   const S_* c;
-  __device__ __forceinline__ F2 operator()(int, int dx, int dy, int) const {
-    const S_* rb = c + dy * WS;
+  __device__ __forceinline__ F2 operator()(int f, int dx, int dy, int) const {
+    const S_* rb = c + f * FS + dy * WS;
     if (dx == 0) return ld_pair(rb);
     if (dx == -2) return ld_pair(rb - 2);
     if (dx == 2) return ld_pair(rb + 2);
@@ -1741,23 +1741,36 @@ struct Smem2Acc {  // every tap of a star function from one staged 2D buffer
   __device__ __forceinline__ int64_t gidx() const { return 0; }
 };
 
+// Shared-memory sizes of the two-sweep 2D tiles: a stage holds the wide box of
+// every field (one field: the box alone; several: at the field stride of the
+// stage layout, which issue_plane writes), a u1 buffer TY + 2R rows of
+// TX + 8 FP32 columns per field.
+template <class T, int TY, int R, int NF>
+struct Tb2Mem2D {
+  using L = Layout<T, 64, TY, 2 * R, NF>;
+  static constexpr uint32_t STAGE = NF == 1 ? L::OFF_COLL : NF * L::FIELD_B;
+  static constexpr int W1 = 64 + 8;
+  static constexpr uint32_t U1B = (uint32_t(TY + 2 * R) * W1 * 4 + 127) / 128 * 128;
+};
+
 template <class Op, class T, int TY, int RY, int S, bool WRAP>
 __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
-    tma2d_tb2_kernel(const __grid_constant__ TmaMaps<1> maps, const TmaParams<Op, T> p) {
-  constexpr int TX = 64, R = Op::R, H = 2 * R;
-  static_assert(Op::NF == 1 && Op::STAR && R <= 2, "radius <= 2 star function of one field");
-  using L = Layout<T, TX, TY, H, 1>;
+    tma2d_tb2_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
+  constexpr int TX = 64, R = Op::R, H = 2 * R, NF = Op::NF;
+  static_assert(Op::STAR && R <= 2 && NF <= kMaxFields, "radius <= 2 star function");
+  using L = Layout<T, TX, TY, H, NF>;
+  using M = Tb2Mem2D<T, TY, R, NF>;
   constexpr int NW = TY / RY, NCONS = 32 * NW, W = L::W, CW = L::CW, NC = RY + 2 * R;
   static_assert(CW >= H, "the staged columns cover two sweeps of the radius");
-  constexpr int W1 = TX + 8;             // u1 row: columns -4 .. TX+3 (floats)
-  constexpr int U1R = TY + 2 * R;        // u1 rows -R .. TY+R-1
-  constexpr uint32_t STAGE = L::OFF_COLL;  // the wide box alone
-  constexpr uint32_t U1B = (uint32_t(U1R) * W1 * 4 + 127) / 128 * 128;
+  constexpr int W1 = M::W1;              // u1 row: columns -4 .. TX+3 (floats)
+  constexpr uint32_t STAGE = M::STAGE;
+  constexpr uint32_t U1B = M::U1B;
+  constexpr int FB = int(L::FIELD_B / sizeof(T)), FU = int(U1B / 4);  // field strides
   constexpr int NRING = 2 * R * 32 + 2 * TY;  // ring pairs: 2R rows x 32, 2 columns x TY rows
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = align128(smem_raw);
   float* u1s = reinterpret_cast<float*>(smem + S * STAGE);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * STAGE + 2 * U1B);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * STAGE + 2 * NF * U1B);
   uint64_t* empty = full + S;
   __shared__ volatile int abort_flag;
 
@@ -1774,7 +1787,8 @@ __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
 
   if (tid >= NCONS) {  // producer warp
     if (tid == NCONS) {
-      tma_prefetch_desc(&maps.wide[0]);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) tma_prefetch_desc(&maps.wide[f]);
       int i = 0;
       for (int u = blockIdx.x; u < p.nunits; u += gridDim.x, ++i) {
         const int s = i % S;
@@ -1785,7 +1799,8 @@ __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
         if (abort_flag) break;
         const TileInfo t = classify<T, TX, TY, H>((u % p.tiles_x) * TX, (u / p.tiles_x) * TY, p.nx,
                                                   p.ny, 0, 0);
-        issue_plane<T, TX, TY, H, 1, 2, kStageWide>(maps, smem + s * STAGE, &full[s], t, 0, p.nx, p.ny);
+        issue_plane<T, TX, TY, H, NF, 2, kStageWide>(maps, smem + s * STAGE, &full[s], t, 0, p.nx,
+                                                     p.ny);
       }
       if (abort_flag) {  // let copies already issued land before the block exits
         for (int k = max(0, i - S); k < i; ++k) mbar_wait_bounded(&full[k % S], (k / S) & 1, nullptr);
@@ -1807,8 +1822,8 @@ __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
     const int s = i % S;
     const bool got = mbar_wait_bounded(&full[s], (i / S) & 1, p.err) && !abort_flag;
     const int x0 = (u % p.tiles_x) * TX, y0 = (u / p.tiles_x) * TY;
-    T* box = reinterpret_cast<T*>(smem + s * STAGE);
-    float* u1 = u1s + (i & 1) * (U1B / 4);
+    T* box = reinterpret_cast<T*>(smem + s * STAGE);  // field f at box + f * FB
+    float* u1 = u1s + (i & 1) * NF * FU;               // field f at u1 + f * FU
     // cells of this tile's window past a grid side; the others compute unmasked
     const bool edge = x0 < CW || x0 + TX + CW > p.nx || y0 < H || y0 + TY + H > p.ny;
     if (WRAP && edge && (per_x || per_y)) {
@@ -1821,9 +1836,11 @@ __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
       auto fix = [&](int br, int bcol) {
         const int gy = y0 - H + br, gx = x0 - CW + bcol;
         const bool oy = gy < 0 || gy >= p.ny, ox = gx < 0 || gx >= p.nx;
-        if ((!oy || per_y) && (!ox || per_x))
-          box[br * W + bcol] =
-              p.in[0][int64_t(oy ? wrap(gy, p.ny) : gy) * p.nx + (ox ? wrap(gx, p.nx) : gx)];
+        if ((!oy || per_y) && (!ox || per_x)) {
+          const int64_t g = int64_t(oy ? wrap(gy, p.ny) : gy) * p.nx + (ox ? wrap(gx, p.nx) : gx);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) box[f * FB + br * W + bcol] = p.in[f][g];
+        }
       };
       const int xs = cl + (W - cr);  // columns past the x sides, per row
       if (got && per_x && xs > 0)
@@ -1849,23 +1866,26 @@ __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
     };
     auto sweep1 = [&](auto edge_tag) {
       constexpr bool EDGE = decltype(edge_tag)::value;
-      F2 col[NC];
+      F2 col[NF][NC];
 #pragma unroll
-      for (int k = 0; k < NC; ++k) col[k] = ld_pair(box + (H - R + cy0 + k) * W + CW + cx2);
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) col[f][k] = ld_pair(box + f * FB + (H - R + cy0 + k) * W + CW + cx2);
 #pragma unroll
       for (int r = 0; r < RY; ++r) {
-        PairAcc<T, TX, TY, R, 1, NC> acc;
-        acc.b[0] = box + (H + cy0 + r) * W + CW + cx2;
-        acc.col = &col;
+        PairAcc<T, TX, TY, R, NF, NC> acc;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc.b[f] = box + f * FB + (H + cy0 + r) * W + CW + cx2;
+        acc.col = col;
         acc.r = r;
         acc.g = 0;
-        F2 o[1];
+        F2 o[NF];
         F2 unused(0.f);
         p.op(acc, o, unused);
-        F2 v = stored_pair<T>(o[0]);
-        if constexpr (EDGE)
-          if (!keep(cy0 + r, cx2)) v = F2(0.f);
-        st_pair_f(u1 + (R + cy0 + r) * W1 + 4 + cx2, v);
+        const bool kp = !EDGE || keep(cy0 + r, cx2);
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          st_pair_f(u1 + f * FU + (R + cy0 + r) * W1 + 4 + cx2, kp ? stored_pair<T>(o[f]) : F2(0.f));
       }
       for (int c = tid; c < NRING; c += NCONS) {
         int tr, tc;
@@ -1878,14 +1898,14 @@ __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
           tr = d >> 1;
           tc = (d & 1) ? TX : -2;
         }
-        Smem2Acc<T, W> acc{box + (H + tr) * W + CW + tc};
-        F2 o[1];
+        Smem2Acc<T, W, FB> acc{box + (H + tr) * W + CW + tc};
+        F2 o[NF];
         F2 unused(0.f);
         p.op(acc, o, unused);
-        F2 v = stored_pair<T>(o[0]);
-        if constexpr (EDGE)
-          if (!keep(tr, tc)) v = F2(0.f);
-        st_pair_f(u1 + (R + tr) * W1 + 4 + tc, v);
+        const bool kp = !EDGE || keep(tr, tc);
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          st_pair_f(u1 + f * FU + (R + tr) * W1 + 4 + tc, kp ? stored_pair<T>(o[f]) : F2(0.f));
       }
     };
     if (got) {
@@ -1900,22 +1920,28 @@ __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
     }
     // ---- second sweep: the tile from u1
     {
-      F2 col[NC];
+      F2 col[NF][NC];
 #pragma unroll
-      for (int k = 0; k < NC; ++k) col[k] = ld_pair(u1 + (cy0 + k) * W1 + 4 + cx2);
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) col[f][k] = ld_pair(u1 + f * FU + (cy0 + k) * W1 + 4 + cx2);
       const bool xin = x0 + cx2 < p.nx;
-      T* o_row = p.out[0] + int64_t(y0 + cy0) * p.nx + x0 + cx2;
+      const int64_t o_row = int64_t(y0 + cy0) * p.nx + x0 + cx2;
 #pragma unroll
       for (int r = 0; r < RY; ++r) {
-        PairAcc<float, TX, TY, R, 1, NC> acc;
-        acc.b[0] = u1 + (R + cy0 + r) * W1 + 4 + cx2;
-        acc.col = &col;
+        PairAcc<float, TX, TY, R, NF, NC> acc;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc.b[f] = u1 + f * FU + (R + cy0 + r) * W1 + 4 + cx2;
+        acc.col = col;
         acc.r = r;
         acc.g = 0;
-        F2 o[1];
+        F2 o[NF];
         F2 unused(0.f);
         p.op(acc, o, unused);
-        if (!edge || (xin && y0 + cy0 + r < p.ny)) st_pair(o_row + int64_t(r) * p.nx, o[0]);
+        if (!edge || (xin && y0 + cy0 + r < p.ny)) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) st_pair(p.out[f] + o_row + int64_t(r) * p.nx, o[f]);
+        }
       }
     }
   }

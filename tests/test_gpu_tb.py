@@ -131,6 +131,48 @@ def test_two_sweeps_2d_bitwise_equal_one_sweep(lope, orc, dtype, bc, kind, prm, 
         assert np.max(np.abs(to_host(ref) - want)) <= 5 * G ** 5 * eps
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("bc", [[0, 0], [1, 1], [0, 1], [1, 0]])
+@pytest.mark.parametrize("shape", SHAPES_2D, ids=lambda s: "x".join(map(str, s)))
+def test_two_sweeps_2d_three_fields_bitwise_equal_one_sweep(lope, dtype, bc, shape):
+    """The linearised shallow water (h, u, v): three fields staged per tile, u1
+    of each kept on chip; both warp layouts of the 32-row tiles."""
+    h, u, v = LI.swe_fields(1714, shape)
+    fields = [to_device(x, dtype)[0] for x in (h - 1.0 if dtype == "bf16" else h, u, v)]
+    g = lope.Grid(shape, dtype, halo=1, nfields=3)
+    g.set_boundaries(bc)
+    st = lope.Stencil.builtin("swe_cgrid", 0.02, 1.0, 1.0)
+    for T in (2, 5):
+        ref = _run(lope, g, st, fields, T, lope.Launch(TMA, 0, 0, 1, -1))
+        for ty in (0, SHORT):
+            got = _run(lope, g, st, fields, T, lope.Launch(TMA, 0, ty, 2, -1))
+            for k in range(3):
+                assert torch.equal(got[k], ref[k]), (T, ty, k)
+    direct = _run(lope, g, st, fields, 5, lope.Launch(DIRECT, 0, 0, 0, -1))
+    for k in range(3):
+        assert torch.equal(direct[k], ref[k]), k
+
+
+def test_two_sweeps_2d_three_fields_write_only_their_output(lope):
+    shape = (300, 200)
+    n = int(np.prod(shape))
+    guard, sentinel = 4096, -7.0e30
+    h, u, v = LI.swe_fields(1715, shape)
+    fields = [to_device(x, "f32")[0] for x in (h, u, v)]
+    keep = [f.clone() for f in fields]
+    st = lope.Stencil.builtin("swe_cgrid", 0.02, 1.0, 1.0)
+    for bc in ([0, 0], [1, 1]):
+        g = lope.Grid(shape, "f32", halo=1, nfields=3)
+        g.set_boundaries(bc)
+        bufs = [torch.full((n + 2 * guard,), sentinel, device="cuda") for _ in range(6)]
+        views = [b[guard:guard + n].view(shape) for b in bufs]
+        _run(lope, g, st, fields, 5, lope.Launch(TMA, 0, 0, 2, -1), out=views[:3], work=views[3:])
+        for b in bufs:
+            assert bool((b[:guard] == sentinel).all()) and bool((b[guard + n:] == sentinel).all())
+        for f, k in zip(fields, keep):
+            assert torch.equal(f, k)
+
+
 def test_two_sweeps_2d_linear_asymmetric_tables(lope):
     rng = np.random.default_rng(1711)
     shape = (200, 136)
