@@ -262,11 +262,14 @@ constexpr int tma_index(bool stage, bool wrap, bool tall) {
 constexpr int tb2_index(bool wrap) { return kNumKernels + 8 + (wrap ? 1 : 0); }
 
 // Whether the two-sweep kernels are compiled for the program: star functions
-// of one field in FP32 / BF16 storage, radius 1 in 3D, 1 or 2 in 2D.
+// in FP32 / BF16 storage, of one field and radius 1 in 3D, of radius 1 or 2
+// in 2D.  The 2D tiles of several fields take 2 rows per consumer warp, as
+// the builtins' do.
 template <class T, int RANK, int R, int NF>
 constexpr bool jit_tb2(bool star) {
-  return star && NF == 1 && !std::is_same<T, double>::value && (RANK == 3 ? R == 1 : R <= 2);
+  return star && !std::is_same<T, double>::value && (RANK == 3 ? R == 1 && NF == 1 : R <= 2);
 }
+template <int NF> constexpr int jit_tb2_ry() { return NF == 1 ? 8 : 2; }
 
 template <class T, int RANK, int R, int NF>
 void all_names(const JitProgram& jp, std::vector<std::string>* names) {
@@ -288,7 +291,7 @@ void all_names(const JitProgram& jp, std::vector<std::string>* names) {
                     t.c_str(), Sh::TX, Sh::TY, Sh::RY, Sh::S);
       (*names)[tb2_index(false)] = buf;
     } else {
-      using Sh = Tb2Shape2D<T, R, 8>;
+      using Sh = Tb2Shape2D<T, R, jit_tb2_ry<NF>(), NF>;
       for (int wrap = 0; wrap < 2; ++wrap) {
         std::snprintf(buf, sizeof(buf), "&lope::tma2d_tb2_kernel<lope::UserOp, %s, %d, %d, %d, %s>",
                       t.c_str(), Sh::TY, Sh::RY, Sh::S, wrap ? "true" : "false");
@@ -496,10 +499,11 @@ cudaError_t run_tb2(JitProgram& jp, const StepArgs& a, int dtype) {
     TmaParams<Host, T> p;
     for (int i = 0; i < kUserParams; ++i) p.op.p[i] = jp.prm[i];
     p.op.err = a.err;
-    TmaMaps<1> maps;
+    TmaMaps<NF> maps;
     CUfunction f = nullptr;
     int occ = 1, blocks = 0;
     if constexpr (RANK == 3) {
+      static_assert(NF == 1, "the 3D two-sweep march takes one field");
       using Sh = Tb2sShape<T>;
       cudaError_t e = get_kernel(jp, dtype, tb2_index(false), Sh::SMEM, Sh::THREADS, &f, &occ);
       if (e != cudaSuccess) return e;
@@ -508,7 +512,7 @@ cudaError_t run_tb2(JitProgram& jp, const StepArgs& a, int dtype) {
       void* args[] = {&maps, &p};
       return launch(f, blocks, Sh::THREADS, Sh::SMEM, a.stream, args);
     } else {
-      using Sh = Tb2Shape2D<T, R, 8>;
+      using Sh = Tb2Shape2D<T, R, jit_tb2_ry<NF>(), NF>;
       const bool wrap = a.g.bc[2][0] == kPeriodic || a.g.bc[1][0] == kPeriodic;
       cudaError_t e = get_kernel(jp, dtype, tb2_index(wrap), Sh::SMEM, Sh::THREADS, &f, &occ);
       if (e != cudaSuccess) return e;

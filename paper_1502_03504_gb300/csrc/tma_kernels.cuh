@@ -275,14 +275,16 @@ int tb2_2d_geometry(const Geom& g, P& p, int occ) {
 // (radius 1 in 3D: diffusion builtin, linear table or run-time compiled
 // function; radius 1 or 2 in 2D: jacobi5, star9r2, a linear table or a run-time
 // compiled function), or in 2D the three-field linear shallow water
-// (swe_cgrid), FP32 or BF16 storage, no external
+// (swe_cgrid) and run-time compiled functions of several fields, FP32 or BF16
+// storage, no external
 // halo, Dirichlet sides of value 0, no adjoint, no multi-stage combination.
 // The 3D z-march also needs every x and y side Dirichlet (its ring of u1 is
 // masked, not wrapped); the 2D tiles take periodic sides too.
 inline bool tb2_supported(const StepArgs& a) {
   const Geom& g = a.g;
   const StencilDesc& s = a.s;
-  if ((g.nf != 1 && (g.ndim != 2 || s.kind != kSwe)) || !s.star || a.adjoint || a.stage >= 2)
+  if ((g.nf != 1 && (g.ndim != 2 || (s.kind != kSwe && s.kind != kUser))) || !s.star ||
+      a.adjoint || a.stage >= 2)
     return false;
   if (g.dtype != kF32 && g.dtype != kBF16) return false;
   for (int ax = 0; ax < 3; ++ax)

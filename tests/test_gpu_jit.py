@@ -107,6 +107,16 @@ def test_user_two_sweeps_per_launch_bitwise_equals_builtin(lope, dtype):
         a = _run(lope, g, user2, u2, T, k2)[0]
         assert torch.equal(a, _run(lope, g, builtin2, u2, T, k2)[0]), bc
         assert torch.equal(a, _run(lope, g, builtin2, u2, T, k1)[0]), bc
+    # two coupled fields (Gray-Scott, no builtin): both warp layouts of the
+    # multi-field tiles against one sweep per launch
+    gs = [to_device(x, dtype)[0] for x in _gs_fields(1205, shape2)]
+    usr = lope.Stencil.source(GRAY_SCOTT, ndim=2, radius=1, nfields=2, params=GRAY_SCOTT_PRM)
+    for bc in ([0, 0], [1, 0]):
+        g = _grid(lope, shape2, dtype, 1, bc, nf=2)
+        ref = _run(lope, g, usr, gs, T, k1)
+        for ty in (0, 1):
+            got = _run(lope, g, usr, gs, T, _launch(lope, TMA, 0, ty, 2))
+            assert all(torch.equal(x, y) for x, y in zip(got, ref)), (bc, ty)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f64"])
