@@ -257,9 +257,15 @@ Choice default_choice(const Geom& g, const StencilDesc& s, int* err) {
     //   already and the two-sweep march is bound by instruction issue);
     //   2D star9r2 FP32 8192^2 periodic 4.26 -> 3.25 ms, Dirichlet 4.14 ->
     //   3.05; jacobi5 FP32 8192^2 4.13 -> 2.84 / 4.21 -> 2.63; BF16 8192^2
-    //   star9r2 3.71 -> 3.47, jacobi5 about equal; 4096^2 FP32 1.2-1.45x.
+    //   star9r2 3.71 -> 3.47, jacobi5 about equal; 4096^2 FP32 1.2-1.45x;
+    //   linear shallow water 4096^2 x3 x200 FP32 14.97 -> 7.82 ms, BF16
+    //   7.60 -> 7.18; nonlinear shallow water (box halo) FP32 per sweep
+    //   74.8 -> 56.4 us.  BF16 box functions stay at one sweep per launch:
+    //   their two-sweep tiles are bound by instruction issue (nonlinear
+    //   shallow water 47.1 -> 59.2 us per sweep).
     a.ksteps = 2;
-    if (tma_supported(a)) return {kPathTma, 0, 0, 2};
+    if (!(g.ndim == 2 && g.dtype == kBF16 && !s.star) && tma_supported(a))
+      return {kPathTma, 0, 0, 2};
     a.ksteps = 1;
   }
   if (tma_supported(a)) return {kPathTma, 0, 0, 1};

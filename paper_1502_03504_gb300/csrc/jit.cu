@@ -261,15 +261,17 @@ constexpr int tma_index(bool stage, bool wrap, bool tall) {
 }
 constexpr int tb2_index(bool wrap) { return kNumKernels + 8 + (wrap ? 1 : 0); }
 
-// Whether the two-sweep kernels are compiled for the program: star functions
-// in FP32 / BF16 storage, of one field and radius 1 in 3D, of radius 1 or 2
-// in 2D.  The 2D tiles of several fields take 2 rows per consumer warp, as
+// Whether the two-sweep kernels are compiled for the program: FP32 / BF16
+// storage, star functions of one field and radius 1 in 3D, functions of
+// radius 1 or 2 in 2D (box functions included).  The 2D tiles of several fields take 2 rows per consumer warp, as
 // the builtins' do.
 template <class T, int RANK, int R, int NF>
 constexpr bool jit_tb2(bool star) {
-  return star && !std::is_same<T, double>::value && (RANK == 3 ? R == 1 && NF == 1 : R <= 2);
+  return !std::is_same<T, double>::value && (RANK == 3 ? star && R == 1 && NF == 1 : R <= 2);
 }
 template <int NF> constexpr int jit_tb2_ry() { return NF == 1 ? 8 : 2; }
+// (The builtins' box functions of several fields take 4 rows per warp; the
+// run-time compiled ones keep one layout, 2 rows, for every function.)
 
 template <class T, int RANK, int R, int NF>
 void all_names(const JitProgram& jp, std::vector<std::string>* names) {
@@ -282,7 +284,7 @@ void all_names(const JitProgram& jp, std::vector<std::string>* names) {
       (*names)[tma_index(stage, wrap, false)] = tma_name<T, RANK, R, NF, false>(stage, wrap);
     }
   if constexpr (jit_tb2<T, RANK, R, NF>(true)) {
-    if (!jp.star) return;
+    if (!jit_tb2<T, RANK, R, NF>(jp.star)) return;
     const std::string t = type_name(std::is_same<T, float>::value ? kF32 : kBF16);
     char buf[256];
     if constexpr (RANK == 3) {
@@ -494,7 +496,7 @@ cudaError_t run_tma_t(JitProgram& jp, const StepArgs& a, int dtype) {
 template <class T, int RANK, int R, int NF>
 cudaError_t run_tb2(JitProgram& jp, const StepArgs& a, int dtype) {
   if constexpr (jit_tb2<T, RANK, R, NF>(true)) {
-    if (!jp.star) return cudaErrorNotSupported;
+    if (!jit_tb2<T, RANK, R, NF>(jp.star)) return cudaErrorNotSupported;
     using Host = UserOpHost<RANK, R, NF, true>;
     TmaParams<Host, T> p;
     for (int i = 0; i < kUserParams; ++i) p.op.p[i] = jp.prm[i];

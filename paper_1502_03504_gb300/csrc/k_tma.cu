@@ -24,6 +24,17 @@ template <class T> cudaError_t dispatch_t(const StepArgs& a, int* blocks) {
     if (s.kind == kStar9r2) return TmaRunner<OpStar9r2, T, 2>::run_tb2(a, {s.prm[0]}, blocks);
     if (s.kind == kSwe)
       return TmaRunner<OpSwe, T, 2>::run_tb2(a, {-s.prm[0] * s.prm[2], -s.prm[0] * s.prm[1]}, blocks);
+    if (s.kind == kSweFlux) return TmaRunner<OpSweFlux, T, 2>::run_tb2(a, OpSweFlux::make(s.prm), blocks);
+    if (!s.star) {  // box tables (2D)
+      if (s.radius == 1) {
+        OpBoxLinear<2, 1> op;
+        for (int i = 0; i < 9; ++i) op.w[i] = s.box[i];
+        return TmaRunner<OpBoxLinear<2, 1>, T, 2>::run_tb2(a, op, blocks);
+      }
+      OpBoxLinear<2, 2> op;
+      for (int i = 0; i < 25; ++i) op.w[i] = s.box[i];
+      return TmaRunner<OpBoxLinear<2, 2>, T, 2>::run_tb2(a, op, blocks);
+    }
     if (s.ndim == 3) {
       OpStarLinear<3, 1> op;
       for (int ax = 0; ax < 3; ++ax) for (int d = 0; d < 3; ++d) op.w[ax][d] = s.star_w[ax][d];

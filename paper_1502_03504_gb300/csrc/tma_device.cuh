@@ -1715,12 +1715,13 @@ __global__ void __launch_bounds__((TX / 2) * (TY / RY) + 32, 1)
 }
 
 // ------------------------------------------------------------------ 2D tiles, two sweeps
-// Temporal blocking of depth 2 on the 2D TMA tiles (radius-1 and radius-2 star
-// functions of one or more fields, paired consumers): each 64 x TY tile is
-// staged once with a 2R-row / 16-byte-column halo, the first sweep u1 = E(u0)
-// is computed on the tile plus an R-wide ring (the rows above and below it and
-// the column pairs beside it: every cell the second sweep reads) into a
-// shared-memory buffer per field, and the second sweep writes the tile.
+// Temporal blocking of depth 2 on the 2D TMA tiles (radius-1 and radius-2
+// functions of one or more fields, star or box, paired consumers): each 64 x
+// TY tile is staged once with a 2R-row / 16-byte-column halo, the first sweep
+// u1 = E(u0) is computed on the tile plus an R-wide ring (the rows above and
+// below it and the column pairs beside it, corners included for box
+// functions: every cell the second sweep reads) into a shared-memory buffer
+// per field, and the second sweep writes the tile.
 // Periodic sides: on tiles whose staged halo crosses one, the consumers first
 // rewrite the cells past it from the wrapped global coordinates (the TMA box
 // holds zeros there), so the staged window is the periodic extension and u1 on
@@ -1757,7 +1758,7 @@ template <class Op, class T, int TY, int RY, int S, bool WRAP>
 __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
     tma2d_tb2_kernel(const __grid_constant__ TmaMaps<Op::NF> maps, const TmaParams<Op, T> p) {
   constexpr int TX = 64, R = Op::R, H = 2 * R, NF = Op::NF;
-  static_assert(Op::STAR && R <= 2 && NF <= kMaxFields, "radius <= 2 star function");
+  static_assert(R <= 2 && NF <= kMaxFields, "radius <= 2");
   using L = Layout<T, TX, TY, H, NF>;
   using M = Tb2Mem2D<T, TY, R, NF>;
   constexpr int NW = TY / RY, NCONS = 32 * NW, W = L::W, CW = L::CW, NC = RY + 2 * R;
@@ -1766,7 +1767,9 @@ __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
   constexpr uint32_t STAGE = M::STAGE;
   constexpr uint32_t U1B = M::U1B;
   constexpr int FB = int(L::FIELD_B / sizeof(T)), FU = int(U1B / 4);  // field strides
-  constexpr int NRING = 2 * R * 32 + 2 * TY;  // ring pairs: 2R rows x 32, 2 columns x TY rows
+  // ring pairs: 2R rows x 32, 2 columns x TY rows, and for box functions the
+  // 2R x 2 corner pairs
+  constexpr int NRING = 2 * R * 32 + 2 * TY + (Op::STAR ? 0 : 4 * R);
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = align128(smem_raw);
   float* u1s = reinterpret_cast<float*>(smem + S * STAGE);
@@ -1893,9 +1896,13 @@ __global__ void __launch_bounds__((TY / RY) * 32 + 32, 1)
           const int row = c >> 5;
           tr = row < R ? row - R : TY + row - R;
           tc = (c & 31) * 2;
-        } else {  // the column pairs left and right of the tile
+        } else if (c < 2 * R * 32 + 2 * TY) {  // the column pairs left and right of the tile
           const int d = c - 2 * R * 32;
           tr = d >> 1;
+          tc = (d & 1) ? TX : -2;
+        } else {  // box functions: those column pairs on the R rows above and below
+          const int d = c - 2 * R * 32 - 2 * TY, row = d >> 1;
+          tr = row < R ? row - R : TY + row - R;
           tc = (d & 1) ? TX : -2;
         }
         Smem2Acc<T, W, FB> acc{box + (H + tr) * W + CW + tc};

@@ -271,20 +271,19 @@ int tb2_2d_geometry(const Geom& g, P& p, int occ) {
   return std::min(p.nunits, occ * sm_count());
 }
 
-// Whether the two-sweep kernels run this launch: a star function of one field
-// (radius 1 in 3D: diffusion builtin, linear table or run-time compiled
-// function; radius 1 or 2 in 2D: jacobi5, star9r2, a linear table or a run-time
-// compiled function), or in 2D the three-field linear shallow water
-// (swe_cgrid) and run-time compiled functions of several fields, FP32 or BF16
-// storage, no external
+// Whether the two-sweep kernels run this launch: in 3D a radius-1 star
+// function of one field (diffusion builtin, linear table or run-time compiled
+// function); in 2D a radius-1 or 2 function, star or box, of one to three
+// fields (jacobi5, star9r2, the shallow-water builtins, linear tables,
+// run-time compiled functions); FP32 or BF16 storage, no external
 // halo, Dirichlet sides of value 0, no adjoint, no multi-stage combination.
 // The 3D z-march also needs every x and y side Dirichlet (its ring of u1 is
 // masked, not wrapped); the 2D tiles take periodic sides too.
 inline bool tb2_supported(const StepArgs& a) {
   const Geom& g = a.g;
   const StencilDesc& s = a.s;
-  if ((g.nf != 1 && (g.ndim != 2 || (s.kind != kSwe && s.kind != kUser))) || !s.star ||
-      a.adjoint || a.stage >= 2)
+  if ((g.nf != 1 && (g.ndim != 2 || (s.kind != kSwe && s.kind != kSweFlux && s.kind != kUser))) ||
+      (!s.star && g.ndim != 2) || a.adjoint || a.stage >= 2)
     return false;
   if (g.dtype != kF32 && g.dtype != kBF16) return false;
   for (int ax = 0; ax < 3; ++ax)
@@ -299,7 +298,7 @@ inline bool tb2_supported(const StepArgs& a) {
     return true;
   }
   return s.radius <= 2 && (s.kind == kJacobi5 || s.kind == kStar9r2 || s.kind == kLinear ||
-                            s.kind == kUser || s.kind == kSwe);
+                            s.kind == kUser || s.kind == kSwe || s.kind == kSweFlux);
 }
 
 // Paired consumers for FP32/BF16 storage (radius <= 2), adjoint functors
@@ -408,7 +407,7 @@ struct TmaRunner {
 
   template <bool WRAP, int RY>
   static cudaError_t run_tb2_2d_t(const StepArgs& a, const Op& op, int* blocks_out) {
-    if constexpr (RANK == 2 && Op::R <= 2 && Op::STAR && PAIR && !Op::REDUCES) {
+    if constexpr (RANK == 2 && Op::R <= 2 && PAIR && !Op::REDUCES) {
       using Sh2 = Tb2Shape2D<T, Op::R, RY, Op::NF>;
       auto kern = &tma2d_tb2_kernel<Op, T, Sh2::TY, Sh2::RY, Sh2::S, WRAP>;
       static int occ = -1;
@@ -482,11 +481,14 @@ struct TmaRunner {
     }
     if constexpr (RANK == 2) {
       // One field: lope_launch.tile_y 1 takes 16 rows per consumer warp (8
-      // warps), else 8 rows (16 warps).  Several fields (32-row tiles):
-      // tile_y 1 takes 4 rows per warp (8 warps), else 2 (16 warps; shallow
-      // water 4096^2 x200 BF16 periodic: 7.18 against 7.57 ms, FP32 equal).
+      // warps), else 8 rows (16 warps).  Several fields (32-row tiles): star
+      // functions 2 rows (16 warps; linear shallow water 4096^2 x200 BF16
+      // periodic 7.18 against 7.57 ms with 4 rows, FP32 equal), box
+      // functions 4 rows (8 warps; nonlinear shallow water FP32 56.4
+      // against 58.4 us per sweep); tile_y 1 takes the other layout.
       const bool wrap = a.g.bc[2][0] == kPeriodic || a.g.bc[1][0] == kPeriodic;
-      constexpr int RY_A = Op::NF == 1 ? 16 : 4, RY_B = Op::NF == 1 ? 8 : 2;
+      constexpr int RY_M = Op::STAR ? 2 : 4, RY_N = Op::STAR ? 4 : 2;
+      constexpr int RY_A = Op::NF == 1 ? 16 : RY_N, RY_B = Op::NF == 1 ? 8 : RY_M;
       if (a.tile_y == 1)
         return wrap ? run_tb2_2d_t<true, RY_A>(a, op, blocks_out)
                     : run_tb2_2d_t<false, RY_A>(a, op, blocks_out);

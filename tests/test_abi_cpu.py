@@ -211,6 +211,12 @@ PLAN_CASES = [  # shape, dtype, builtin, params, halo, scheme, bc, expected plan
     ((130, 500, 510), "f32", "diff7", [0.1], 1, "euler", [1, 0, 1], "path=march"),
     ((8192, 8192), "f32", "jacobi5", [0.2], 1, "rk3", [0, 0], "path=trapezoid tile=128x16 k=1"),
     ((4096, 4096), "f32", "swe_flux", [0.02, 1.0, 0.5, 1.0], 1, "rk3", [0, 0], "path=tma"),
+    ((4096, 4096), "f32", "swe_cgrid", [0.02, 1.0, 1.0], 1, "euler", [0, 0], "path=tma tile=0x0 k=2"),
+    ((4096, 4096), "bf16", "swe_cgrid", [0.02, 1.0, 1.0], 1, "euler", [0, 0], "path=tma tile=0x0 k=2"),
+    ((4096, 4096), "f32", "swe_flux", [0.02, 1.0, 0.5, 1.0], 1, "euler", [0, 0],
+     "path=tma tile=0x0 k=2"),
+    ((4096, 4096), "bf16", "swe_flux", [0.02, 1.0, 0.5, 1.0], 1, "euler", [0, 0],
+     "path=tma tile=0x0 k=1"),
 ]
 
 

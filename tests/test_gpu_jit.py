@@ -127,7 +127,10 @@ def test_user_swe_flux_bitwise_equals_builtin(lope, dtype):
     g = _grid(lope, shape, dtype, 1, [0, 0], nf=3)
     user = lope.Stencil.source(SWE_FLUX, ndim=2, radius=1, nfields=3, params=FLUX, box=True)
     builtin = lope.Stencil.builtin("swe_flux", *FLUX)
-    for launch in (_launch(lope, TMA), _launch(lope, TRAP, 64, 32, 1), _launch(lope, DIRECT)):
+    launches = [_launch(lope, TMA), _launch(lope, TRAP, 64, 32, 1), _launch(lope, DIRECT)]
+    if dtype != "f64":
+        launches.append(_launch(lope, TMA, k=2))  # two sweeps per launch, box halo
+    for launch in launches:
         a = _run(lope, g, user, dev, T, launch)
         b = _run(lope, g, builtin, dev, T, launch)
         for k in range(3):

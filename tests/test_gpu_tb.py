@@ -134,14 +134,18 @@ def test_two_sweeps_2d_bitwise_equal_one_sweep(lope, orc, dtype, bc, kind, prm, 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("bc", [[0, 0], [1, 1], [0, 1], [1, 0]])
 @pytest.mark.parametrize("shape", SHAPES_2D, ids=lambda s: "x".join(map(str, s)))
-def test_two_sweeps_2d_three_fields_bitwise_equal_one_sweep(lope, dtype, bc, shape):
-    """The linearised shallow water (h, u, v): three fields staged per tile, u1
-    of each kept on chip; both warp layouts of the 32-row tiles."""
+@pytest.mark.parametrize("kind,prm", [("swe_cgrid", [0.02, 1.0, 1.0]), ("swe_flux", [0.02, 1.0, 0.5, 1.0])])
+def test_two_sweeps_2d_three_fields_bitwise_equal_one_sweep(lope, dtype, bc, shape, kind, prm):
+    """Shallow water on three fields: the linearised star form and the
+    nonlinear flux form (box halo: corner taps, u1 on the ring's corners);
+    three fields staged per tile, u1 of each kept on chip; both warp layouts
+    of the 32-row tiles."""
     h, u, v = LI.swe_fields(1714, shape)
-    fields = [to_device(x, dtype)[0] for x in (h - 1.0 if dtype == "bf16" else h, u, v)]
+    eta = kind == "swe_flux" or dtype == "bf16"
+    fields = [to_device(x, dtype)[0] for x in (h - 1.0 if eta else h, u, v)]
     g = lope.Grid(shape, dtype, halo=1, nfields=3)
     g.set_boundaries(bc)
-    st = lope.Stencil.builtin("swe_cgrid", 0.02, 1.0, 1.0)
+    st = lope.Stencil.builtin(kind, *prm)
     for T in (2, 5):
         ref = _run(lope, g, st, fields, T, lope.Launch(TMA, 0, 0, 1, -1))
         for ty in (0, SHORT):
@@ -171,6 +175,23 @@ def test_two_sweeps_2d_three_fields_write_only_their_output(lope):
             assert bool((b[:guard] == sentinel).all()) and bool((b[guard + n:] == sentinel).all())
         for f, k in zip(fields, keep):
             assert torch.equal(f, k)
+
+
+def test_two_sweeps_2d_box_tables(lope):
+    """Box weight tables of radius 1 and 2 (every corner tap weighted): the
+    first sweep fills the corners of its ring."""
+    rng = np.random.default_rng(1716)
+    shape = (200, 136)
+    u0, _ = to_device(LI.uniform_field(1717, shape), "f32")
+    for r in (1, 2):
+        w = rng.uniform(0.0, 0.08, (2 * r + 1, 2 * r + 1))
+        w[r, r] = 1.0 - (w.sum() - w[r, r])
+        st = lope.Stencil.linear(w)
+        for bc in ([0, 0], [1, 0], [0, 1]):
+            g = lope.Grid(shape, "f32", halo=r)
+            g.set_boundaries(bc)
+            ref = _run(lope, g, st, u0, 6, lope.Launch(DIRECT, 0, 0, 0, -1))
+            assert torch.equal(_run(lope, g, st, u0, 6, lope.Launch(TMA, 0, 0, 2, -1)), ref), (r, bc)
 
 
 def test_two_sweeps_2d_linear_asymmetric_tables(lope):
