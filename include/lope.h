@@ -270,7 +270,7 @@ lope_status lope_tune_cache_load(const char* path, const char* gpu_name, int* lo
  * cfg may be NULL: the choice of the batch autotuner for this batch (see
  * lope_autotune_batch), else, for FP32 star functions of radius 1-2 (jacobi5,
  * star9r2, linear star tables), the two-sweep register tiles (cfg->path 1:
- * 64 x 128 tiles staged by plain loads, any row pitch, two sweeps per pass),
+ * 64 x 64 tiles staged by plain loads, any row pitch, two sweeps per pass),
  * and the trapezoid tiles otherwise (cfg->path 2: 64 x 32 tiles, depth 4;
  * tile_x, tile_y and tsteps choose another shape and depth).  Errors as
  * lope_apply; LOPE_ERR_TIMEOUT is reported by lope_sync_status if a bounded

@@ -753,7 +753,7 @@ std::mutex g_batch_mu;
 std::map<std::vector<int64_t>, std::shared_ptr<BatchPlan>> g_batch;
 
 // Batch workspace: the barrier and claim counters (256 B), the grid list, and
-// one record per tile of the two-sweep batched tiles (64 x 128 tiles).
+// one record per tile of the two-sweep batched tiles (64 x 64 tiles).
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 int64_t batch_tb2_items(int n, const lope_grid* const* grids) {
   int64_t items = 0;
@@ -1299,7 +1299,7 @@ lope_status lope_apply_batch(int n, const lope_grid* const* grids, const lope_st
     void* work1[1] = {work ? work[i] : nullptr};
     if ((rs = check_fields(grids[i]->g, in1, out1, work1, true)) != LOPE_OK) return rs;
   }
-  // The two-sweep register tiles (path 1: 64 x 128 tiles, two sweeps per
+  // The two-sweep register tiles (path 1: 64 x 64 tiles, two sweeps per
   // pass) serve FP32 star functions of radius 1-2 (jacobi5, star9r2, linear
   // star tables) and are the default there; other batches take the trapezoid
   // tiles (path 2, 64 x 32, four sweeps per pass).  A choice remembered by the

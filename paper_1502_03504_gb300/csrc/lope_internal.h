@@ -179,14 +179,14 @@ struct BatchPlanDev {
   unsigned long long wait_ns;  // limit of each barrier wait
   int skip_block;              // test hook: this block skips its first arrival (-1: none)
   int mode;                    // 0: trapezoid tiles (k sweeps per pass); 1: two-sweep
-                               // register tiles (64 x 128, two sweeps per pass)
+                               // register tiles (64 x 64, two sweeps per pass)
 };
 cudaError_t launch_batch(const BatchPlanDev& p, const StencilDesc& s, int dtype, int blocks,
                          cudaStream_t st);
 int batch_max_blocks(const StencilDesc& s, int dtype, int tile_x, int tile_y, int ksteps,
                      int mode = 0);
 // Tile of the two-sweep batched tiles (mode 1).
-constexpr int kBatchTb2X = 64, kBatchTb2Y = 128;
+constexpr int kBatchTb2X = 64, kBatchTb2Y = 64;
 size_t trap_smem_bytes(int dtype, int nf, int tile_x, int tile_y, int halo, int stages = 1);
 
 void count_launches(int64_t n);
