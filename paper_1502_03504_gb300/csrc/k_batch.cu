@@ -223,14 +223,25 @@ __global__ void __launch_bounds__(32 * (TY / RY), 3) batch_tb2_kernel(Op op, Bat
       const float* src = pass == 0 ? t.in : (to_out ? t.work : t.out);
       const int nx = t.nx, ny = t.ny, x0 = t.x0, y0 = t.y0;
       if (x0 >= CW && x0 + TX + CW <= nx && y0 >= H && y0 + TY + H <= ny) {
-        const float* rp = src + int64_t(y0 - H + warp) * nx + (x0 - CW + lane);
+        // a box row is a run of consecutive cells: 16- or 8-byte copies where
+        // the run's first cell is so aligned (box rows are 16-byte aligned)
+        const float* r0 = src + int64_t(y0 - H + warp) * nx + (x0 - CW);
         const int64_t step = int64_t(NW) * nx;
-        uint32_t d = sbox + 4u * unsigned(warp * W + lane);
+        uint32_t d = sbox + 4u * unsigned(warp * W);
+        static_assert(W % 4 == 0 && W / 4 <= 32 && W / 2 <= 64 && W <= 96, "box row copies");
 #pragma unroll 4
-        for (int br = warp; br < BH; br += NW, rp += step, d += 4u * NW * W) {
-          cp_async_elem<4>(d, rp);
-          cp_async_elem<4>(d + 128u, rp + 32);
-          if (lane < W - 64) cp_async_elem<4>(d + 256u, rp + 64);
+        for (int br = warp; br < BH; br += NW, r0 += step, d += 4u * NW * W) {
+          const unsigned mis = unsigned(reinterpret_cast<uintptr_t>(r0)) & 15u;
+          if (mis == 0) {
+            if (lane < W / 4) cp_async_16(d + 16u * lane, r0 + 4 * lane);
+          } else if ((mis & 7u) == 0) {
+            cp_async_elem<8>(d + 8u * lane, r0 + 2 * lane);
+            if (lane < W / 2 - 32) cp_async_elem<8>(d + 8u * (lane + 32), r0 + 2 * (lane + 32));
+          } else {
+            cp_async_elem<4>(d + 4u * lane, r0 + lane);
+            cp_async_elem<4>(d + 4u * (lane + 32), r0 + lane + 32);
+            if (lane < W - 64) cp_async_elem<4>(d + 4u * (lane + 64), r0 + lane + 64);
+          }
         }
       } else {
         const int bcy0 = t.bc & 255, bcy1 = (t.bc >> 8) & 255;
