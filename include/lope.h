@@ -265,8 +265,10 @@ lope_status lope_tune_cache_load(const char* path, const char* gpu_name, int* lo
  * boundaries (same dtype, nfields and stencil) advanced nsteps each in one
  * persistent launch per call, replayed from a cached CUDA graph.  in/out/work
  * hold n*nfields pointers, grid-major.  workspace is caller device memory of at
- * least lope_batch_workspace_size bytes; it holds the work list and the
- * inter-block barrier and must stay untouched between calls that reuse it.
+ * least lope_batch_workspace_size bytes (about 64 bytes per 64 x 64 tile of
+ * the batch, plus the grid list); it holds the work list, the tile records,
+ * the tile-claim counter and the inter-block barrier, and must stay untouched
+ * between calls that reuse it.
  * cfg may be NULL: the choice of the batch autotuner for this batch (see
  * lope_autotune_batch), else, for FP32 star functions of radius 1-2 (jacobi5,
  * star9r2, linear star tables), the two-sweep register tiles (cfg->path 1:
