@@ -204,8 +204,13 @@ lope_status lope_apply_host(const lope_grid* grid, const lope_stencil* stencil,
  *              stencil, any shape);
  *            3 direct (any stencil, one thread per point);
  *            4 plane march (3D, any stencil and row pitch; not for the
- *              adjoint or source stencils): 64 x 4 column tiles marched along
- *              z through a shared-memory ring of planes.
+ *              adjoint; source stencils only as one-field star functions with
+ *              FP32 / FP64 storage and plain sweeps): tiles marched along z
+ *              through a shared-memory ring of planes.  FP32 / FP64 star
+ *              functions: 64 x 64 tiles (32 x 32 for FP64; tile_y = 1 for a
+ *              builtin: 64 x 32 / 32 x 32) whose planes producer warps copy in;
+ *              box functions and multi-stage steps: 64 x 16 tiles; BF16:
+ *              64 x 4 tiles.
  *            For grids whose row pitch is not a multiple of 16 bytes the
  *            planner takes trapezoid tiles fusing 4 sweeps in 2D (128 x 32
  *            for one field, 64 x 16 for several) and the plane march in 3D.

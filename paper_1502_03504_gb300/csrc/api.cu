@@ -284,8 +284,10 @@ Choice default_choice(const Geom& g, const StencilDesc& s, int* err) {
     return {kPathTrap, 64, 32, 1};
   }
   // 3D rows that cannot be TMA-staged: the plane march (diff7 FP32
-  // 130 x 500 x 510, 20 steps: 2.72 ms against 4.64 ms on the direct kernel),
-  // else the direct kernel (adjoint and run-time compiled functions).
+  // 130 x 500 x 510: 75.5 us per sweep on the copied-plane z-march against
+  // 232 us on the direct kernel), else the direct kernel (the adjoint, and
+  // run-time compiled functions of several fields, box functions, BF16 storage
+  // or multi-stage steps).
   a.ksteps = 1;
   if (march_supported(a)) return {kPathMarch, 0, 0, 1};
   return {kPathDirect, 0, 0, 1};

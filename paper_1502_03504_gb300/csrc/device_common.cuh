@@ -100,10 +100,12 @@ __device__ __forceinline__ F2 sub(F2 a, F2 b) {
   return d;
 }
 // The packed product is an FMA with a -0 addend (a*b + -0 = a*b exactly, with
-// the sign of a zero product kept): ptxas contracts a packed mul.rn followed
-// by a packed add/sub into a single FMA despite the rounding qualifier
-// (measured on sm_103a), which would round a product once less than the
-// scalar paths do; an FMA is never contracted further.
+// the sign of a zero product kept).  ptxas contracts a packed mul.rn followed
+// by a packed add/sub into a single FMA despite the rounding qualifier, and
+// it can still do so with this form (measured on sm_103a: sub(s, mul(3, u))
+// gave fma(-3, u, s) at every point where the two differ), so a product that
+// feeds a sum may round once less than on the scalar paths.  The builtins
+// write such products as fma_, which rounds alike on every path.
 __device__ __forceinline__ F2 mul(F2 a, F2 b) {
   F2 d;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(0x8000000080000000ull));

@@ -260,6 +260,14 @@ constexpr int tma_index(bool stage, bool wrap, bool tall) {
   return kNumKernels + (stage ? 4 : 0) + (wrap ? 2 : 0) + (tall ? 1 : 0);
 }
 constexpr int tb2_index(bool wrap) { return kNumKernels + 8 + (wrap ? 1 : 0); }
+// The z-march with planes copied by producer warps (ca3d_kernel, tall tiles)
+// follows at march_index(): 3D star functions of one field with FP32 / FP64
+// storage, for grids whose rows TMA cannot stage.
+constexpr int march_index() { return kNumKernels + 10; }
+template <class T, int RANK, int NF>
+constexpr bool jit_march() {
+  return RANK == 3 && NF == 1 && !std::is_same<T, __nv_bfloat16>::value;
+}
 
 // Whether the two-sweep kernels are compiled for the program: FP32 / BF16
 // storage, star functions of one field and radius 1 in 3D, functions of
@@ -276,8 +284,17 @@ template <int NF> constexpr int jit_tb2_ry() { return NF == 1 ? 8 : 2; }
 template <class T, int RANK, int R, int NF>
 void all_names(const JitProgram& jp, std::vector<std::string>* names) {
   kernel_names<T, RANK, R, NF>(jp, names);
-  names->resize(kNumKernels + 10);
+  names->resize(kNumKernels + 11);
   if (!jp.tma_ok()) return;
+  if constexpr (jit_march<T, RANK, NF>()) {
+    using CR = CaRunner<UserOpHost<RANK, R, NF, true>, T>;
+    using S_ = typename CR::template Sh<true>;
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "&lope::ca3d_kernel<lope::UserOp, %s, %d, %d, %d, %d, %s, %d>",
+                  std::is_same<T, float>::value ? "float" : "double", S_::TX, S_::TY, S_::RY,
+                  CR::template stages<true>(), CR::PAIR ? "true" : "false", CR::NPW);
+    (*names)[march_index()] = buf;
+  }
   for (int stage = 0; stage < 2; ++stage)
     for (int wrap = 0; wrap < 2; ++wrap) {
       (*names)[tma_index(stage, wrap, true)] = tma_name<T, RANK, R, NF, true>(stage, wrap);
@@ -538,6 +555,53 @@ cudaError_t run_tma(JitProgram& jp, const StepArgs& a, int dtype) {
                      : run_tma_t<T, RANK, R, NF, false>(jp, a, dtype);
 }
 
+// One sweep on the copied-plane z-march (march_supported decided the grid),
+// with the builtins' tiles, ring depth and z-chunk split.
+template <class T, int RANK, int R, int NF>
+cudaError_t run_march(JitProgram& jp, const StepArgs& a, int dtype) {
+  if constexpr (jit_march<T, RANK, NF>()) {
+    if (!jp.star || a.stage >= 2 || a.ksteps != 1) return cudaErrorNotSupported;
+    using Host = UserOpHost<RANK, R, NF, true>;
+    using CR = CaRunner<Host, T>;
+    using S_ = typename CR::template Sh<true>;
+    constexpr size_t smem = CR::template smem<true>();
+    constexpr int threads = CR::template threads<true>();
+    CUfunction f = nullptr;
+    int occ = 1, blocks = 0, zchunk = 0;
+    cudaError_t e = get_kernel(jp, dtype, march_index(), smem, threads, &f, &occ);
+    if (e != cudaSuccess) return e;
+    if (!march_chunks(a.g, S_::TX, S_::TY, R, occ, &blocks, &zchunk))
+      return cudaErrorInvalidConfiguration;
+    TmaParams<Host, T> p;
+    for (int i = 0; i < kUserParams; ++i) p.op.p[i] = jp.prm[i];
+    p.op.err = a.err;
+    p.nx = int(a.g.n[2]);
+    p.ny = int(a.g.n[1]);
+    p.nz = int(a.g.n[0]);
+    p.per_x = p.per_y = p.per_z = 0;  // the producers apply every side's rule
+    p.tiles_x = (p.nx + S_::TX - 1) / S_::TX;
+    p.tiles_y = (p.ny + S_::TY - 1) / S_::TY;
+    p.zchunk = zchunk;
+    p.nunits = blocks;
+    p.soff = 0;
+    p.sext = 0;
+    for (int k = 0; k < kMaxFields; ++k) {
+      p.in[k] = k < NF ? static_cast<const T*>(a.in[k]) : nullptr;
+      p.out[k] = k < NF ? static_cast<T*>(a.out[k]) : nullptr;
+    }
+    p.partials = nullptr;
+    p.err = a.err;
+    Geom g = a.g;
+    void* args[] = {&g, &p};
+    return launch(f, blocks, threads, smem, a.stream, args);
+  } else {
+    (void)jp;
+    (void)a;
+    (void)dtype;
+    return cudaErrorNotSupported;
+  }
+}
+
 template <class T, int RANK, int R, int NF>
 cudaError_t run_direct(JitProgram& jp, const StepArgs& a, int dtype) {
   using Host = UserOpHost<RANK, R, NF, true>;
@@ -634,6 +698,7 @@ cudaError_t jit_launch(const StepArgs& a, int path) {
     constexpr int RANK = decltype(rank)::value, R = decltype(r)::value, NF = decltype(nf)::value;
     if (path == kPathTma) return run_tma<T, RANK, R, NF>(*jp, a, dtype);
     if (path == kPathTrap) return run_trap<T, RANK, R, NF>(*jp, a, dtype);
+    if (path == kPathMarch) return run_march<T, RANK, R, NF>(*jp, a, dtype);
     return run_direct<T, RANK, R, NF>(*jp, a, dtype);
   });
 }

@@ -33,8 +33,12 @@ bool direct_supported(const StepArgs& a) { return a.ksteps == 1; }
 
 bool march_supported(const StepArgs& a) {
   int blocks = 0, zchunk = 0;
-  return a.g.ndim == 3 && !a.adjoint && a.s.kind != kUser && a.ksteps == 1 &&
-         !has_external(a.g) && march_geometry(a.g, &blocks, &zchunk);
+  // Run-time compiled functions take the copied-plane z-march: one-field star
+  // functions with FP32 / FP64 storage, plain sweeps only.
+  const bool user_ok = a.s.kind != kUser || (a.s.star && a.g.nf == 1 && a.g.dtype != kBF16 &&
+                                             a.s.stages == 1 && a.stage < 2);
+  return a.g.ndim == 3 && !a.adjoint && user_ok && a.ksteps == 1 && !has_external(a.g) &&
+         march_geometry(a.g, &blocks, &zchunk);
 }
 
 cudaError_t launch_trap2d(const StepArgs& a) {
@@ -51,6 +55,7 @@ cudaError_t launch_direct(const StepArgs& a, int* blocks) {
   return dispatch_generic<false>(a, kGenDirect, blocks);
 }
 cudaError_t launch_march(const StepArgs& a) {
+  if (a.s.kind == kUser) return jit_launch(a, kPathMarch);
   if (a.stage >= 2) return launch_generic_rk(a, kGenMarch, nullptr);
   return dispatch_generic<false>(a, kGenMarch, nullptr);
 }

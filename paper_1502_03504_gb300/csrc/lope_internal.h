@@ -107,8 +107,9 @@ bool tma_supported(const StepArgs& a);
 cudaError_t launch_trap2d(const StepArgs& a);
 bool trap2d_supported(const StepArgs& a);
 cudaError_t launch_direct(const StepArgs& a, int* blocks);
-// 3D plane march for grids the TMA tiles cannot stage (not for adjoint or
-// run-time compiled functions).
+// 3D plane march for grids the TMA tiles cannot stage (not for the adjoint;
+// run-time compiled functions: one-field star functions, FP32 / FP64, plain
+// sweeps).
 cudaError_t launch_march(const StepArgs& a);
 bool march_supported(const StepArgs& a);
 // Run-time compiled local functions (jit.cu).
@@ -118,8 +119,8 @@ lope_status jit_create(const char* body, int ndim, int radius, int nf, bool star
 void jit_destroy(JitProgram* jp);
 lope_status jit_compile(JitProgram* jp, int dtype, std::string* err);
 bool jit_tma_ok(const JitProgram* jp);
-// Launch one sweep / stage of a kUser stencil on path kPathTma, kPathTrap or
-// kPathDirect (a.stage >= 2: combining Runge-Kutta stage; a.s.stages >= 2 on
+// Launch one sweep / stage of a kUser stencil on path kPathTma, kPathTrap,
+// kPathMarch or kPathDirect (a.stage >= 2: combining Runge-Kutta stage; a.s.stages >= 2 on
 // the trapezoid: fused steps).
 cudaError_t jit_launch(const StepArgs& a, int path);
 

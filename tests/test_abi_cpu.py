@@ -252,6 +252,38 @@ def test_planner_default_choices(lope, capfd, case, fake_addresses):
     assert f"launches={launches}" in err
 
 
+USER_PLAN_CASES = [  # dtype, nfields, box, scheme, expected path on rows TMA cannot stage
+    ("f32", 1, False, "euler", "march"),
+    ("f64", 1, False, "euler", "march"),
+    ("bf16", 1, False, "euler", "direct"),
+    ("f32", 1, True, "euler", "direct"),
+    ("f32", 1, False, "rk3", "direct"),
+    ("f32", 2, False, "euler", "direct"),
+]
+
+
+@pytest.mark.parametrize("case", USER_PLAN_CASES, ids=lambda c: "-".join(map(str, c)))
+def test_planner_user_function_on_unaligned_3d_rows(lope, case, fake_addresses):
+    """Run-time compiled functions on 3D rows whose pitch TMA cannot stage: the
+    copied-plane z-march for one-field star functions with FP32 / FP64 storage
+    and plain sweeps, else the direct kernel (plan query only, no CUDA call)."""
+    dtype, nf, box, scheme, want = case
+    shape = (130, 500, 509)
+    body = "\n".join(f"out[{k}] = add(U({k}, 0, 0, 0), mul(P[0], U({k}, 1, 0, 0)));"
+                      for k in range(nf))
+    g = lope.Grid(shape, dtype, halo=1, nfields=nf)
+    g.set_boundaries([1, 0, 1])
+    st = lope.Stencil.source(body, ndim=3, radius=1, nfields=nf, params=[0.1], box=box)
+    st.set_scheme(scheme)
+    field = int(np.prod(shape)) * {"f32": 4, "f64": 8, "bf16": 2}[dtype]
+    base = 1 << 44
+    ins = [base + k * field for k in range(nf)]
+    outs = [base + (nf + k) * field for k in range(nf)]
+    works = [base + (2 * nf + 2 * k) * field for k in range(nf)]
+    plan, _ = lope.lope_plan(g.handle, st.handle, ins, outs, works, 10)
+    assert {3: "direct", 4: "march"}.get(plan.path) == want, plan.path
+
+
 def test_apply_host_checks_device_buffers_before_copying(lope, fake_addresses):
     """lope_apply_host refuses bad device buffers before it issues any copy (on a
     machine without a GPU the error is the argument's, not a CUDA error)."""

@@ -19,7 +19,7 @@ from user_bodies import DIFF7, GRAY_SCOTT, GRAY_SCOTT_PRM, JACOBI5, SWE_FLUX
 
 pytestmark = pytest.mark.gpu
 
-TMA, TRAP, DIRECT = 1, 2, 3
+TMA, TRAP, DIRECT, MARCH = 1, 2, 3, 4
 FLUX = [0.02, 1.0, 0.5, 1.0]
 
 
@@ -271,6 +271,53 @@ def test_user_3d_box_takes_direct_path(lope, orc):
     got = to_host(_run(lope, g, st, u0, T)[0])
     want = orc.apply_source(u0s, BOX_3D, [0.1], T, bc=[0, 0, 1])
     assert normwise(got, want) <= 1e-12
+
+
+# Asymmetric taps of radius 2; products that feed a sum are written as fma_,
+# so that the paired FP32 tiles round as the scalar kernels do.
+STAR_R2_3D = """
+const C u = U(0, 0, 0, 0);
+const C far = add(add(U(0, 2, 0, 0), U(0, -2, 0, 0)), add(U(0, 0, 2, 0), U(0, 0, 0, -2)));
+const C near = add(add(U(0, 1, 0, 0), U(0, 0, -1, 0)), U(0, 0, 0, 1));
+out[0] = fma_(P[0], fma_(C(-4), u, far), fma_(P[1], fma_(C(-3), u, near), u));
+"""
+
+
+# 205 and 206 points per row: FP32 rows TMA cannot stage, starting at every
+# 4-byte (205) or 8-byte (206) offset; 45 points: tiles narrower than the box.
+@pytest.mark.parametrize("shape", [(12, 70, 205), (9, 67, 206), (21, 19, 45)],
+                         ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_user_3d_unaligned_rows_take_the_march(lope, orc, dtype, shape, capfd):
+    """One-field star functions on rows TMA cannot stage run on the copied-plane
+    z-march by default: bitwise the builtin diff7 on the march and the
+    function's own direct kernel; a radius-2 function also matches the oracle
+    (FP64: normwise 1e-12)."""
+    T = 5
+    u0, u0s = to_device(LI.uniform_field(1460, shape), dtype)
+    bval = [(0.5, -0.3), -0.25, (1.0, 0.2)]
+    for bc in ([1, 0, 1], [0, 0, 0], [1, 1, 1]):
+        g = _grid(lope, shape, dtype, 1, bc, bval)
+        user = lope.Stencil.source(DIFF7, ndim=3, radius=1, params=[0.1])
+        lope.lope_set_option("log", 1)
+        try:
+            a = _run(lope, g, user, u0, T)[0]
+        finally:
+            lope.lope_set_option("log", 0)
+        log = capfd.readouterr().err
+        if (shape[2] * (8 if dtype == "f64" else 4)) % 16:  # rows TMA cannot stage
+            assert "path=march" in log, bc
+        builtin = lope.Stencil.builtin("diff7", 0.1)
+        assert torch.equal(a, _run(lope, g, builtin, u0, T, _launch(lope, MARCH))[0]), bc
+        assert torch.equal(a, _run(lope, g, user, u0, T, _launch(lope, DIRECT))[0]), bc
+    bc = [1, 0, 0]
+    g = _grid(lope, shape, dtype, 2, bc, bval)
+    st = lope.Stencil.source(STAR_R2_3D, ndim=3, radius=2, params=[0.03, 0.05])
+    a = _run(lope, g, st, u0, T, _launch(lope, MARCH))[0]
+    assert torch.equal(a, _run(lope, g, st, u0, T, _launch(lope, DIRECT))[0])
+    if dtype == "f64":
+        want = orc.apply_source(u0s, STAR_R2_3D, [0.03, 0.05], T, bc=bc, bval=bval)
+        assert normwise(to_host(a), want) <= 1e-12
 
 
 def test_user_trapezoid_with_large_shared_memory(lope, orc):
