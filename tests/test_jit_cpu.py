@@ -45,6 +45,23 @@ for (int f = 0; f < 3; ++f)
     lope.Stencil.source(body, ndim=2, radius=2, nfields=3, params=[0.1, 0.2, 0.3]).compile("f32")
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64", "bf16"])
+def test_3d_radius_two_star_and_three_fields_compile(lope, dtype):
+    """3D instances beyond diff7: a radius-2 star function (TMA z-march, and for
+    FP32 / FP64 the z-march with copied planes) and three coupled fields."""
+    star_r2 = """
+const C u = U(0, 0, 0, 0);
+const C far = add(add(U(0, 2, 0, 0), U(0, -2, 0, 0)), add(U(0, 0, 2, 0), U(0, 0, 0, -2)));
+out[0] = fma_(P[0], fma_(C(-4), u, far), u);
+"""
+    three = """
+for (int f = 0; f < 3; ++f)
+  out[f] = fma_(P[0], sub(U((f + 1) % 3, 0, 0, 1), U(f, 1, 0, 0)), U(f, 0, 0, 0));
+"""
+    lope.Stencil.source(star_r2, ndim=3, radius=2, params=[0.05]).compile(dtype)
+    lope.Stencil.source(three, ndim=3, radius=1, nfields=3, params=[0.1]).compile(dtype)
+
+
 def test_compile_error_reports_the_compiler_log(lope):
     st = lope.Stencil.source("out[0] = U(0, 0, 0) + undefined_name;", params=[1.0])
     with pytest.raises(lope.LopeError, match="undefined_name"):
