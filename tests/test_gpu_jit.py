@@ -15,7 +15,7 @@ import torch
 import lope_inputs as LI
 from error_bounds import gray_scott_majorant
 from gpu_helpers import normwise, to_device, to_host
-from user_bodies import DIFF7, GRAY_SCOTT, GRAY_SCOTT_PRM, JACOBI5, SWE_FLUX
+from user_bodies import DIFF7, GRAY_SCOTT, GRAY_SCOTT_PRM, JACOBI5, STAR_R2_3D, SWE_FLUX
 
 pytestmark = pytest.mark.gpu
 
@@ -271,16 +271,6 @@ def test_user_3d_box_takes_direct_path(lope, orc):
     got = to_host(_run(lope, g, st, u0, T)[0])
     want = orc.apply_source(u0s, BOX_3D, [0.1], T, bc=[0, 0, 1])
     assert normwise(got, want) <= 1e-12
-
-
-# Asymmetric taps of radius 2; products that feed a sum are written as fma_,
-# so that the paired FP32 tiles round as the scalar kernels do.
-STAR_R2_3D = """
-const C u = U(0, 0, 0, 0);
-const C far = add(add(U(0, 2, 0, 0), U(0, -2, 0, 0)), add(U(0, 0, 2, 0), U(0, 0, 0, -2)));
-const C near = add(add(U(0, 1, 0, 0), U(0, 0, -1, 0)), U(0, 0, 0, 1));
-out[0] = fma_(P[0], fma_(C(-4), u, far), fma_(P[1], fma_(C(-3), u, near), u));
-"""
 
 
 # 205 and 206 points per row: FP32 rows TMA cannot stage, starting at every

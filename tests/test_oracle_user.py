@@ -7,7 +7,7 @@ import pytest
 
 import lope_inputs as LI
 from dense_ref import normwise
-from user_bodies import DIFF7, GRAY_SCOTT, GRAY_SCOTT_PRM, JACOBI5, SWE_FLUX
+from user_bodies import DIFF7, GRAY_SCOTT, GRAY_SCOTT_PRM, JACOBI5, STAR_R2_3D, SWE_FLUX
 
 
 @pytest.mark.parametrize("scheme", ["euler", "rk3"])
@@ -34,6 +34,43 @@ def test_user_swe_flux_reproduces_builtin(orc):
     b = orc.apply_source([h - 1, u, v], SWE_FLUX, prm, 20)
     for k in range(3):
         assert normwise(b[k], a[k]) <= 1e-13
+
+
+def _padded(u, R, bc, bval):
+    """u with an R-wide halo on every side: the wrapped cells for a periodic
+    side, the side's constant for a Dirichlet side (star functions read no
+    corner, so the order of the axes does not matter)."""
+    p = u
+    for ax in range(u.ndim):
+        if bc[ax] == 0:
+            p = np.concatenate([np.take(p, range(-R, 0), axis=ax), p,
+                                np.take(p, range(0, R), axis=ax)], axis=ax)
+        else:
+            lo, hi = bval[ax]
+            shape = list(p.shape)
+            shape[ax] = R
+            p = np.concatenate([np.full(shape, lo), p, np.full(shape, hi)], axis=ax)
+    return p
+
+
+@pytest.mark.parametrize("bc", [[1, 0, 0], [0, 1, 1], [0, 0, 0]])
+def test_user_radius_two_3d_matches_brute_force(orc, bc):
+    """An asymmetric radius-2 star body in 3D, per-side Dirichlet values: the
+    oracle's user path against slices of an explicitly padded array."""
+    shape, T, R, (a, b) = (7, 9, 11), 4, 2, (0.03, 0.05)
+    bval = [(0.5, -0.3), (-0.25, 0.4), (1.0, 0.2)]
+    u = LI.uniform_field(43, shape)
+    want = u.copy()
+    nz, ny, nx = shape
+    for _ in range(T):
+        p = _padded(want, R, bc, bval)
+        tap = lambda dx, dy, dz: p[R + dz:R + dz + nz, R + dy:R + dy + ny, R + dx:R + dx + nx]
+        c = tap(0, 0, 0)
+        far = (tap(2, 0, 0) + tap(-2, 0, 0)) + (tap(0, 2, 0) + tap(0, 0, -2))
+        near = (tap(1, 0, 0) + tap(0, -1, 0)) + tap(0, 0, 1)
+        want = a * (far - 4 * c) + (b * (near - 3 * c) + c)
+    got = orc.apply_source(u, STAR_R2_3D, [a, b], T, bc=bc, bval=bval)
+    assert normwise(got, want) <= 1e-14
 
 
 def test_gray_scott_uniform_state_is_the_reaction_map(orc):

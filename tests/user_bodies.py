@@ -53,3 +53,12 @@ out[0] = fma_(P[0], fma_(P[1], lu, fma_(P[3], sub(C(1), u), -uvv)), u);
 out[1] = fma_(P[0], fma_(P[2], lv, fma_(-add(P[3], P[4]), v, uvv)), v);
 """
 GRAY_SCOTT_PRM = [1.0, 0.16, 0.08, 0.035, 0.065]
+
+# Asymmetric taps of radius 2 in 3D (P = (a, b)); products that feed a sum are
+# written as fma_, so that the paired FP32 tiles round as the scalar kernels do.
+STAR_R2_3D = """
+const C u = U(0, 0, 0, 0);
+const C far = add(add(U(0, 2, 0, 0), U(0, -2, 0, 0)), add(U(0, 0, 2, 0), U(0, 0, 0, -2)));
+const C near = add(add(U(0, 1, 0, 0), U(0, 0, -1, 0)), U(0, 0, 0, 1));
+out[0] = fma_(P[0], fma_(C(-4), u, far), fma_(P[1], fma_(C(-3), u, near), u));
+"""
